@@ -1,0 +1,366 @@
+"""Benchmark: node-source updates per second of the leapfrog wave path.
+
+One step = one pass of the whole path over the 2D asteroid workload
+(62,641 nodes, 124,416 P1 triangles, 128 backscatter shots, 8000 leapfrog
+steps): the batched forward (keeping checkpoints every 256 steps), the
+adjoint gradient J^T w on the 7,776 level-1 cells (w = the traces, i.e. the
+gradient of 0.5 |y|^2; recomputation from the checkpoints), and one tangent
+J v.  Units per step: n * S * nt for each of the three wave fields that the
+method needs (forward, adjoint, tangent); the recomputation inside the
+adjoint pass and the forward re-run inside the tangent pass are overhead and
+are not counted.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import configs  # noqa: E402
+
+METRIC = "node-source updates/s (forward + adjoint + tangent wave fields)"
+UNIT = "node*source updates/s"
+CKPT = 256
+LEVEL = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nt", type=int, default=None, help="override the step count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_for_rank(rank: int, nt=None):
+    # weak scaling: every rank owns a full 128-shot batch; rank r's shots sit
+    # at angles offset by r/(world) of the shot spacing (a different batch)
+    w = configs.asteroid_2d(nt=nt or 8000)
+    if rank:
+        from workloads import shots as shots_mod
+
+        S = w.shots.n_shots
+        th_off = 2 * math.pi * rank / (S * 8)
+        w.shots = shots_mod.asteroid_shots(w.mesh, S, rotation=th_off)
+    return w
+
+
+def describe(w):
+    m = w.mesh
+    return (f"asteroid_2d: {m.coords.shape[0]} nodes, {m.cells.shape[0]} P1 triangles "
+            f"(level 0: {m.n_cells[0]}), {w.shots.n_shots} backscatter shots, {w.nt} steps; "
+            f"forward + J^T w on {m.n_cells[LEVEL]} level-{LEVEL} cells (checkpoints every "
+            f"{CKPT}) + J v")
+
+
+def clocks_start():
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def clocks_stop(proc, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except Exception:
+        proc.kill()
+        return None
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or f[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, f[5:9]):
+            if val.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(w, dt, budget_s=20.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the same workload: 2 shots, forward + tangent + adjoint over nt_s steps."""
+    from oracle import wave
+
+    m = w.mesh
+    pb = wave.Problem(m.coords, m.cells, m.bnd, w.eps, w.bc)
+    sub = w.shots.subset([0, 1])
+    nt_s = 400
+    s = w.wavelet(dt, nt_s)
+    t0 = time.perf_counter()
+    y = wave.forward(pb, dt, s, sub.src, sub.rec_ptr, sub.rec)
+    v = np.zeros(m.n_cells[LEVEL])
+    v[0] = 1.0
+    wave.tangent(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, wave.prolong(v, m.ancestor(LEVEL)))
+    wave.adjoint_eps(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, y)
+    el = time.perf_counter() - t0
+    units = 3.0 * m.coords.shape[0] * sub.n_shots * nt_s
+    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"2 of {w.shots.n_shots} shots, {nt_s} of {w.nt} steps, forward + tangent "
+                      f"+ adjoint on the full mesh ({el:.1f} s, single-threaded numpy/scipy)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload_for_rank(0, args.nt)
+    from oracle import wave
+
+    m = w.mesh
+    pb = wave.Problem(m.coords, m.cells, m.bnd, w.eps, w.bc)
+    dt = w.cfl_fraction * pb.cfl_dt()
+    sub = w.shots.subset([0])
+    nt_s = 200
+    s = w.wavelet(dt, nt_s)
+    v = np.zeros(m.n_cells[LEVEL])
+    v[0] = 1.0
+    de = wave.prolong(v, m.ancestor(LEVEL))
+
+    def step():
+        y = wave.forward(pb, dt, s, sub.src, sub.rec_ptr, sub.rec)
+        wave.tangent(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, de)
+        wave.adjoint_eps(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, y)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    units = 3.0 * m.coords.shape[0] * sub.n_shots * nt_s * args.steps
+    val = units / el
+    sample = (f"1 of {w.shots.n_shots} shots, {nt_s} of {w.nt} steps per step, forward + "
+              f"tangent + adjoint on the full mesh, single-threaded numpy/scipy FP64")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": describe(w)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1707_04605_gb300 import build as _build
+
+    if rank == 0:
+        _build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import paper_1707_04605_gb300 as mg
+
+    w = workload_for_rank(rank, args.nt)
+    mesh = mg.mesh_from_workload(w)
+    n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
+    eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
+    dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)
+    wav = w.wavelet(dt)
+    wav_d = torch.as_tensor(wav, dtype=torch.float64, device=dev)
+    nlev = w.mesh.n_cells[LEVEL]
+    v = np.zeros(nlev)
+    v[np.random.default_rng(0).integers(nlev)] = 1.0
+    v_d = torch.as_tensor(v, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def allreduce(g):
+        if ws > 1:
+            torch.distributed.all_reduce(g)
+        return g
+
+    phase_ev = {}
+
+    def step(record=False):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        evs[0].record(stream)
+        y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, ckpt_every=CKPT, keep_checkpoints=True)
+        evs[1].record(stream)
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=CKPT,
+                                reuse_checkpoints=True)
+        allreduce(g)
+        evs[2].record(stream)
+        mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d)
+        evs[3].record(stream)
+        if record:
+            phase_ev.setdefault("ev", []).append(evs)
+        return evs
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks_start() if rank == 0 else None
+    launches0 = mesh.launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # evict L2 between timed steps
+        evs = step(record=True)
+        times.append(evs)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = mesh.launch_count() - launches0
+    clocks = clocks_stop(clk, dev.index) if rank == 0 else None
+    step_ms = [e[0].elapsed_time(e[3]) for e in times]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in times]
+    adj_ms = [e[1].elapsed_time(e[2]) for e in times]
+    tan_ms = [e[2].elapsed_time(e[3]) for e in times]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    units_per_step = 3.0 * n * S * nt
+    value = units_per_step * args.steps * ws / total_s
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    pin = lambda a, dt_: torch.as_tensor(np.ascontiguousarray(a), dtype=dt_).pin_memory().numpy()
+    eps_h, wav_h, v_h = pin(w.eps, torch.float64), pin(wav, torch.float64), pin(v, torch.float64)
+
+    def step_host():
+        y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, ckpt_every=CKPT, keep_checkpoints=True)
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, y, ckpt_every=CKPT,
+                                reuse_checkpoints=True)
+        if ws > 1:
+            gt = torch.as_tensor(g, device=dev)
+            allreduce(gt)
+            g = gt.cpu().numpy()
+        jv = mg.jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h)
+        return y, g, jv
+
+    y, g, jv = step_host()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        y, g, jv = step_host()
+    e2e_s = time.perf_counter() - t0
+    R = w.shots.n_traces
+    h2d = 3 * (w.eps.nbytes + wav.nbytes) + 4 * R * nt + v.nbytes
+    d2h = 4 * R * nt + 8 * nlev + 4 * R * nt
+
+    # plain single-source GPU path on the same workload (forward only, 4 shots)
+    sub = w.shots.subset(range(4))
+    for _ in range(2):
+        mg.forward(mesh, eps_d, sub, wav_d, dt, single_source=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mg.forward(mesh, eps_d, sub, wav_d, dt, single_source=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_rate = n * 4 * nt / (e0.elapsed_time(e1) / 1e3)
+    fwd_rate = n * S * nt / (statistics.mean(fwd_ms) / 1e3)
+
+    if rank != 0:
+        return 0
+    # roofline of the batched forward step kernel: algorithmic bytes per launch
+    info = mesh.info()
+    S_pad = S
+    bytes_fwd = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
+    fwd_launch_s = statistics.mean(fwd_ms) / 1e3 / nt   # includes launch gaps
+    peak, peak_kind = peaks()
+    achieved = bytes_fwd / fwd_launch_s / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": describe(w), "nodes": n, "shots": S, "nt": nt,
+                   "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "phases_ms": {"forward": statistics.mean(fwd_ms), "adjoint": statistics.mean(adj_ms),
+                      "tangent": statistics.mean(tan_ms)},
+        "forward_updates_per_s": fwd_rate,
+        "single_source_forward_updates_per_s": single_rate,
+        "batched_vs_single_source": fwd_rate / single_rate,
+        "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": bytes_fwd,
+                     "note": "per-launch time = forward phase / nt (includes launch gaps); "
+                             "state (2 x 32 MB) is L2-resident"},
+        "e2e": {"value": units_per_step * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, dt)
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

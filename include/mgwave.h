@@ -1,0 +1,201 @@
+/*
+ * mgwave.h - C ABI of the GB300 leapfrog wave-propagation library.
+ *
+ * The library advances the scalar wave equation (pde1) of Takala, Us and
+ * Pursiainen, "Multigrid-based inversion for volumetric radar imaging"
+ * (Sec. II-A/II-B, App. A), discretised with nodal P1 elements on a nested
+ * simplex mesh, by the explicit leapfrog of Eqs. (leap-frog1)-(leap-frog2)
+ * with the flux eliminated:
+ *
+ *   (M + dt/2 D) p_{l+1} = 2 M p_l - (M - dt/2 D) p_{l-1} - dt^2 (K p_l - s_l e_src)
+ *
+ * K  P1 stiffness, K_ij = sum_e |e| grad phi_i . grad phi_j (App. A: the
+ *    product sum_k B^(k)T A^-1 B^(k));
+ * M  lumped eps-mass, m_i = sum_{e contains i} eps_e |e| / (d+1)
+ *    (App. A's C, lumped);
+ * D  first-order absorbing boundary (du/dn = -sqrt(eps) du/dt), lumped:
+ *    D_ii = sum_{boundary facets F contains i} sqrt(eps_{e(F)}) |F| / d.
+ *    It replaces App. A's split-field PML.
+ * s  wavelet samples s_l = s(l dt); p_0 = p_{-1} = 0.
+ *
+ * Sample l of the trace of receiver node r of a shot is p_{l+1}[r].
+ *
+ * The Jacobian is the exact derivative of the traces with respect to the
+ * permittivity of the cells of a chosen coarse level of the nested mesh
+ * (Sec. II-B: eps_r = sum_j c_j chi'_j; the partial derivatives dp_l/dc_j).
+ * Its tangent form is the auxiliary system of Eqs. (aku_ankka),
+ * (linearized1)-(linearized2); its transpose is the discrete adjoint.
+ *
+ * Conventions for every call:
+ *  - returns MG_OK (0) or a negative MG_ERR_* code; mg_strerror() names it;
+ *  - node and cell ids are the caller's; the internal reordering is hidden;
+ *  - the caller owns every input and output buffer; the mesh handle owns
+ *    the device copy of the mesh and all scratch (states, checkpoints);
+ *  - array arguments marked "data" are DEVICE pointers unless the call's
+ *    flags contain MG_HOST_PTRS, in which case they are host pointers and
+ *    the call copies them in and out itself and returns after the results
+ *    have reached the host.  Shot descriptions are always host memory;
+ *  - without MG_HOST_PTRS, work is queued on `stream` (a cudaStream_t, or
+ *    NULL for the legacy default stream) and the call may return before it
+ *    completes; outputs are valid once the stream has reached that point;
+ *  - a handle must not be used by two calls at the same time (the scratch
+ *    is shared); distinct handles are independent;
+ *  - the current CUDA device at create time is the handle's device.
+ */
+#ifndef MGWAVE_H
+#define MGWAVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MG_OK                 0
+#define MG_ERR_ARG           -1  /* invalid argument (null, range, shape)   */
+#define MG_ERR_NESTING       -2  /* parent maps do not describe a nesting   */
+#define MG_ERR_OOM           -3  /* device allocation failed                */
+#define MG_ERR_CUDA          -4  /* CUDA runtime error (no device, launch)  */
+#define MG_ERR_CFL           -5  /* dt above the stability bound           */
+#define MG_ERR_TIMEOUT       -6  /* a bounded device wait ran out           */
+#define MG_ERR_UNSUPPORTED   -7  /* valid but not supported combination     */
+
+/* ---- boundary modes ---------------------------------------------------- */
+#define MG_BC_ABC1       0  /* first-order absorbing boundary (default)     */
+#define MG_BC_NEUMANN    1  /* natural boundary, D = 0                      */
+#define MG_BC_DIRICHLET  2  /* boundary nodes held at 0                      */
+
+/* ---- mesh_create flags ------------------------------------------------- */
+#define MG_ORDER_RCM     0  /* reverse Cuthill-McKee row order (default)    */
+#define MG_ORDER_MORTON  1  /* Z-order of node coordinates                  */
+#define MG_ORDER_NONE    2  /* caller order                                 */
+
+/* ---- per-call flags ---------------------------------------------------- */
+#define MG_HOST_PTRS        0x01  /* data pointers are host memory          */
+#define MG_SINGLE_SOURCE    0x02  /* run the plain one-shot-at-a-time path   */
+#define MG_NO_GRAPH         0x04  /* plain launches, no CUDA graph           */
+#define MG_PERSISTENT       0x08  /* multi-step persistent launch            */
+#define MG_ALLOW_CFL        0x10  /* do not reject dt above the CFL bound    */
+#define MG_KEEP_CHECKPOINTS 0x20  /* mg_forward: keep (p_l, p_{l-1}) every
+                                     ckpt_every steps in the handle for a
+                                     later mg_jacobian_T_apply               */
+#define MG_REUSE_CHECKPOINTS 0x40 /* mg_jacobian_T_apply: use the
+                                     checkpoints of the last mg_forward on
+                                     this handle (same eps, shots, wavelet,
+                                     dt, nt) instead of re-running it        */
+
+typedef struct mg_mesh mg_mesh;
+
+/* A batch of shots (host memory).  Shot k places the point source of
+ * Eq. (pde1) at node src[k] (nodal load int delta_p phi_i = 1, App. A's
+ * f_i) and records receivers rec[rec_ptr[k] .. rec_ptr[k+1]-1].  Trace rows
+ * are numbered in that order: row r of a trace array belongs to the shot k
+ * with rec_ptr[k] <= r < rec_ptr[k+1]. */
+typedef struct {
+  int32_t n_shots;
+  const int32_t* src;      /* [n_shots]                   */
+  const int64_t* rec_ptr;  /* [n_shots + 1], rec_ptr[0]=0 */
+  const int32_t* rec;      /* [rec_ptr[n_shots]]          */
+} mg_shots;
+
+typedef struct {
+  int32_t dim;
+  int32_t n_levels;
+  int64_t n_nodes;
+  int64_t n_cells;        /* finest level                          */
+  int64_t n_bnd;
+  int64_t nnz;            /* stiffness non-zeros                   */
+  int64_t ell_entries;    /* sliced-ELL entries incl. padding      */
+  int32_t slice_height;
+  int32_t max_row_nnz;
+  int64_t device_bytes;   /* device memory held by the handle now  */
+} mg_mesh_info_t;
+
+/* Build a mesh handle (Sec. II-B nested meshes, App. A assembly).
+ *  dim            2 (triangles) or 3 (tetrahedra)
+ *  n_levels       L+1 >= 1 levels, level L the finest
+ *  coords         [n_nodes][dim] float64, finest-level nodes (host)
+ *  cells          [n_cells][dim+1] int32, finest-level cells (host)
+ *  cell_parent    n_levels-1 host arrays; cell_parent[l-1][c] is the cell
+ *                 of level l-1 containing cell c of level l (the nesting /
+ *                 prolongation map).  May be NULL when n_levels == 1.
+ *  n_cells_per_level [n_levels], last entry == n_cells
+ *  bnd            [n_bnd][dim] int32 boundary facets (host); each must be a
+ *                 facet of exactly one cell
+ *  bc_mode        MG_BC_*
+ *  order          MG_ORDER_*
+ * Errors: MG_ERR_ARG (shapes, ids out of range, degenerate cell, facet not
+ * on a cell), MG_ERR_NESTING (parent id out of range, a coarse cell with no
+ * child), MG_ERR_CUDA / MG_ERR_OOM (device).  Argument checks run before
+ * any CUDA call. */
+int mg_mesh_create(int dim, int n_levels, const double* coords, int64_t n_nodes,
+                   const int32_t* cells, int64_t n_cells,
+                   const int32_t* const* cell_parent,
+                   const int64_t* n_cells_per_level, const int32_t* bnd,
+                   int64_t n_bnd, int bc_mode, int order, mg_mesh** out);
+
+void mg_mesh_destroy(mg_mesh* mesh);
+
+int mg_mesh_get_info(const mg_mesh* mesh, mg_mesh_info_t* info);
+
+/* Internal row of each caller node id ([n_nodes] int32, host). */
+int mg_mesh_get_permutation(const mg_mesh* mesh, int32_t* perm);
+
+/* Stability bound dt_cfl = 2 / sqrt(max_i sum_j |K_ij| / m_i) (Gershgorin
+ * bound of the largest eigenvalue of M^-1 K) for the permittivity eps
+ * (data, [n_cells] float64).  Synchronous. */
+int mg_cfl_dt(mg_mesh* mesh, const double* eps, int flags, void* stream,
+              double* dt_out);
+
+/* Forward traces (App. A leapfrog).
+ *  eps      data, [n_cells] float64, > 0
+ *  shots    host, see mg_shots
+ *  wavelet  data, [nt] float64 samples s(l dt)
+ *  traces   data, [rec_ptr[n_shots]][nt] float32 output
+ *  ckpt_every  checkpoint spacing when MG_KEEP_CHECKPOINTS is set (>0)
+ * All shots advance together in one node-major FP32 state (sources in the
+ * fast dimension); MG_SINGLE_SOURCE runs them one at a time instead. */
+int mg_forward(mg_mesh* mesh, const double* eps, const mg_shots* shots,
+               const double* wavelet, double dt, int nt, float* traces,
+               int ckpt_every, void* stream, int flags);
+
+/* Tangent: jv = J v, the derivative of the traces in the direction
+ * eps_fine = eps + t * v[anc_level(e)] (Eqs. (aku_ankka), (linearized1)-
+ * (linearized2), exact for the lumped scheme).
+ *  level  0..n_levels-1, the mesh level that carries v
+ *  v      data, [cells of level] float64
+ *  jv     data, [rec_ptr[n_shots]][nt] float32 output */
+int mg_jacobian_apply(mg_mesh* mesh, int level, const double* eps,
+                      const mg_shots* shots, const double* wavelet, double dt,
+                      int nt, const double* v, float* jv, void* stream,
+                      int flags);
+
+/* Transpose: g = J^T w, the gradient of sum_{r,l} w[r][l] y[r][l] with
+ * respect to the permittivity of each cell of `level`, by the discrete
+ * adjoint (reverse-time leapfrog) with checkpoints every ckpt_every steps
+ * and recomputation in between.
+ *  w  data, [rec_ptr[n_shots]][nt] float32 trace weights
+ *  g  data, [cells of level] float64 output */
+int mg_jacobian_T_apply(mg_mesh* mesh, int level, const double* eps,
+                        const mg_shots* shots, const double* wavelet, double dt,
+                        int nt, const float* w, double* g, int ckpt_every,
+                        void* stream, int flags);
+
+/* Release the handle's scratch (states, checkpoints, graphs). */
+int mg_mesh_trim(mg_mesh* mesh);
+
+/* Number of kernel launches the handle has issued so far (graph-launched
+ * kernels counted per node).  Used to report launch counts. */
+int64_t mg_launch_count(const mg_mesh* mesh);
+
+const char* mg_strerror(int code);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGWAVE_H */

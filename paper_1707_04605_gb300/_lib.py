@@ -1,0 +1,102 @@
+"""ctypes declarations of the C ABI in include/mgwave.h.
+
+Loading fails loudly (ImportError) when the compiled library is missing:
+there is no CPU fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmgwave.so")
+
+MG_OK = 0
+MG_ERR_ARG = -1
+MG_ERR_NESTING = -2
+MG_ERR_OOM = -3
+MG_ERR_CUDA = -4
+MG_ERR_CFL = -5
+MG_ERR_TIMEOUT = -6
+MG_ERR_UNSUPPORTED = -7
+
+MG_BC = {"abc": 0, "neumann": 1, "dirichlet": 2}
+MG_ORDER = {"rcm": 0, "morton": 1, "none": 2}
+
+MG_HOST_PTRS = 0x01
+MG_SINGLE_SOURCE = 0x02
+MG_NO_GRAPH = 0x04
+MG_PERSISTENT = 0x08
+MG_ALLOW_CFL = 0x10
+MG_KEEP_CHECKPOINTS = 0x20
+MG_REUSE_CHECKPOINTS = 0x40
+
+
+class mg_shots(C.Structure):
+    _fields_ = [("n_shots", C.c_int32), ("src", C.POINTER(C.c_int32)),
+                ("rec_ptr", C.POINTER(C.c_int64)), ("rec", C.POINTER(C.c_int32))]
+
+
+class mg_mesh_info_t(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_levels", C.c_int32), ("n_nodes", C.c_int64),
+                ("n_cells", C.c_int64), ("n_bnd", C.c_int64), ("nnz", C.c_int64),
+                ("ell_entries", C.c_int64), ("slice_height", C.c_int32),
+                ("max_row_nnz", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+# name -> (restype, argtypes); every symbol include/mgwave.h declares
+SIGNATURES = {
+    "mg_mesh_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "mg_mesh_destroy": (None, [C.c_void_p]),
+    "mg_mesh_get_info": (C.c_int, [C.c_void_p, C.POINTER(mg_mesh_info_t)]),
+    "mg_mesh_get_permutation": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mg_cfl_dt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                            C.POINTER(C.c_double)]),
+    "mg_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mg_shots), C.c_void_p,
+                             C.c_double, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "mg_jacobian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(mg_shots),
+                                    C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int]),
+    "mg_jacobian_T_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(mg_shots),
+                                      C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "mg_mesh_trim": (C.c_int, [C.c_void_p]),
+    "mg_launch_count": (C.c_int64, [C.c_void_p]),
+    "mg_strerror": (C.c_char_p, [C.c_int]),
+    "mg_version": (C.c_int, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library and declare every entry point; raises ImportError
+    if the library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"CUDA library not built: {path} is missing "
+            "(run paper_1707_04605_gb300.build.build() first)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = load().mg_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def check(code: int, where: str):
+    if code != MG_OK:
+        raise MgError(code, where)

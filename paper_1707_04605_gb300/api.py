@@ -1,0 +1,235 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Every function mirrors one entry point of include/mgwave.h.  Array
+arguments are either all CUDA tensors (device mode: work is queued on the
+current torch stream, results are CUDA tensors) or all host arrays (host
+mode, MG_HOST_PTRS: the library copies in and out itself and returns host
+arrays).  Nothing here computes any part of the wave path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    import torch
+
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _host(x, dtype):
+    a = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+    return a, C.c_void_p(a.ctypes.data)
+
+
+def _dev(x, dtype_name):
+    import torch
+
+    want = {"float64": torch.float64, "float32": torch.float32}[dtype_name]
+    if x.dtype != want:
+        raise TypeError(f"expected a {dtype_name} CUDA tensor, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError("CUDA tensor arguments must be contiguous")
+    return x, C.c_void_p(x.data_ptr())
+
+
+class Shots:
+    """Host-side shot batch (mg_shots): src [S] int32, rec_ptr [S+1] int64,
+    rec [R] int32 in caller node ids."""
+
+    def __init__(self, src, rec_ptr, rec):
+        self.src = np.ascontiguousarray(src, dtype=np.int32)
+        self.rec_ptr = np.ascontiguousarray(rec_ptr, dtype=np.int64)
+        self.rec = np.ascontiguousarray(rec, dtype=np.int32)
+        self.c = L.mg_shots(
+            len(self.src),
+            self.src.ctypes.data_as(C.POINTER(C.c_int32)),
+            self.rec_ptr.ctypes.data_as(C.POINTER(C.c_int64)),
+            self.rec.ctypes.data_as(C.POINTER(C.c_int32)))
+
+    @property
+    def n_shots(self) -> int:
+        return int(self.src.shape[0])
+
+    @property
+    def n_traces(self) -> int:
+        return int(self.rec_ptr[-1])
+
+    @classmethod
+    def of(cls, shots) -> "Shots":
+        if isinstance(shots, Shots):
+            return shots
+        return cls(shots.src, shots.rec_ptr, shots.rec)
+
+
+class Mesh:
+    """Handle of mg_mesh_create; destroyed with the object or by close()."""
+
+    def __init__(self, handle, dim, n_cells_per_level):
+        self._h = handle
+        self.dim = dim
+        self.n_cells_per_level = [int(x) for x in n_cells_per_level]
+        self._lib = L.load()
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("mesh handle is closed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.mg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = L.mg_mesh_info_t()
+        L.check(self._lib.mg_mesh_get_info(self.handle, C.byref(inf)), "mg_mesh_get_info")
+        return {k: getattr(inf, k) for k, _ in L.mg_mesh_info_t._fields_}
+
+    def permutation(self) -> np.ndarray:
+        n = self.info()["n_nodes"]
+        out = np.empty(n, dtype=np.int32)
+        L.check(self._lib.mg_mesh_get_permutation(self.handle, C.c_void_p(out.ctypes.data)),
+                "mg_mesh_get_permutation")
+        return out
+
+    def trim(self):
+        L.check(self._lib.mg_mesh_trim(self.handle), "mg_mesh_trim")
+
+    def launch_count(self) -> int:
+        return int(self._lib.mg_launch_count(self.handle))
+
+
+def mesh_create(dim, coords, cells, cell_parent, n_cells_per_level, bnd, bc="abc",
+                order="rcm") -> Mesh:
+    lib = L.load()
+    coords, pc = _host(coords, np.float64)
+    cells, pcells = _host(cells, np.int32)
+    bnd, pb = _host(bnd, np.int32)
+    ncl, pncl = _host(n_cells_per_level, np.int64)
+    parents = [np.ascontiguousarray(p, dtype=np.int32) for p in (cell_parent or [])]
+    arr = (C.c_void_p * max(1, len(parents)))(*[p.ctypes.data for p in parents])
+    h = C.c_void_p()
+    rc = lib.mg_mesh_create(int(dim), len(ncl), pc, coords.shape[0], pcells, cells.shape[0],
+                            C.cast(arr, C.c_void_p) if parents else None, pncl, pb,
+                            bnd.shape[0], L.MG_BC[bc], L.MG_ORDER[order], C.byref(h))
+    L.check(rc, "mg_mesh_create")
+    return Mesh(h, dim, ncl)
+
+
+def mesh_from_workload(w, order="rcm", bc=None) -> Mesh:
+    m = w.mesh
+    return mesh_create(m.dim, m.coords, m.cells, m.cell_parent, m.n_cells, m.bnd,
+                       bc or w.bc, order)
+
+
+def cfl_dt(mesh: Mesh, eps, stream=None) -> float:
+    lib = L.load()
+    out = C.c_double()
+    if _is_cuda(eps):
+        eps, pe = _dev(eps, "float64")
+        rc = lib.mg_cfl_dt(mesh.handle, pe, 0, _stream_ptr(stream), C.byref(out))
+    else:
+        eps, pe = _host(eps, np.float64)
+        rc = lib.mg_cfl_dt(mesh.handle, pe, L.MG_HOST_PTRS, None, C.byref(out))
+    L.check(rc, "mg_cfl_dt")
+    return float(out.value)
+
+
+def _prep(eps, wavelet, extra, stream):
+    """Marshal eps (float64), wavelet (float64) and extra arrays."""
+    if _is_cuda(eps):
+        eps, pe = _dev(eps, "float64")
+        wavelet, pw = _dev(wavelet, "float64")
+        ex = [_dev(x, dt) for x, dt in extra]
+        return True, (eps, pe), (wavelet, pw), ex, _stream_ptr(stream), 0
+    eps, pe = _host(eps, np.float64)
+    wavelet, pw = _host(wavelet, np.float64)
+    ex = [_host(x, np.dtype(dt)) for x, dt in extra]
+    return False, (eps, pe), (wavelet, pw), ex, None, L.MG_HOST_PTRS
+
+
+def _alloc(device, shape, dtype_name, like):
+    if device:
+        import torch
+
+        return torch.empty(shape, dtype=getattr(torch, dtype_name), device=like.device)
+    return np.empty(shape, dtype=np.dtype(dtype_name))
+
+
+def _ptr(x):
+    return C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data)
+
+
+def forward(mesh: Mesh, eps, shots, wavelet, dt, nt=None, *, ckpt_every=0,
+            keep_checkpoints=False, single_source=False, allow_cfl=False,
+            stream=None, flags=0):
+    """Traces [n_traces, nt] float32 of mg_forward."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    dev, (eps, pe), (wav, pw), _, st, f0 = _prep(eps, wavelet, [], stream)
+    out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
+    f = f0 | flags
+    if keep_checkpoints:
+        f |= L.MG_KEEP_CHECKPOINTS
+    if single_source:
+        f |= L.MG_SINGLE_SOURCE
+    if allow_cfl:
+        f |= L.MG_ALLOW_CFL
+    rc = lib.mg_forward(mesh.handle, pe, C.byref(sh.c), pw, float(dt), nt, _ptr(out),
+                        int(ckpt_every), st, f)
+    L.check(rc, "mg_forward")
+    return out
+
+
+def jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
+                   allow_cfl=False, stream=None, flags=0):
+    """J v: tangent traces [n_traces, nt] float32 for a level-cell direction v."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, [(v, "float64")], stream)
+    (v, pv), = ex
+    out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
+    f = f0 | flags | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_jacobian_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt), nt,
+                               pv, _ptr(out), st, f)
+    L.check(rc, "mg_jacobian_apply")
+    return out
+
+
+def jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, w, nt=None, *,
+                     ckpt_every=256, reuse_checkpoints=False, allow_cfl=False,
+                     stream=None, flags=0):
+    """J^T w: gradient [cells of level] float64 for trace weights w [n_traces, nt]."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, [(w, "float32")], stream)
+    (w, pwt), = ex
+    out = _alloc(dev, (mesh.n_cells_per_level[level],), "float64", eps)
+    f = f0 | flags | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    if reuse_checkpoints:
+        f |= L.MG_REUSE_CHECKPOINTS
+    rc = lib.mg_jacobian_T_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
+                                 nt, pwt, _ptr(out), int(ckpt_every), st, f)
+    L.check(rc, "mg_jacobian_T_apply")
+    return out

@@ -1,0 +1,699 @@
+// C ABI of the leapfrog wave library: mesh handle, device residency,
+// scratch management and the forward / tangent / adjoint drivers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mgwave.h"
+#include "kernels.cuh"
+#include "mg_internal.h"
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+int ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return MG_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_OOM;
+  }
+  b.bytes = bytes;
+  return MG_OK;
+}
+
+template <class T>
+int upload(Buf& b, const std::vector<T>& v) {
+  int rc = ensure(b, v.size() * sizeof(T));
+  if (rc) return rc;
+  if (!v.empty() && cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+template <class T>
+T* P(Buf& b) { return static_cast<T*>(b.p); }
+
+int round_pad(int S) {
+  if (S <= 4) return 4;
+  if (S <= 128) {
+    int p = 4;
+    while (p < S) p <<= 1;
+    return p;
+  }
+  return (S + 127) / 128 * 128;
+}
+
+// RAII: make the handle's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; cudaGetLastError(); return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) { ok = false; cudaGetLastError(); }
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct mg_mesh {
+  int device = 0;
+  mg::HostMesh hm;
+  // resident mesh arrays
+  Buf ell, slice_off, slice_w, nc_ptr, nc_cell, nc_w, nf_ptr, nf_cell, nf_w,
+      is_bnd, row_abs, cells, vol, cf_ptr, cf_facet, bnd, bnd_meas;
+  std::vector<Buf> anc, lvl_ptr, lvl_idx;  // per level, uploaded on first use
+  // scratch
+  Buf eps_h, wav_h, wavf, coef, tcoef, mass, scal, stA, stB, stC, stD, out_h,
+      w_h, v_h, g_h, ev, G, ckpt, seg, gfine, step_base;
+  // event cache
+  std::vector<int32_t> ev_src, ev_rec;
+  std::vector<int64_t> ev_ptr;
+  int ev_S_pad = 0;
+  int64_t ev_n_src = 0, ev_n_rec = 0;
+  bool ev_valid = false;
+  // checkpoints of the last mg_forward with MG_KEEP_CHECKPOINTS
+  bool ck_valid = false;
+  int ck_every = 0, ck_nt = 0, ck_S_pad = 0, ck_nshots = 0;
+  double ck_dt = 0.0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+const char* kErr[] = {"ok", "invalid argument", "invalid nesting", "out of device memory",
+                      "CUDA error", "dt above the CFL bound", "device wait timed out",
+                      "unsupported combination"};
+
+mg::DevEll dev_ell(mg_mesh* M) {
+  return {P<const int2>(M->ell), P<const int64_t>(M->slice_off), P<const int32_t>(M->slice_w),
+          (int32_t)M->hm.n};
+}
+
+mg::CoefArgs coef_args(mg_mesh* M, const double* eps, double dt) {
+  mg::CoefArgs c;
+  c.n = (int32_t)M->hm.n;
+  c.nc_ptr = P<int64_t>(M->nc_ptr); c.nc_cell = P<int32_t>(M->nc_cell); c.nc_w = P<double>(M->nc_w);
+  c.nf_ptr = P<int64_t>(M->nf_ptr); c.nf_cell = P<int32_t>(M->nf_cell); c.nf_w = P<double>(M->nf_w);
+  c.is_bnd = P<int32_t>(M->is_bnd);
+  c.eps = eps;
+  c.dt = dt;
+  c.bc = M->hm.bc;
+  c.coef = P<float4>(M->coef);
+  c.mass = nullptr;
+  return c;
+}
+
+int validate_shots(mg_mesh* M, const mg_shots* sh) {
+  if (!sh || sh->n_shots < 1 || !sh->src || !sh->rec_ptr) return MG_ERR_ARG;
+  if (sh->rec_ptr[0] != 0) return MG_ERR_ARG;
+  for (int k = 0; k < sh->n_shots; ++k) {
+    if (sh->src[k] < 0 || sh->src[k] >= M->hm.n) return MG_ERR_ARG;
+    if (sh->rec_ptr[k + 1] < sh->rec_ptr[k]) return MG_ERR_ARG;
+  }
+  const int64_t R = sh->rec_ptr[sh->n_shots];
+  if (R > 0 && !sh->rec) return MG_ERR_ARG;
+  if (R > 0x7fffffffLL) return MG_ERR_ARG;
+  for (int64_t r = 0; r < R; ++r)
+    if (sh->rec[r] < 0 || sh->rec[r] >= M->hm.n) return MG_ERR_ARG;
+  return MG_OK;
+}
+
+// Per-row source / receiver lists of a shot batch, uploaded once per batch.
+int build_events(mg_mesh* M, const mg_shots* sh, mg::DevEvents& ev) {
+  const int64_t n = M->hm.n;
+  const int S = sh->n_shots;
+  const int64_t R = sh->rec_ptr[S];
+  std::vector<int32_t> src(sh->src, sh->src + S), rec(sh->rec, sh->rec + R);
+  std::vector<int64_t> ptr(sh->rec_ptr, sh->rec_ptr + S + 1);
+  const bool same = M->ev_valid && src == M->ev_src && rec == M->ev_rec && ptr == M->ev_ptr;
+  const size_t total = 2 * (size_t)(n + 1) + S + 2 * (size_t)R;
+  if (!same) {
+    std::vector<int32_t> h(total, 0);
+    int32_t* src_ptr = h.data();
+    int32_t* src_shot = src_ptr + (n + 1);
+    int32_t* rec_ptr = src_shot + S;
+    int32_t* rec_shot = rec_ptr + (n + 1);
+    int32_t* rec_trace = rec_shot + R;
+    for (int k = 0; k < S; ++k) src_ptr[M->hm.perm[src[k]] + 1]++;
+    for (int64_t r = 0; r < n; ++r) src_ptr[r + 1] += src_ptr[r];
+    {
+      std::vector<int32_t> fill(src_ptr, src_ptr + n);
+      for (int k = 0; k < S; ++k) src_shot[fill[M->hm.perm[src[k]]]++] = k;
+    }
+    for (int64_t r = 0; r < R; ++r) rec_ptr[M->hm.perm[rec[r]] + 1]++;
+    for (int64_t r = 0; r < n; ++r) rec_ptr[r + 1] += rec_ptr[r];
+    {
+      std::vector<int32_t> fill(rec_ptr, rec_ptr + n);
+      for (int k = 0; k < S; ++k)
+        for (int64_t r = ptr[k]; r < ptr[k + 1]; ++r) {
+          const int32_t pos = fill[M->hm.perm[rec[r]]]++;
+          rec_shot[pos] = k;
+          rec_trace[pos] = (int32_t)r;
+        }
+    }
+    int rc = upload(M->ev, h);
+    if (rc) return rc;
+    M->ev_src = src;
+    M->ev_rec = rec;
+    M->ev_ptr = ptr;
+    M->ev_valid = true;
+  }
+  int32_t* base = P<int32_t>(M->ev);
+  ev.src_ptr = base;
+  ev.src_shot = base + (n + 1);
+  ev.rec_ptr = ev.src_shot + S;
+  ev.rec_shot = ev.rec_ptr + (n + 1);
+  ev.rec_trace = ev.rec_shot + R;
+  return MG_OK;
+}
+
+int ensure_level(mg_mesh* M, int level) {
+  if (M->anc[level].p) return MG_OK;
+  int rc = upload(M->anc[level], M->hm.ancestors[level]);
+  if (rc) return rc;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> idx;
+  mg::level_children(M->hm, level, ptr, idx);
+  rc = upload(M->lvl_ptr[level], ptr);
+  if (rc) return rc;
+  return upload(M->lvl_idx[level], idx);
+}
+
+// Inputs: device pointers, staged from the host when MG_HOST_PTRS is set.
+int stage_in(Buf& b, const void* src, size_t bytes, int flags, cudaStream_t st,
+             const void** dev) {
+  if (!(flags & MG_HOST_PTRS)) { *dev = src; return MG_OK; }
+  int rc = ensure(b, bytes);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return MG_ERR_CUDA;
+  *dev = b.p;
+  return MG_OK;
+}
+
+int finish_out(Buf& b, void* dst, size_t bytes, int flags, cudaStream_t st) {
+  if (!(flags & MG_HOST_PTRS)) return MG_OK;
+  if (cudaMemcpyAsync(dst, b.p, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MG_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+#define MG_TRY(x) do { int _rc = (x); if (_rc != MG_OK) return _rc; } while (0)
+#define MG_CU(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); return MG_ERR_CUDA; } } while (0)
+
+int cfl_lambda(mg_mesh* M, const double* eps_d, cudaStream_t st, double* lam) {
+  MG_TRY(ensure(M->mass, M->hm.n * sizeof(double)));
+  MG_TRY(ensure(M->coef, M->hm.n * sizeof(float4)));
+  MG_TRY(ensure(M->scal, 8 * sizeof(double)));
+  mg::CoefArgs c = coef_args(M, eps_d, 1.0);
+  c.mass = P<double>(M->mass);
+  MG_TRY(mg::launch_coefs(c, st));
+  MG_TRY(mg::launch_cfl_reduce((int32_t)M->hm.n, P<double>(M->row_abs), P<double>(M->mass),
+                               P<double>(M->scal), st));
+  M->launches += 2;
+  MG_CU(cudaMemcpyAsync(lam, M->scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MG_CU(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+// Common preparation of a propagation call: inputs on the device, per-row
+// coefficients, wavelet in FP32, event lists, dt check.
+struct Prep {
+  const double* eps = nullptr;
+  const double* wav = nullptr;
+  mg::DevEvents ev{};
+  int S = 0, S_pad = 0, tiles = 1;
+  int64_t R = 0;
+};
+
+int prepare(mg_mesh* M, const double* eps, const mg_shots* shots, const double* wavelet,
+            double dt, int nt, int flags, cudaStream_t st, Prep& pp) {
+  if (!eps || !wavelet || nt < 1 || !(dt > 0.0) || !std::isfinite(dt)) return MG_ERR_ARG;
+  MG_TRY(validate_shots(M, shots));
+  pp.S = shots->n_shots;
+  pp.S_pad = round_pad(pp.S);
+  pp.tiles = pp.S_pad >= 128 ? pp.S_pad / 128 : 1;
+  pp.R = shots->rec_ptr[pp.S];
+  const void* d;
+  MG_TRY(stage_in(M->eps_h, eps, M->hm.m * sizeof(double), flags, st, &d));
+  pp.eps = static_cast<const double*>(d);
+  MG_TRY(stage_in(M->wav_h, wavelet, nt * sizeof(double), flags, st, &d));
+  pp.wav = static_cast<const double*>(d);
+  if (!(flags & MG_ALLOW_CFL)) {
+    double lam = 0.0;
+    MG_TRY(cfl_lambda(M, pp.eps, st, &lam));
+    if (!(lam > 0.0) || dt > 2.0 / std::sqrt(lam) * (1.0 + 1e-12)) return MG_ERR_CFL;
+  }
+  MG_TRY(ensure(M->coef, M->hm.n * sizeof(float4)));
+  MG_TRY(mg::launch_coefs(coef_args(M, pp.eps, dt), st));
+  MG_TRY(ensure(M->wavf, nt * sizeof(float)));
+  MG_TRY(mg::launch_d2f(pp.wav, P<float>(M->wavf), nt, st));
+  M->launches += 2;
+  MG_TRY(build_events(M, shots, pp.ev));
+  return MG_OK;
+}
+
+mg::StepArgs step_args(mg_mesh* M, const Prep& pp, int ld, int nt) {
+  mg::StepArgs a{};
+  a.K = dev_ell(M);
+  a.ev = pp.ev;
+  a.coef = P<const float4>(M->coef);
+  a.ld = ld;
+  a.wavelet = P<const float>(M->wavf);
+  a.nt = nt;
+  a.step_base = nullptr;
+  return a;
+}
+
+// Batched forward loop over steps [0, nt); optional traces and checkpoints.
+int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_every,
+                float* ckpt, cudaStream_t st) {
+  const int64_t n = M->hm.n;
+  const size_t state = (size_t)n * pp.S_pad;
+  MG_TRY(ensure(M->stA, state * sizeof(float)));
+  MG_TRY(ensure(M->stB, state * sizeof(float)));
+  float* p = P<float>(M->stA);
+  float* pm = P<float>(M->stB);
+  MG_CU(cudaMemsetAsync(p, 0, state * sizeof(float), st));
+  MG_CU(cudaMemsetAsync(pm, 0, state * sizeof(float), st));
+  mg::StepArgs a = step_args(M, pp, pp.S_pad, nt);
+  a.traces = traces;
+  for (int l = 0; l < nt; ++l) {
+    if (ckpt && l % ckpt_every == 0) {
+      float* slot = ckpt + (size_t)(l / ckpt_every) * 2 * state;
+      MG_TRY(mg::launch_copy_f4(p, slot, (int64_t)state, st));
+      MG_TRY(mg::launch_copy_f4(pm, slot + state, (int64_t)state, st));
+      M->launches += 2;
+    }
+    a.p = p;
+    a.pm = pm;
+    a.pout = pm;
+    a.step = l;
+    MG_TRY(mg::launch_step(a, pp.S_pad, st));
+    M->launches += 1;
+    std::swap(p, pm);
+  }
+  return MG_OK;
+}
+
+int run_forward_single(mg_mesh* M, const Prep& pp, int nt, float* traces, cudaStream_t st) {
+  const int64_t n = M->hm.n;
+  MG_TRY(ensure(M->stA, n * sizeof(float)));
+  MG_TRY(ensure(M->stB, n * sizeof(float)));
+  mg::StepArgs a = step_args(M, pp, 1, nt);
+  a.traces = traces;
+  for (int s = 0; s < pp.S; ++s) {
+    float* p = P<float>(M->stA);
+    float* pm = P<float>(M->stB);
+    MG_CU(cudaMemsetAsync(p, 0, n * sizeof(float), st));
+    MG_CU(cudaMemsetAsync(pm, 0, n * sizeof(float), st));
+    for (int l = 0; l < nt; ++l) {
+      a.p = p;
+      a.pm = pm;
+      a.pout = pm;
+      a.step = l;
+      MG_TRY(mg::launch_step_single(a, s, st));
+      M->launches += 1;
+      std::swap(p, pm);
+    }
+  }
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mg_strerror(int code) {
+  if (code > 0 || code < -7) return "unknown error";
+  return kErr[-code];
+}
+
+int mg_version(void) { return 100; }
+
+int mg_mesh_create(int dim, int n_levels, const double* coords, int64_t n_nodes,
+                   const int32_t* cells, int64_t n_cells,
+                   const int32_t* const* cell_parent,
+                   const int64_t* n_cells_per_level, const int32_t* bnd,
+                   int64_t n_bnd, int bc_mode, int order, mg_mesh** out) {
+  if (!out) return MG_ERR_ARG;
+  *out = nullptr;
+  mg_mesh* M = new mg_mesh();
+  std::string msg;
+  int rc = mg::build_host_mesh(dim, n_levels, coords, n_nodes, cells, n_cells, cell_parent,
+                               n_cells_per_level, bnd, n_bnd, bc_mode, order, M->hm, msg);
+  if (rc != MG_OK) {
+    delete M;
+    return rc;
+  }
+  if (cudaGetDevice(&M->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete M;
+    return MG_ERR_CUDA;
+  }
+  mg::HostMesh& h = M->hm;
+  // cell -> owned boundary facets
+  std::vector<int64_t> cf_ptr(h.m + 1, 0);
+  for (int64_t f = 0; f < h.nb; ++f) cf_ptr[h.bnd_owner[f] + 1]++;
+  for (int64_t c = 0; c < h.m; ++c) cf_ptr[c + 1] += cf_ptr[c];
+  std::vector<int32_t> cf_facet(h.nb);
+  {
+    std::vector<int64_t> fill(cf_ptr.begin(), cf_ptr.end() - 1);
+    for (int64_t f = 0; f < h.nb; ++f) cf_facet[fill[h.bnd_owner[f]]++] = (int32_t)f;
+  }
+  std::vector<int32_t> ell_raw(2 * h.ell.size());
+  std::memcpy(ell_raw.data(), h.ell.data(), h.ell.size() * sizeof(mg::EllEntry));
+  rc = MG_OK;
+  if (!rc) rc = upload(M->ell, ell_raw);
+  if (!rc) rc = upload(M->slice_off, h.slice_off);
+  if (!rc) rc = upload(M->slice_w, h.slice_w);
+  if (!rc) rc = upload(M->nc_ptr, h.nc_ptr);
+  if (!rc) rc = upload(M->nc_cell, h.nc_cell);
+  if (!rc) rc = upload(M->nc_w, h.nc_w);
+  if (!rc) rc = upload(M->nf_ptr, h.nf_ptr);
+  if (!rc) rc = upload(M->nf_cell, h.nf_cell);
+  if (!rc) rc = upload(M->nf_w, h.nf_w);
+  if (!rc) rc = upload(M->is_bnd, h.is_bnd_row);
+  if (!rc) rc = upload(M->row_abs, h.row_abs);
+  if (!rc) rc = upload(M->cells, h.cells);
+  if (!rc) rc = upload(M->vol, h.cell_vol);
+  if (!rc) rc = upload(M->cf_ptr, cf_ptr);
+  if (!rc) rc = upload(M->cf_facet, cf_facet);
+  if (!rc) rc = upload(M->bnd, h.bnd);
+  if (!rc) rc = upload(M->bnd_meas, h.bnd_meas);
+  M->anc.resize(h.n_levels);
+  M->lvl_ptr.resize(h.n_levels);
+  M->lvl_idx.resize(h.n_levels);
+  if (rc != MG_OK) {
+    mg_mesh_destroy(M);
+    return rc;
+  }
+  // free host copies not needed after upload
+  std::vector<mg::EllEntry>().swap(h.ell);
+  std::vector<int32_t>().swap(h.col);
+  std::vector<double>().swap(h.val);
+  *out = M;
+  return MG_OK;
+}
+
+void mg_mesh_destroy(mg_mesh* M) {
+  if (!M) return;
+  DeviceGuard g(M->device);
+  Buf* all[] = {&M->ell, &M->slice_off, &M->slice_w, &M->nc_ptr, &M->nc_cell, &M->nc_w,
+                &M->nf_ptr, &M->nf_cell, &M->nf_w, &M->is_bnd, &M->row_abs, &M->cells,
+                &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas};
+  for (Buf* b : all)
+    if (b->p) cudaFree(b->p);
+  for (auto* v : {&M->anc, &M->lvl_ptr, &M->lvl_idx})
+    for (Buf& b : *v)
+      if (b.p) cudaFree(b.p);
+  mg_mesh_trim(M);
+  delete M;
+}
+
+int mg_mesh_trim(mg_mesh* M) {
+  if (!M) return MG_ERR_ARG;
+  DeviceGuard g(M->device);
+  Buf* all[] = {&M->eps_h, &M->wav_h, &M->wavf, &M->coef, &M->tcoef, &M->mass, &M->scal,
+                &M->stA, &M->stB, &M->stC, &M->stD, &M->out_h, &M->w_h, &M->v_h, &M->g_h,
+                &M->ev, &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base};
+  for (Buf* b : all) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+  M->ev_valid = false;
+  M->ck_valid = false;
+  return MG_OK;
+}
+
+int mg_mesh_get_info(const mg_mesh* M, mg_mesh_info_t* info) {
+  if (!M || !info) return MG_ERR_ARG;
+  const mg::HostMesh& h = M->hm;
+  info->dim = h.dim;
+  info->n_levels = h.n_levels;
+  info->n_nodes = h.n;
+  info->n_cells = h.m;
+  info->n_bnd = h.nb;
+  info->nnz = h.rowptr.empty() ? 0 : h.rowptr.back();
+  info->ell_entries = h.slice_off.empty() ? 0 : h.slice_off.back();
+  info->slice_height = mg::kSliceH;
+  info->max_row_nnz = h.max_row_nnz;
+  int64_t bytes = 0;
+  const Buf* all[] = {&M->ell, &M->slice_off, &M->slice_w, &M->nc_ptr, &M->nc_cell, &M->nc_w,
+                      &M->nf_ptr, &M->nf_cell, &M->nf_w, &M->is_bnd, &M->row_abs, &M->cells,
+                      &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas, &M->eps_h,
+                      &M->wav_h, &M->wavf, &M->coef, &M->tcoef, &M->mass, &M->scal, &M->stA,
+                      &M->stB, &M->stC, &M->stD, &M->out_h, &M->w_h, &M->v_h, &M->g_h, &M->ev,
+                      &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base};
+  for (const Buf* b : all) bytes += (int64_t)b->bytes;
+  info->device_bytes = bytes;
+  return MG_OK;
+}
+
+int mg_mesh_get_permutation(const mg_mesh* M, int32_t* perm) {
+  if (!M || !perm) return MG_ERR_ARG;
+  std::copy(M->hm.perm.begin(), M->hm.perm.end(), perm);
+  return MG_OK;
+}
+
+int64_t mg_launch_count(const mg_mesh* M) { return M ? M->launches : 0; }
+
+int mg_cfl_dt(mg_mesh* M, const double* eps, int flags, void* stream, double* dt_out) {
+  if (!M || !eps || !dt_out) return MG_ERR_ARG;
+  DeviceGuard g(M->device);
+  if (!g.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void* d;
+  MG_TRY(stage_in(M->eps_h, eps, M->hm.m * sizeof(double), flags, st, &d));
+  double lam = 0.0;
+  MG_TRY(cfl_lambda(M, static_cast<const double*>(d), st, &lam));
+  if (!(lam > 0.0) || !std::isfinite(lam)) return MG_ERR_ARG;
+  *dt_out = 2.0 / std::sqrt(lam);
+  return MG_OK;
+}
+
+int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const double* wavelet,
+               double dt, int nt, float* traces, int ckpt_every, void* stream, int flags) {
+  if (!M || !traces) return MG_ERR_ARG;
+  if ((flags & MG_KEEP_CHECKPOINTS) && (ckpt_every < 1 || (flags & MG_SINGLE_SOURCE)))
+    return MG_ERR_ARG;
+  DeviceGuard g(M->device);
+  if (!g.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Prep pp;
+  MG_TRY(prepare(M, eps, shots, wavelet, dt, nt, flags, st, pp));
+  const size_t tbytes = (size_t)pp.R * nt * sizeof(float);
+  float* tr = traces;
+  if (flags & MG_HOST_PTRS) {
+    MG_TRY(ensure(M->out_h, tbytes));
+    tr = P<float>(M->out_h);
+  }
+  if (flags & MG_SINGLE_SOURCE) {
+    MG_TRY(run_forward_single(M, pp, nt, tr, st));
+  } else {
+    float* ck = nullptr;
+    M->ck_valid = false;
+    if (flags & MG_KEEP_CHECKPOINTS) {
+      const int nck = (nt + ckpt_every - 1) / ckpt_every;
+      MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * M->hm.n * pp.S_pad * sizeof(float)));
+      ck = P<float>(M->ckpt);
+    }
+    MG_TRY(run_forward(M, pp, nt, tr, ckpt_every, ck, st));
+    if (ck) {
+      M->ck_valid = true;
+      M->ck_every = ckpt_every;
+      M->ck_nt = nt;
+      M->ck_S_pad = pp.S_pad;
+      M->ck_nshots = pp.S;
+      M->ck_dt = dt;
+    }
+  }
+  return finish_out(M->out_h, traces, tbytes, flags, st);
+}
+
+int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* shots,
+                      const double* wavelet, double dt, int nt, const double* v, float* jv,
+                      void* stream, int flags) {
+  if (!M || !v || !jv) return MG_ERR_ARG;
+  if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
+  if (flags & MG_SINGLE_SOURCE) return MG_ERR_UNSUPPORTED;
+  DeviceGuard g(M->device);
+  if (!g.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Prep pp;
+  MG_TRY(prepare(M, eps, shots, wavelet, dt, nt, flags, st, pp));
+  MG_TRY(ensure_level(M, level));
+  const void* d;
+  MG_TRY(stage_in(M->v_h, v, M->hm.n_cells_level[level] * sizeof(double), flags, st, &d));
+  MG_TRY(ensure(M->tcoef, M->hm.n * sizeof(float2)));
+  mg::TangentCoefArgs tca;
+  tca.c = coef_args(M, pp.eps, dt);
+  tca.v = static_cast<const double*>(d);
+  tca.anc = P<int32_t>(M->anc[level]);
+  tca.tcoef = P<float2>(M->tcoef);
+  MG_TRY(mg::launch_tangent_coefs(tca, st));
+  M->launches += 1;
+  const size_t tbytes = (size_t)pp.R * nt * sizeof(float);
+  float* tr = jv;
+  if (flags & MG_HOST_PTRS) {
+    MG_TRY(ensure(M->out_h, tbytes));
+    tr = P<float>(M->out_h);
+  }
+  const int64_t n = M->hm.n;
+  const size_t state = (size_t)n * pp.S_pad;
+  Buf* bufs[] = {&M->stA, &M->stB, &M->stC, &M->stD};
+  for (Buf* b : bufs) {
+    MG_TRY(ensure(*b, state * sizeof(float)));
+    MG_CU(cudaMemsetAsync(b->p, 0, state * sizeof(float), st));
+  }
+  float *p = P<float>(M->stA), *pm = P<float>(M->stB), *q = P<float>(M->stC),
+        *qm = P<float>(M->stD);
+  mg::TangentArgs a{};
+  a.f = step_args(M, pp, pp.S_pad, nt);
+  a.tcoef = P<const float2>(M->tcoef);
+  a.dtraces = tr;
+  for (int l = 0; l < nt; ++l) {
+    a.f.p = p;
+    a.f.pm = pm;
+    a.f.pout = pm;
+    a.q = q;
+    a.qm = qm;
+    a.f.step = l;
+    MG_TRY(mg::launch_tangent(a, pp.S_pad, st));
+    M->launches += 1;
+    std::swap(p, pm);
+    std::swap(q, qm);
+  }
+  return finish_out(M->out_h, jv, tbytes, flags, st);
+}
+
+int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots* shots,
+                        const double* wavelet, double dt, int nt, const float* w, double* g,
+                        int ckpt_every, void* stream, int flags) {
+  if (!M || !w || !g || ckpt_every < 1) return MG_ERR_ARG;
+  if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
+  if (flags & MG_SINGLE_SOURCE) return MG_ERR_UNSUPPORTED;
+  DeviceGuard guard(M->device);
+  if (!guard.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Prep pp;
+  MG_TRY(prepare(M, eps, shots, wavelet, dt, nt, flags, st, pp));
+  MG_TRY(ensure_level(M, level));
+  const int64_t n = M->hm.n;
+  const size_t state = (size_t)n * pp.S_pad;
+  const void* d;
+  MG_TRY(stage_in(M->w_h, w, (size_t)pp.R * nt * sizeof(float), flags, st, &d));
+  const float* wd = static_cast<const float*>(d);
+  // checkpoints
+  const bool reuse = (flags & MG_REUSE_CHECKPOINTS) && M->ck_valid && M->ck_every == ckpt_every &&
+                     M->ck_nt == nt && M->ck_S_pad == pp.S_pad && M->ck_nshots == pp.S &&
+                     M->ck_dt == dt;
+  if ((flags & MG_REUSE_CHECKPOINTS) && !reuse) return MG_ERR_ARG;
+  const int nck = (nt + ckpt_every - 1) / ckpt_every;
+  if (!reuse) {
+    MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * state * sizeof(float)));
+    MG_TRY(run_forward(M, pp, nt, nullptr, ckpt_every, P<float>(M->ckpt), st));
+  }
+  float* ck = P<float>(M->ckpt);
+  // segment buffer: slots for p_{l0-1} .. p_{l0+K}
+  MG_TRY(ensure(M->seg, (size_t)(ckpt_every + 2) * state * sizeof(float)));
+  float* seg = P<float>(M->seg);
+  // adjoint states and accumulators
+  MG_TRY(ensure(M->stC, state * sizeof(float)));
+  MG_TRY(ensure(M->stD, state * sizeof(float)));
+  float* mu = P<float>(M->stC);
+  float* mu1 = P<float>(M->stD);
+  MG_CU(cudaMemsetAsync(mu, 0, state * sizeof(float), st));
+  MG_CU(cudaMemsetAsync(mu1, 0, state * sizeof(float), st));
+  const size_t acc = (size_t)pp.tiles * n;
+  MG_TRY(ensure(M->G, 4 * acc * sizeof(float)));
+  MG_CU(cudaMemsetAsync(M->G.p, 0, 4 * acc * sizeof(float), st));
+  float* G = P<float>(M->G);
+  mg::StepArgs fa = step_args(M, pp, pp.S_pad, nt);
+  fa.traces = nullptr;
+  mg::AdjointArgs aa{};
+  aa.K = dev_ell(M);
+  aa.ev = pp.ev;
+  aa.coef = P<const float4>(M->coef);
+  aa.ld = pp.S_pad;
+  aa.w = wd;
+  aa.nt = nt;
+  aa.G = G;
+  aa.Gc = G + acc;
+  aa.H = G + 2 * acc;
+  aa.Hc = G + 3 * acc;
+  for (int a = nck - 1; a >= 0; --a) {
+    const int l0 = a * ckpt_every;
+    const int l1 = std::min(nt, l0 + ckpt_every);
+    // slot j holds p_{l0-1+j}
+    MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state, seg + state, (int64_t)state, st));
+    MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state + state, seg, (int64_t)state, st));
+    M->launches += 2;
+    for (int l = l0; l < l1; ++l) {
+      const int j = l - l0 + 1;  // slot of p_l
+      fa.p = seg + (size_t)j * state;
+      fa.pm = seg + (size_t)(j - 1) * state;
+      fa.pout = seg + (size_t)(j + 1) * state;
+      fa.step = l;
+      MG_TRY(mg::launch_step(fa, pp.S_pad, st));
+      M->launches += 1;
+    }
+    for (int k = l1; k > l0; --k) {
+      aa.mu = mu;
+      aa.mu1 = mu1;
+      aa.pk = seg + (size_t)(k - l0 + 1) * state;
+      aa.k = k;
+      MG_TRY(mg::launch_adjoint(aa, pp.S_pad, st));
+      M->launches += 1;
+      std::swap(mu, mu1);
+    }
+  }
+  // per-cell gradient (FP64), then restriction to the level
+  MG_TRY(ensure(M->gfine, M->hm.m * sizeof(double)));
+  mg::GradArgs ga;
+  ga.m = M->hm.m;
+  ga.k = M->hm.dim + 1;
+  ga.dim = M->hm.dim;
+  ga.cells = P<int32_t>(M->cells);
+  ga.vol = P<double>(M->vol);
+  ga.cf_ptr = P<int64_t>(M->cf_ptr);
+  ga.cf_facet = P<int32_t>(M->cf_facet);
+  ga.bnd = P<int32_t>(M->bnd);
+  ga.bnd_meas = P<double>(M->bnd_meas);
+  ga.eps = pp.eps;
+  ga.dt = dt;
+  ga.bc = M->hm.bc;
+  ga.n = (int32_t)n;
+  ga.tiles = pp.tiles;
+  ga.G = aa.G; ga.Gc = aa.Gc; ga.H = aa.H; ga.Hc = aa.Hc;
+  ga.g_fine = P<double>(M->gfine);
+  MG_TRY(mg::launch_cell_gradient(ga, st));
+  const int64_t nc = M->hm.n_cells_level[level];
+  double* gout = g;
+  if (flags & MG_HOST_PTRS) {
+    MG_TRY(ensure(M->g_h, nc * sizeof(double)));
+    gout = P<double>(M->g_h);
+  }
+  MG_TRY(mg::launch_restrict(nc, P<int64_t>(M->lvl_ptr[level]), P<int32_t>(M->lvl_idx[level]),
+                             ga.g_fine, gout, st));
+  M->launches += 2;
+  return finish_out(M->g_h, g, nc * sizeof(double), flags, st);
+}
+
+}  // extern "C"

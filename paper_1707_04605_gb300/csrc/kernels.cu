@@ -1,0 +1,470 @@
+// CUDA kernels of the leapfrog wave path (sm_103a).
+//
+// State layout: node-major, [row][ld] FP32 with the shots of a batch in the
+// fast dimension (ld = padded shot count, a multiple of 4).  A lane owns 4
+// consecutive shots (one float4); LPR lanes cover the <=128 shots of a
+// source tile of one row, so a warp advances 32/LPR rows.  Neighbour rows
+// p[col][tile] are therefore gathered as coalesced 16-byte-per-lane loads,
+// and the stiffness entry (col, K) of a row is a warp-uniform (LPR = 32) or
+// contiguous (LPR < 32, consecutive rows of one ELL slice) 8-byte load that
+// is shared by every shot of the tile.  No tensor cores: the step is a
+// sparse product, bound by memory traffic, not a dense contraction.
+#include <cuda_runtime.h>
+
+#include "../../include/mgwave.h"
+#include "kernels.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+namespace {
+
+constexpr int kWarps = 8;            // warps per block of the batched kernels
+constexpr int kThreads = 32 * kWarps;
+constexpr int kTile = 128;           // shots per source tile
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ld4v(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ void st4(float* p, float4 v) {
+  *reinterpret_cast<float4*>(p) = v;
+}
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z),
+                     fmaf(a, x.w, y.w));
+}
+// Component d (0..3) of a float4 without dynamic register indexing.
+__device__ __forceinline__ void add_comp(float4& v, int d, float x) {
+  v.x += d == 0 ? x : 0.0f;
+  v.y += d == 1 ? x : 0.0f;
+  v.z += d == 2 ? x : 0.0f;
+  v.w += d == 3 ? x : 0.0f;
+}
+__device__ __forceinline__ float get_comp(const float4& v, int d) {
+  return d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w;
+}
+
+// acc = sum_k K_{row,k} p[k][src0..src0+3]; self = p[row][src0..].
+__device__ __forceinline__ float4 stiff_gather(const DevEll& K, int row,
+                                               const float* __restrict__ p,
+                                               int ld, int src0, float4& self) {
+  const int slice = row / kSliceH;
+  const int rl = row - slice * kSliceH;
+  const int2* __restrict__ e = K.ell + K.slice_off[slice] + rl;
+  const int w = K.slice_w[slice];
+  const int2 e0 = __ldg(e);                        // diagonal entry first
+  self = ld4(p + (size_t)row * ld + src0);
+  float4 acc;
+  const float v0 = __int_as_float(e0.y);
+  acc.x = v0 * self.x; acc.y = v0 * self.y; acc.z = v0 * self.z; acc.w = v0 * self.w;
+#pragma unroll 4
+  for (int k = 1; k < w; ++k) {
+    const int2 ek = __ldg(e + k * kSliceH);
+    const float4 x = ld4(p + (size_t)ek.x * ld + src0);
+    acc = fma4(__int_as_float(ek.y), x, acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float4 stiff_gather2(const DevEll& K, int row,
+                                                const float* __restrict__ p,
+                                                const float* __restrict__ q,
+                                                int ld, int src0, float4& ps,
+                                                float4& qs, float4& qacc) {
+  const int slice = row / kSliceH;
+  const int rl = row - slice * kSliceH;
+  const int2* __restrict__ e = K.ell + K.slice_off[slice] + rl;
+  const int w = K.slice_w[slice];
+  const int2 e0 = __ldg(e);
+  ps = ld4(p + (size_t)row * ld + src0);
+  qs = ld4(q + (size_t)row * ld + src0);
+  const float v0 = __int_as_float(e0.y);
+  float4 acc = make_float4(v0 * ps.x, v0 * ps.y, v0 * ps.z, v0 * ps.w);
+  qacc = make_float4(v0 * qs.x, v0 * qs.y, v0 * qs.z, v0 * qs.w);
+#pragma unroll 4
+  for (int k = 1; k < w; ++k) {
+    const int2 ek = __ldg(e + k * kSliceH);
+    const float v = __int_as_float(ek.y);
+    acc = fma4(v, ld4(p + (size_t)ek.x * ld + src0), acc);
+    qacc = fma4(v, ld4(q + (size_t)ek.x * ld + src0), qacc);
+  }
+  return acc;
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kThreads) k_step(StepArgs a) {
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
+  if (row >= a.K.n) return;
+  const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
+  float4 self;
+  const float4 acc = stiff_gather(a.K, row, a.p, a.ld, src0, self);
+  const float4 c = __ldg(a.coef + row);
+  const float4 old = ld4v(a.pm + (size_t)row * a.ld + src0);
+  float4 out;
+  out.x = c.x * self.x - c.y * old.x - c.z * acc.x;
+  out.y = c.x * self.y - c.y * old.y - c.z * acc.y;
+  out.z = c.x * self.z - c.y * old.z - c.z * acc.z;
+  out.w = c.x * self.w - c.y * old.w - c.z * acc.w;
+  const int l = a.step + (a.step_base ? *a.step_base : 0);
+  const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
+  if (s0 != s1) {
+    const float sv = c.z * __ldg(a.wavelet + l);
+    for (int q = s0; q < s1; ++q) {
+      const int d = __ldg(a.ev.src_shot + q) - src0;
+      if (d >= 0 && d < 4) add_comp(out, d, sv);
+    }
+  }
+  st4(a.pout + (size_t)row * a.ld + src0, out);
+  if (a.traces) {
+    const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
+    for (int q = r0; q < r1; ++q) {
+      const int d = __ldg(a.ev.rec_shot + q) - src0;
+      if (d >= 0 && d < 4)
+        a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = get_comp(out, d);
+    }
+  }
+}
+
+// Plain single-shot step (the one-source comparator): one thread per row,
+// scalar state, sliced-ELL entries read coalesced across the warp (a warp is
+// one slice).
+__global__ void __launch_bounds__(256) k_step_single(StepArgs a, int shot) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= a.K.n) return;
+  const int slice = row / kSliceH;
+  const int rl = row - slice * kSliceH;
+  const int2* __restrict__ e = a.K.ell + a.K.slice_off[slice] + rl;
+  const int w = a.K.slice_w[slice];
+  const float self = __ldg(a.p + row);
+  float acc = __int_as_float(__ldg(e).y) * self;
+  for (int k = 1; k < w; ++k) {
+    const int2 ek = __ldg(e + k * kSliceH);
+    acc = fmaf(__int_as_float(ek.y), __ldg(a.p + ek.x), acc);
+  }
+  const float4 c = __ldg(a.coef + row);
+  float out = c.x * self - c.y * a.pm[row] - c.z * acc;
+  const int l = a.step + (a.step_base ? *a.step_base : 0);
+  const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
+  for (int q = s0; q < s1; ++q)
+    if (__ldg(a.ev.src_shot + q) == shot) out += c.z * __ldg(a.wavelet + l);
+  a.pout[row] = out;
+  if (a.traces) {
+    const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
+    for (int q = r0; q < r1; ++q)
+      if (__ldg(a.ev.rec_shot + q) == shot)
+        a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = out;
+  }
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kThreads) k_tangent(TangentArgs a) {
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
+  if (row >= a.f.K.n) return;
+  const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
+  const int ld = a.f.ld;
+  float4 ps, qs, qacc;
+  const float4 acc = stiff_gather2(a.f.K, row, a.f.p, a.q, ld, src0, ps, qs, qacc);
+  const float4 c = __ldg(a.f.coef + row);
+  const float2 tc = __ldg(a.tcoef + row);
+  float* qmr = a.qm + (size_t)row * ld + src0;
+  const float4 pold = ld4v(a.f.pm + (size_t)row * ld + src0), qold = ld4v(qmr);
+  float4 pn, qn;
+  pn.x = c.x * ps.x - c.y * pold.x - c.z * acc.x;
+  pn.y = c.x * ps.y - c.y * pold.y - c.z * acc.y;
+  pn.z = c.x * ps.z - c.y * pold.z - c.z * acc.z;
+  pn.w = c.x * ps.w - c.y * pold.w - c.z * acc.w;
+  const int l = a.f.step + (a.f.step_base ? *a.f.step_base : 0);
+  const int s0 = __ldg(a.f.ev.src_ptr + row), s1 = __ldg(a.f.ev.src_ptr + row + 1);
+  if (s0 != s1) {
+    const float sv = c.z * __ldg(a.f.wavelet + l);
+    for (int q = s0; q < s1; ++q) {
+      const int d = __ldg(a.f.ev.src_shot + q) - src0;
+      if (d >= 0 && d < 4) add_comp(pn, d, sv);
+    }
+  }
+  // dp+ = alpha dp - beta dp- - gamma K dp - cm (p+ - 2p + p-) - cd (p+ - p-)
+#define MG_TAN(X)                                                              \
+  qn.X = c.x * qs.X - c.y * qold.X - c.z * qacc.X -                            \
+         tc.x * (pn.X - 2.0f * ps.X + pold.X) - tc.y * (pn.X - pold.X);
+  MG_TAN(x) MG_TAN(y) MG_TAN(z) MG_TAN(w)
+#undef MG_TAN
+  st4(a.f.pout + (size_t)row * ld + src0, pn);
+  st4(qmr, qn);
+  const int r0 = __ldg(a.f.ev.rec_ptr + row), r1 = __ldg(a.f.ev.rec_ptr + row + 1);
+  for (int q = r0; q < r1; ++q) {
+    const int d = __ldg(a.f.ev.rec_shot + q) - src0;
+    if (d >= 0 && d < 4)
+      a.dtraces[(size_t)__ldg(a.f.ev.rec_trace + q) * a.f.nt + l] = get_comp(qn, d);
+  }
+}
+
+__device__ __forceinline__ void kahan_add(float* s, float* c, float term) {
+  const float y = term - *c;
+  const float t = *s + y;
+  *c = (t - *s) - y;
+  *s = t;
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kThreads) k_adjoint(AdjointArgs a) {
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
+  const bool valid = row < a.K.n;
+  const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
+  float t1 = 0.0f, t2 = 0.0f;
+  if (valid) {
+    float4 self;
+    const float4 acc = stiff_gather(a.K, row, a.mu, a.ld, src0, self);
+    const float4 c = __ldg(a.coef + row);
+    float* m1 = a.mu1 + (size_t)row * a.ld + src0;
+    const float4 old = ld4v(m1);  // mu_{k+1}
+    float4 out;
+    out.x = c.x * self.x - c.y * old.x - c.z * acc.x;
+    out.y = c.x * self.y - c.y * old.y - c.z * acc.y;
+    out.z = c.x * self.z - c.y * old.z - c.z * acc.z;
+    out.w = c.x * self.w - c.y * old.w - c.z * acc.w;
+    const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
+    for (int q = r0; q < r1; ++q) {
+      const int d = __ldg(a.ev.rec_shot + q) - src0;
+      if (d >= 0 && d < 4)
+        add_comp(out, d, c.w * __ldg(a.w + (size_t)__ldg(a.ev.rec_trace + q) * a.nt + (a.k - 1)));
+    }
+    st4(m1, out);
+    const float4 pk = ld4(a.pk + (size_t)row * a.ld + src0);
+#define MG_ACC(X)                                                              \
+  t1 = fmaf(pk.X, (out.X - 2.0f * self.X) + old.X, t1);                        \
+  t2 = fmaf(pk.X, out.X - old.X, t2);
+    MG_ACC(x) MG_ACC(y) MG_ACC(z) MG_ACC(w)
+#undef MG_ACC
+  }
+#pragma unroll
+  for (int off = LPR / 2; off > 0; off >>= 1) {
+    t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+  }
+  if (valid && (lane % LPR) == 0) {
+    const size_t gi = (size_t)blockIdx.y * a.K.n + row;
+    kahan_add(a.G + gi, a.Gc + gi, t1);
+    kahan_add(a.H + gi, a.Hc + gi, t2);
+  }
+}
+
+__global__ void k_coefs(CoefArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n) return;
+  double m = 0.0, D = 0.0;
+  for (int64_t q = a.nc_ptr[r]; q < a.nc_ptr[r + 1]; ++q) m += a.eps[a.nc_cell[q]] * a.nc_w[q];
+  if (a.bc == MG_BC_ABC1)
+    for (int64_t q = a.nf_ptr[r]; q < a.nf_ptr[r + 1]; ++q)
+      D += sqrt(a.eps[a.nf_cell[q]]) * a.nf_w[q];
+  const double w = m + 0.5 * a.dt * D;
+  float4 c = make_float4((float)(2.0 * m / w), (float)((m - 0.5 * a.dt * D) / w),
+                         (float)(a.dt * a.dt / w), (float)(1.0 / w));
+  if (a.bc == MG_BC_DIRICHLET && a.is_bnd[r]) c = make_float4(0.f, 0.f, 0.f, 0.f);
+  a.coef[r] = c;
+  if (a.mass) a.mass[r] = m;
+}
+
+__global__ void k_tangent_coefs(TangentCoefArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.c.n) return;
+  double m = 0.0, D = 0.0, dm = 0.0, dD = 0.0;
+  for (int64_t q = a.c.nc_ptr[r]; q < a.c.nc_ptr[r + 1]; ++q) {
+    const int e = a.c.nc_cell[q];
+    m += a.c.eps[e] * a.c.nc_w[q];
+    dm += a.v[a.anc[e]] * a.c.nc_w[q];
+  }
+  if (a.c.bc == MG_BC_ABC1)
+    for (int64_t q = a.c.nf_ptr[r]; q < a.c.nf_ptr[r + 1]; ++q) {
+      const int e = a.c.nf_cell[q];
+      const double se = sqrt(a.c.eps[e]);
+      D += se * a.c.nf_w[q];
+      dD += a.v[a.anc[e]] / (2.0 * se) * a.c.nf_w[q];
+    }
+  const double w = m + 0.5 * a.c.dt * D;
+  float2 t = make_float2((float)(dm / w), (float)(a.c.dt * dD / (2.0 * w)));
+  if (a.c.bc == MG_BC_DIRICHLET && a.c.is_bnd[r]) t = make_float2(0.f, 0.f);
+  a.tcoef[r] = t;
+}
+
+__global__ void k_cfl_reduce(int32_t n, const double* row_abs, const double* mass,
+                             double* out) {
+  __shared__ double sm[1024];
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) mx = fmax(mx, row_abs[r] / mass[r]);
+  sm[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sm[0];
+}
+
+__device__ __forceinline__ double total(const float* s, const float* c, int n,
+                                        int tiles, int r) {
+  double t = 0.0;
+  for (int j = 0; j < tiles; ++j) t += (double)s[(size_t)j * n + r] - (double)c[(size_t)j * n + r];
+  return t;
+}
+
+__global__ void k_cell_gradient(GradArgs a) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.m) return;
+  double gs = 0.0;
+  for (int j = 0; j < a.k; ++j) gs += total(a.G, a.Gc, a.n, a.tiles, a.cells[e * a.k + j]);
+  double g = -a.vol[e] / a.k * gs;
+  if (a.bc == MG_BC_ABC1) {
+    const double se = sqrt(a.eps[e]);
+    for (int64_t q = a.cf_ptr[e]; q < a.cf_ptr[e + 1]; ++q) {
+      const int f = a.cf_facet[q];
+      double hs = 0.0;
+      for (int j = 0; j < a.dim; ++j) hs += total(a.H, a.Hc, a.n, a.tiles, a.bnd[(int64_t)f * a.dim + j]);
+      g -= 0.5 * a.dt * a.bnd_meas[f] / (2.0 * a.dim * se) * hs;
+    }
+  }
+  a.g_fine[e] = g;
+}
+
+__global__ void k_restrict(int64_t nc, const int64_t* ptr, const int32_t* idx,
+                           const double* g_fine, double* g_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  double s = 0.0;
+  for (int64_t q = ptr[c]; q < ptr[c + 1]; ++q) s += g_fine[idx[q]];
+  g_out[c] = s;
+}
+
+__global__ void k_d2f(const double* in, float* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+__global__ void k_add_int(int32_t* p, int32_t v) { *p += v; }
+
+__global__ void k_copy_f4(const float4* __restrict__ src, float4* __restrict__ dst,
+                          int64_t n4) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+int check_launch() {
+  return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+int lpr_of(int S_pad) { return S_pad >= kTile ? 32 : S_pad / 4; }
+
+}  // namespace
+
+int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
+  const int lpr = lpr_of(S_pad);
+  const int rows_per_block = kWarps * (32 / lpr);
+  dim3 grid((a.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
+  switch (lpr) {
+    case 32: k_step<32><<<grid, kThreads, 0, st>>>(a); break;
+    case 16: k_step<16><<<grid, kThreads, 0, st>>>(a); break;
+    case 8: k_step<8><<<grid, kThreads, 0, st>>>(a); break;
+    case 4: k_step<4><<<grid, kThreads, 0, st>>>(a); break;
+    case 2: k_step<2><<<grid, kThreads, 0, st>>>(a); break;
+    case 1: k_step<1><<<grid, kThreads, 0, st>>>(a); break;
+    default: return MG_ERR_ARG;
+  }
+  return check_launch();
+}
+
+int launch_step_single(const StepArgs& a, int shot, cudaStream_t st) {
+  k_step_single<<<(a.K.n + 255) / 256, 256, 0, st>>>(a, shot);
+  return check_launch();
+}
+
+int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st) {
+  const int lpr = lpr_of(S_pad);
+  const int rows_per_block = kWarps * (32 / lpr);
+  dim3 grid((a.f.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
+  switch (lpr) {
+    case 32: k_tangent<32><<<grid, kThreads, 0, st>>>(a); break;
+    case 16: k_tangent<16><<<grid, kThreads, 0, st>>>(a); break;
+    case 8: k_tangent<8><<<grid, kThreads, 0, st>>>(a); break;
+    case 4: k_tangent<4><<<grid, kThreads, 0, st>>>(a); break;
+    case 2: k_tangent<2><<<grid, kThreads, 0, st>>>(a); break;
+    case 1: k_tangent<1><<<grid, kThreads, 0, st>>>(a); break;
+    default: return MG_ERR_ARG;
+  }
+  return check_launch();
+}
+
+int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st) {
+  const int lpr = lpr_of(S_pad);
+  const int rows_per_block = kWarps * (32 / lpr);
+  dim3 grid((a.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
+  switch (lpr) {
+    case 32: k_adjoint<32><<<grid, kThreads, 0, st>>>(a); break;
+    case 16: k_adjoint<16><<<grid, kThreads, 0, st>>>(a); break;
+    case 8: k_adjoint<8><<<grid, kThreads, 0, st>>>(a); break;
+    case 4: k_adjoint<4><<<grid, kThreads, 0, st>>>(a); break;
+    case 2: k_adjoint<2><<<grid, kThreads, 0, st>>>(a); break;
+    case 1: k_adjoint<1><<<grid, kThreads, 0, st>>>(a); break;
+    default: return MG_ERR_ARG;
+  }
+  return check_launch();
+}
+
+int launch_coefs(const CoefArgs& a, cudaStream_t st) {
+  k_coefs<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+  return check_launch();
+}
+
+int launch_tangent_coefs(const TangentCoefArgs& a, cudaStream_t st) {
+  k_tangent_coefs<<<(a.c.n + 255) / 256, 256, 0, st>>>(a);
+  return check_launch();
+}
+
+int launch_cfl_reduce(int32_t n, const double* row_abs, const double* mass,
+                      double* out, cudaStream_t st) {
+  k_cfl_reduce<<<1, 1024, 0, st>>>(n, row_abs, mass, out);
+  return check_launch();
+}
+
+int launch_cell_gradient(const GradArgs& a, cudaStream_t st) {
+  k_cell_gradient<<<(unsigned)((a.m + 255) / 256), 256, 0, st>>>(a);
+  return check_launch();
+}
+
+int launch_restrict(int64_t nc, const int64_t* ptr, const int32_t* idx,
+                    const double* g_fine, double* g_out, cudaStream_t st) {
+  k_restrict<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, ptr, idx, g_fine, g_out);
+  return check_launch();
+}
+
+int launch_d2f(const double* in, float* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return MG_OK;
+  k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+  return check_launch();
+}
+
+int launch_add_int(int32_t* p, int32_t v, cudaStream_t st) {
+  k_add_int<<<1, 1, 0, st>>>(p, v);
+  return check_launch();
+}
+
+int launch_copy_f4(const float* src, float* dst, int64_t n_floats, cudaStream_t st) {
+  const int64_t n4 = n_floats / 4;
+  if (n4 <= 0) return MG_OK;
+  const int64_t blocks = (n4 + 255) / 256;
+  k_copy_f4<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(
+      reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst), n4);
+  return check_launch();
+}
+
+}  // namespace mg

@@ -1,0 +1,132 @@
+// Device kernels of the leapfrog wave path and their launch wrappers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mg {
+
+// Sparse stiffness in sliced-ELL form (see mg_internal.h).
+struct DevEll {
+  const int2* ell;          // {col, float bits of K_ij}
+  const int64_t* slice_off;
+  const int32_t* slice_w;
+  int32_t n;                // rows
+};
+
+// Per-row event lists built from a shot batch: sources and receivers.
+struct DevEvents {
+  const int32_t* src_ptr;   // [n+1]
+  const int32_t* src_shot;  // shot index of each source at the row
+  const int32_t* rec_ptr;   // [n+1]
+  const int32_t* rec_shot;  // shot index of each receiver entry at the row
+  const int32_t* rec_trace; // trace row of each receiver entry
+};
+
+// One forward step, all shots: pout <- alpha p - beta pm - gamma (K p - s_l e_src)
+// (state [n][ld] FP32, ld = padded shot count), records traces[tr][l].
+struct StepArgs {
+  DevEll K;
+  DevEvents ev;
+  const float4* coef;       // {alpha, beta, gamma, 1/w} per row
+  const float* p;           // p_l
+  const float* pm;          // p_{l-1}
+  float* pout;              // p_{l+1} (may alias pm: in-place update)
+  int32_t ld;
+  const float* wavelet;     // FP32 samples
+  float* traces;            // [n_traces][nt] or null
+  int32_t nt;
+  int32_t step;             // l = step + (step_base ? *step_base : 0)
+  const int32_t* step_base;
+};
+
+// Tangent step: forward and tangent states advance together.
+struct TangentArgs {
+  StepArgs f;               // forward (traces unused)
+  const float* q;           // dp_l
+  float* qm;                // dp_{l-1} in, dp_{l+1} out
+  const float2* tcoef;      // {gamma dm/dt^2, gamma dD/(2 dt)} per row
+  float* dtraces;           // [n_traces][nt]
+};
+
+// Adjoint (reverse) step k: mu_{k+1} buffer <- mu_{k-1}, and the per-row
+// accumulations G += sum_s p_k (mu_{k-1} - 2 mu_k + mu_{k+1}),
+// H += sum_s p_k (mu_{k-1} - mu_{k+1}) with Kahan compensation.
+struct AdjointArgs {
+  DevEll K;
+  DevEvents ev;
+  const float4* coef;
+  const float* mu;          // mu_k
+  float* mu1;               // mu_{k+1} in, mu_{k-1} out
+  const float* pk;          // forward state p_k
+  int32_t ld;
+  const float* w;           // [n_traces][nt] trace weights
+  int32_t nt;
+  int32_t k;                // reverse step index (uses w[.][k-1])
+  float* G;                 // [tiles][n] sums
+  float* Gc;                // compensations
+  float* H;
+  float* Hc;
+};
+
+int launch_step(const StepArgs& a, int S_pad, cudaStream_t st);
+int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);
+int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st);
+int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st);
+
+// Coefficients from eps (FP64 arithmetic, FP32 storage).
+struct CoefArgs {
+  int32_t n;
+  const int64_t* nc_ptr; const int32_t* nc_cell; const double* nc_w;
+  const int64_t* nf_ptr; const int32_t* nf_cell; const double* nf_w;
+  const int32_t* is_bnd;
+  const double* eps;
+  double dt;
+  int32_t bc;
+  float4* coef;             // out
+  double* mass;             // out (may be null)
+};
+int launch_coefs(const CoefArgs& a, cudaStream_t st);
+
+struct TangentCoefArgs {
+  CoefArgs c;
+  const double* v;          // level cells
+  const int32_t* anc;       // ancestor on the level of each finest cell
+  float2* tcoef;            // out
+};
+int launch_tangent_coefs(const TangentCoefArgs& a, cudaStream_t st);
+
+// max_i row_abs_i / m_i -> out[0] (single block reduction).
+int launch_cfl_reduce(int32_t n, const double* row_abs, const double* mass,
+                      double* out, cudaStream_t st);
+
+// g_e per finest cell from G, H; then restriction to level cells.
+struct GradArgs {
+  int64_t m;
+  int32_t k;                // nodes per cell (d+1)
+  int32_t dim;
+  const int32_t* cells;     // [m][k] rows
+  const double* vol;        // |e|
+  const int64_t* cf_ptr;    // cell -> owned boundary facets
+  const int32_t* cf_facet;
+  const int32_t* bnd;       // [nb][dim] rows
+  const double* bnd_meas;
+  const double* eps;
+  double dt;
+  int32_t bc;
+  int32_t n;
+  int32_t tiles;
+  const float* G; const float* Gc; const float* H; const float* Hc;
+  double* g_fine;           // out [m]
+};
+int launch_cell_gradient(const GradArgs& a, cudaStream_t st);
+int launch_restrict(int64_t nc, const int64_t* ptr, const int32_t* idx,
+                    const double* g_fine, double* g_out, cudaStream_t st);
+
+// Small helpers.
+int launch_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
+int launch_add_int(int32_t* p, int32_t v, cudaStream_t st);
+int launch_copy_f4(const float* src, float* dst, int64_t n_floats, cudaStream_t st);
+
+}  // namespace mg

@@ -1,0 +1,175 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated for the method: FP32 state, FP64 coefficients and
+reductions): traces within 1e-4 relative L2 of the oracle after the full
+step count; Jacobian columns J v and gradients J^T w within 1e-3.
+"""
+import numpy as np
+import pytest
+
+from helpers import (JAC_TOL, TRACE_TOL, oracle_dt, oracle_gradient, oracle_problem,
+                     oracle_tangent, oracle_traces, rel_l2)
+from workloads import configs, shots as shots_mod
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mg(cuda_device):
+    from paper_1707_04605_gb300 import build
+
+    build.build()
+    import paper_1707_04605_gb300 as mg
+
+    return mg
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+# ------------------------------------------------------------------ forward
+def test_cfl_matches_oracle(mg):
+    for w in (configs.tiny_2d(), configs.tiny_3d(), configs.square_disc_2d()):
+        mesh = mg.mesh_from_workload(w)
+        pb = oracle_problem(w)
+        assert abs(mg.cfl_dt(mesh, _dev(w.eps)) / pb.cfl_dt() - 1) < 1e-12
+        assert abs(mg.cfl_dt(mesh, w.eps) / pb.cfl_dt() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("make,bc,order", [
+    (configs.tiny_2d, "abc", "rcm"), (configs.tiny_2d, "neumann", "morton"),
+    (configs.tiny_2d, "dirichlet", "none"), (configs.tiny_3d, "abc", "rcm"),
+    (configs.tiny_3d, "neumann", "morton")])
+def test_forward_tiny(mg, make, bc, order):
+    w = make(bc=bc)
+    mesh = mg.mesh_from_workload(w, order=order)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    ref = oracle_traces(w, dt, s, w.shots)
+    assert rel_l2(y, ref) < TRACE_TOL
+
+
+def test_forward_square_disc_2d_full(mg):
+    """4225 nodes, 1 shot x 16 receivers, 2000 steps: all traces."""
+    w = configs.square_disc_2d()
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    ref = oracle_traces(w, dt, s, w.shots)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    assert rel_l2(y, ref) < TRACE_TOL
+    per_trace = max(rel_l2(y[r], ref[r]) for r in range(len(y)))
+    assert per_trace < 10 * TRACE_TOL
+    # host-pointer path (copies inside the call) gives the same bits
+    yh = mg.forward(mesh, w.eps, w.shots, s, dt)
+    assert np.array_equal(yh, y)
+    # the plain one-shot-at-a-time path
+    y1 = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt, single_source=True).cpu().numpy()
+    assert rel_l2(y1, ref) < TRACE_TOL
+
+
+@pytest.mark.parametrize("S,nt", [(37, 900), (200, 400), (1, 600), (6, 700)])
+def test_forward_asteroid_ragged_batches(mg, S, nt):
+    """Level-2 asteroid mesh (15.7k nodes): padded shot counts 64 (LPR 16),
+    256 (two source tiles), 4 and 8; every trace against the oracle."""
+    w = configs.asteroid_2d(n_refine=2, S=S, nt=nt)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    ref = oracle_traces(w, dt, s, w.shots)
+    assert rel_l2(y, ref) < TRACE_TOL
+
+
+def test_forward_asteroid_2d_full_sampled(mg):
+    """Full workload (62,641 nodes, 128 shots, 8000 steps, one launch per
+    step over all shots): shots 0 and 77 against the oracle; batching
+    invariance against the plain one-shot path."""
+    w = configs.asteroid_2d()
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    pick = [0, 77]
+    sub = w.shots.subset(pick)
+    ref = oracle_traces(w, dt, s, sub)
+    rows = w.shots.trace_rows(pick)
+    assert rel_l2(y[rows], ref) < TRACE_TOL
+    y1 = mg.forward(mesh, _dev(w.eps), sub, _dev(s), dt, single_source=True).cpu().numpy()
+    assert rel_l2(y1, y[rows]) < 1e-6
+
+
+def test_cfl_violation_rejected(mg):
+    from paper_1707_04605_gb300 import _lib as L
+
+    w = configs.tiny_2d()
+    mesh = mg.mesh_from_workload(w)
+    dt = 1.01 * oracle_problem(w).cfl_dt()
+    with pytest.raises(L.MgError) as e:
+        mg.forward(mesh, _dev(w.eps), w.shots, _dev(w.wavelet(dt)), dt)
+    assert e.value.code == L.MG_ERR_CFL
+
+
+# ---------------------------------------------------------------- Jacobian
+@pytest.mark.parametrize("make,bc", [(configs.tiny_2d, "abc"), (configs.tiny_2d, "dirichlet"),
+                                     (configs.tiny_3d, "abc")])
+def test_tangent_and_adjoint_tiny(mg, make, bc):
+    w = make(bc=bc)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    rng = np.random.default_rng(0)
+    level = 1
+    v = rng.standard_normal(w.mesh.n_cells[level])
+    W = rng.standard_normal((w.shots.n_traces, len(s)))
+    jv = mg.jacobian_apply(mesh, level, _dev(w.eps), w.shots, _dev(s), dt, _dev(v)).cpu().numpy()
+    assert rel_l2(jv, oracle_tangent(w, dt, s, w.shots, v, level)) < JAC_TOL
+    g = mg.jacobian_T_apply(mesh, level, _dev(w.eps), w.shots, _dev(s), dt,
+                            _dev(W, torch.float32), ckpt_every=16).cpu().numpy()
+    ref = oracle_gradient(w, dt, s, w.shots, W.astype(np.float32).astype(np.float64), level)
+    assert rel_l2(g, ref) < JAC_TOL
+    # dot-product test on the GPU outputs, inner products in FP64
+    lhs = float(np.sum(jv.astype(np.float64) * W.astype(np.float32)))
+    rhs = float(np.sum(v * g))
+    assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), 1e-30)
+
+
+def test_adjoint_checkpoint_spacing_and_reuse(mg):
+    w = configs.asteroid_2d(n_refine=1, S=12, nt=300)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    eps = _dev(w.eps)
+    W = _dev(np.random.default_rng(1).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    g7 = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=7)
+    g64 = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+    assert torch.equal(g7, g64)
+    mg.forward(mesh, eps, w.shots, s, dt, ckpt_every=64, keep_checkpoints=True)
+    gr = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64,
+                             reuse_checkpoints=True)
+    assert torch.equal(gr, g64)
+    gh = mg.jacobian_T_apply(mesh, 1, w.eps, w.shots, w.wavelet(dt), dt,
+                             W.cpu().numpy(), ckpt_every=64)
+    assert np.array_equal(gh, g64.cpu().numpy())
+
+
+def test_jacobian_square_disc_2d(mg):
+    """4225 nodes, 2000 steps: a level-1 column J e_j and J^T w vs oracle."""
+    w = configs.square_disc_2d()
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    level = 1
+    rng = np.random.default_rng(2)
+    v = np.zeros(w.mesh.n_cells[level])
+    v[rng.integers(len(v))] = 1.0
+    jv = mg.jacobian_apply(mesh, level, _dev(w.eps), w.shots, _dev(s), dt, _dev(v)).cpu().numpy()
+    assert rel_l2(jv, oracle_tangent(w, dt, s, w.shots, v, level)) < JAC_TOL
+    W = rng.standard_normal((w.shots.n_traces, len(s))).astype(np.float32)
+    g = mg.jacobian_T_apply(mesh, level, _dev(w.eps), w.shots, _dev(s), dt,
+                            _dev(W, torch.float32), ckpt_every=256).cpu().numpy()
+    assert rel_l2(g, oracle_gradient(w, dt, s, w.shots, W.astype(np.float64), level)) < JAC_TOL
