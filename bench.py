@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="override the step count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the timed device steps (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -272,6 +274,11 @@ def main():
         torch.distributed.barrier()
     launches = mesh.launch_count() - launches0
     clocks = clocks_stop(clk, dev.index) if rank == 0 else None
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "launches": int(launches),
+                              "step_ms": [e[0].elapsed_time(e[3]) for e in times]}))
+        return 0
     step_ms = [e[0].elapsed_time(e[3]) for e in times]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in times]
     adj_ms = [e[1].elapsed_time(e[2]) for e in times]

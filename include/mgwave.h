@@ -185,6 +185,15 @@ int mg_jacobian_T_apply(mg_mesh* mesh, int level, const double* eps,
 /* Release the handle's scratch (states, checkpoints, graphs). */
 int mg_mesh_trim(mg_mesh* mesh);
 
+/* Launch-shape tuning of a handle (no effect on results):
+ *  chunk  leapfrog steps captured per CUDA graph; an even number >= 2, or 0
+ *         for one plain launch per step.  Default 128.
+ *  batch  stiffness entries whose neighbour rows are gathered together per
+ *         row, 4 or 8.  Default 8.
+ * Pass -1 to keep a value.  Drops the handle's cached graphs.
+ * Errors: MG_ERR_ARG for values outside these sets. */
+int mg_mesh_set_tuning(mg_mesh* mesh, int chunk, int batch);
+
 /* Number of kernel launches the handle has issued so far (graph-launched
  * kernels counted per node).  Used to report launch counts. */
 int64_t mg_launch_count(const mg_mesh* mesh);

@@ -116,6 +116,11 @@ class Mesh:
     def launch_count(self) -> int:
         return int(self._lib.mg_launch_count(self.handle))
 
+    def set_tuning(self, chunk: int = -1, batch: int = -1):
+        """Graph chunk length (even, 0 = plain launches) and gather batch (4/8)."""
+        L.check(self._lib.mg_mesh_set_tuning(self.handle, int(chunk), int(batch)),
+                "mg_mesh_set_tuning")
+
 
 def mesh_create(dim, coords, cells, cell_parent, n_cells_per_level, bnd, bc="abc",
                 order="rcm") -> Mesh:

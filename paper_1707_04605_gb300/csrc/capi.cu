@@ -5,7 +5,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <initializer_list>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -88,11 +91,19 @@ struct mg_mesh {
   int ev_S_pad = 0;
   int64_t ev_n_src = 0, ev_n_rec = 0;
   bool ev_valid = false;
+  int64_t ev_gen = 0;                     // bumped whenever the event lists change
   // checkpoints of the last mg_forward with MG_KEEP_CHECKPOINTS
   bool ck_valid = false;
   int ck_every = 0, ck_nt = 0, ck_S_pad = 0, ck_nshots = 0;
   double ck_dt = 0.0;
+  int64_t ck_ev_gen = -1;
   int64_t launches = 0;
+  // CUDA graphs of step chunks, keyed by kind, buffers and sizes
+  int chunk = 128;                        // steps per graph (even), 0 = off
+  int batch = 8;                          // stiffness entries per gather batch
+  cudaStream_t cap = nullptr;             // private capture stream
+  std::map<std::string, cudaGraphExec_t> graphs;
+  Buf tr;                                 // internal trace buffer [R][nt]
 };
 
 namespace {
@@ -174,6 +185,7 @@ int build_events(mg_mesh* M, const mg_shots* sh, mg::DevEvents& ev) {
     M->ev_rec = rec;
     M->ev_ptr = ptr;
     M->ev_valid = true;
+    M->ev_gen++;
   }
   int32_t* base = P<int32_t>(M->ev);
   ev.src_ptr = base;
@@ -207,9 +219,15 @@ int stage_in(Buf& b, const void* src, size_t bytes, int flags, cudaStream_t st,
   return MG_OK;
 }
 
-int finish_out(Buf& b, void* dst, size_t bytes, int flags, cudaStream_t st) {
-  if (!(flags & MG_HOST_PTRS)) return MG_OK;
-  if (cudaMemcpyAsync(dst, b.p, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MG_ERR_CUDA;
+// Results leave the handle's buffer for the caller's: device to device on
+// the stream, or device to host followed by a stream synchronisation.
+int deliver(Buf& b, void* dst, size_t bytes, int flags, cudaStream_t st) {
+  if (bytes == 0) return MG_OK;
+  const bool host = flags & MG_HOST_PTRS;
+  if (cudaMemcpyAsync(dst, b.p, bytes, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                      st) != cudaSuccess)
+    return MG_ERR_CUDA;
+  if (!host) return MG_OK;
   return cudaStreamSynchronize(st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
@@ -277,12 +295,56 @@ mg::StepArgs step_args(mg_mesh* M, const Prep& pp, int ld, int nt) {
   a.wavelet = P<const float>(M->wavf);
   a.nt = nt;
   a.step_base = nullptr;
+  a.batch = M->batch;
   return a;
 }
 
+// Replays a captured sequence of launches on `st`.  The sequence is recorded
+// once per key on the handle's private capture stream (the caller's stream
+// may be the legacy default stream, which cannot be captured); step indices
+// inside it are relative to the device int `step_base`.
+template <class F>
+int run_graph(mg_mesh* M, const std::string& key, int nodes, cudaStream_t st, F&& record) {
+  auto it = M->graphs.find(key);
+  cudaGraphExec_t exec = nullptr;
+  if (it == M->graphs.end()) {
+    if (!M->cap) MG_CU(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
+    MG_CU(cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = record(M->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(M->cap, &g);
+    if (rc != MG_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc != MG_OK ? rc : MG_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { cudaGetLastError(); return MG_ERR_CUDA; }
+    M->graphs[key] = exec;
+  } else {
+    exec = it->second;
+  }
+  MG_CU(cudaGraphLaunch(exec, st));
+  M->launches += nodes;
+  return MG_OK;
+}
+
+std::string key_of(const char* kind, std::initializer_list<const void*> ptrs,
+                   std::initializer_list<long long> ints) {
+  std::string k(kind);
+  char buf[32];
+  for (const void* p : ptrs) { snprintf(buf, sizeof buf, "|%p", p); k += buf; }
+  for (long long v : ints) { snprintf(buf, sizeof buf, "|%lld", v); k += buf; }
+  return k;
+}
+
+bool graphs_on(mg_mesh* M, int flags) { return M->chunk >= 2 && !(flags & MG_NO_GRAPH); }
+
 // Batched forward loop over steps [0, nt); optional traces and checkpoints.
+// Whole chunks of M->chunk steps run as one graph launch each.
 int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_every,
-                float* ckpt, cudaStream_t st) {
+                float* ckpt, cudaStream_t st, int flags) {
   const int64_t n = M->hm.n;
   const size_t state = (size_t)n * pp.S_pad;
   MG_TRY(ensure(M->stA, state * sizeof(float)));
@@ -293,7 +355,40 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
   MG_CU(cudaMemsetAsync(pm, 0, state * sizeof(float), st));
   mg::StepArgs a = step_args(M, pp, pp.S_pad, nt);
   a.traces = traces;
-  for (int l = 0; l < nt; ++l) {
+  int l = 0;
+  const int C = M->chunk;
+  if (graphs_on(M, flags) && nt >= C && (!ckpt || ckpt_every % C == 0)) {
+    MG_TRY(ensure(M->step_base, 16));
+    int32_t* base = P<int32_t>(M->step_base);
+    MG_TRY(mg::launch_set_int(base, 0, st));
+    M->launches += 1;
+    const std::string key = key_of("fwd", {p, pm, traces, a.wavelet, a.coef, a.ev.src_ptr, base},
+                                   {pp.S_pad, pp.S, pp.R, nt, C, n});
+    for (; l + C <= nt; l += C) {
+      if (ckpt && l % ckpt_every == 0) {
+        float* slot = ckpt + (size_t)(l / ckpt_every) * 2 * state;
+        MG_TRY(mg::launch_copy_f4(p, slot, (int64_t)state, st));
+        MG_TRY(mg::launch_copy_f4(pm, slot + state, (int64_t)state, st));
+        M->launches += 2;
+      }
+      MG_TRY(run_graph(M, key, C + 1, st, [&](cudaStream_t cs) {
+        mg::StepArgs b = a;
+        b.step_base = base;
+        float* x = p;
+        float* y = pm;
+        for (int j = 0; j < C; ++j) {
+          b.p = x;
+          b.pm = y;
+          b.pout = y;
+          b.step = j;
+          MG_TRY(mg::launch_step(b, pp.S_pad, cs));
+          std::swap(x, y);
+        }
+        return mg::launch_add_int(base, C, cs);
+      }));
+    }
+  }
+  for (; l < nt; ++l) {
     if (ckpt && l % ckpt_every == 0) {
       float* slot = ckpt + (size_t)(l / ckpt_every) * 2 * state;
       MG_TRY(mg::launch_copy_f4(p, slot, (int64_t)state, st));
@@ -423,15 +518,19 @@ void mg_mesh_destroy(mg_mesh* M) {
     for (Buf& b : *v)
       if (b.p) cudaFree(b.p);
   mg_mesh_trim(M);
+  if (M->cap) cudaStreamDestroy(M->cap);
   delete M;
 }
 
 int mg_mesh_trim(mg_mesh* M) {
   if (!M) return MG_ERR_ARG;
   DeviceGuard g(M->device);
+  // graphs hold the scratch pointers: drop them with the scratch
+  for (auto& kv : M->graphs) cudaGraphExecDestroy(kv.second);
+  M->graphs.clear();
   Buf* all[] = {&M->eps_h, &M->wav_h, &M->wavf, &M->coef, &M->tcoef, &M->mass, &M->scal,
                 &M->stA, &M->stB, &M->stC, &M->stD, &M->out_h, &M->w_h, &M->v_h, &M->g_h,
-                &M->ev, &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base};
+                &M->ev, &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base, &M->tr};
   for (Buf* b : all) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -439,6 +538,18 @@ int mg_mesh_trim(mg_mesh* M) {
   }
   M->ev_valid = false;
   M->ck_valid = false;
+  return MG_OK;
+}
+
+int mg_mesh_set_tuning(mg_mesh* M, int chunk, int batch) {
+  if (!M) return MG_ERR_ARG;
+  if (chunk != -1 && (chunk < 0 || chunk == 1 || chunk % 2 != 0 || chunk > 4096)) return MG_ERR_ARG;
+  if (batch != -1 && batch != 4 && batch != 8) return MG_ERR_ARG;
+  DeviceGuard g(M->device);
+  for (auto& kv : M->graphs) cudaGraphExecDestroy(kv.second);
+  M->graphs.clear();
+  if (chunk != -1) M->chunk = chunk;
+  if (batch != -1) M->batch = batch;
   return MG_OK;
 }
 
@@ -499,11 +610,8 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
   Prep pp;
   MG_TRY(prepare(M, eps, shots, wavelet, dt, nt, flags, st, pp));
   const size_t tbytes = (size_t)pp.R * nt * sizeof(float);
-  float* tr = traces;
-  if (flags & MG_HOST_PTRS) {
-    MG_TRY(ensure(M->out_h, tbytes));
-    tr = P<float>(M->out_h);
-  }
+  MG_TRY(ensure(M->tr, tbytes));
+  float* tr = P<float>(M->tr);
   if (flags & MG_SINGLE_SOURCE) {
     MG_TRY(run_forward_single(M, pp, nt, tr, st));
   } else {
@@ -514,7 +622,7 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
       MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * M->hm.n * pp.S_pad * sizeof(float)));
       ck = P<float>(M->ckpt);
     }
-    MG_TRY(run_forward(M, pp, nt, tr, ckpt_every, ck, st));
+    MG_TRY(run_forward(M, pp, nt, tr, ckpt_every, ck, st, flags));
     if (ck) {
       M->ck_valid = true;
       M->ck_every = ckpt_every;
@@ -522,9 +630,10 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
       M->ck_S_pad = pp.S_pad;
       M->ck_nshots = pp.S;
       M->ck_dt = dt;
+      M->ck_ev_gen = M->ev_gen;
     }
   }
-  return finish_out(M->out_h, traces, tbytes, flags, st);
+  return deliver(M->tr, traces, tbytes, flags, st);
 }
 
 int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* shots,
@@ -550,11 +659,8 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
   MG_TRY(mg::launch_tangent_coefs(tca, st));
   M->launches += 1;
   const size_t tbytes = (size_t)pp.R * nt * sizeof(float);
-  float* tr = jv;
-  if (flags & MG_HOST_PTRS) {
-    MG_TRY(ensure(M->out_h, tbytes));
-    tr = P<float>(M->out_h);
-  }
+  MG_TRY(ensure(M->tr, tbytes));
+  float* tr = P<float>(M->tr);
   const int64_t n = M->hm.n;
   const size_t state = (size_t)n * pp.S_pad;
   Buf* bufs[] = {&M->stA, &M->stB, &M->stC, &M->stD};
@@ -568,7 +674,36 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
   a.f = step_args(M, pp, pp.S_pad, nt);
   a.tcoef = P<const float2>(M->tcoef);
   a.dtraces = tr;
-  for (int l = 0; l < nt; ++l) {
+  int l = 0;
+  const int C = M->chunk;
+  if (graphs_on(M, flags) && nt >= C) {
+    MG_TRY(ensure(M->step_base, 16));
+    int32_t* base = P<int32_t>(M->step_base);
+    MG_TRY(mg::launch_set_int(base, 0, st));
+    M->launches += 1;
+    const std::string key = key_of("tan", {p, pm, q, qm, tr, a.f.wavelet, a.f.coef, a.tcoef,
+                                           a.f.ev.src_ptr, base}, {pp.S_pad, pp.S, pp.R, nt, C, n});
+    for (; l + C <= nt; l += C) {
+      MG_TRY(run_graph(M, key, C + 1, st, [&](cudaStream_t cs) {
+        mg::TangentArgs b = a;
+        b.f.step_base = base;
+        float *x = p, *y = pm, *u = q, *z = qm;
+        for (int j = 0; j < C; ++j) {
+          b.f.p = x;
+          b.f.pm = y;
+          b.f.pout = y;
+          b.q = u;
+          b.qm = z;
+          b.f.step = j;
+          MG_TRY(mg::launch_tangent(b, pp.S_pad, cs));
+          std::swap(x, y);
+          std::swap(u, z);
+        }
+        return mg::launch_add_int(base, C, cs);
+      }));
+    }
+  }
+  for (; l < nt; ++l) {
     a.f.p = p;
     a.f.pm = pm;
     a.f.pout = pm;
@@ -580,7 +715,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
     std::swap(p, pm);
     std::swap(q, qm);
   }
-  return finish_out(M->out_h, jv, tbytes, flags, st);
+  return deliver(M->tr, jv, tbytes, flags, st);
 }
 
 int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots* shots,
@@ -597,22 +732,28 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   MG_TRY(ensure_level(M, level));
   const int64_t n = M->hm.n;
   const size_t state = (size_t)n * pp.S_pad;
-  const void* d;
-  MG_TRY(stage_in(M->w_h, w, (size_t)pp.R * nt * sizeof(float), flags, st, &d));
-  const float* wd = static_cast<const float*>(d);
+  // trace weights into the handle's buffer (stable address for the graphs)
+  const size_t wbytes = (size_t)pp.R * nt * sizeof(float);
+  MG_TRY(ensure(M->w_h, wbytes));
+  MG_CU(cudaMemcpyAsync(M->w_h.p, w, wbytes,
+                        (flags & MG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                        st));
+  const float* wd = P<const float>(M->w_h);
   // checkpoints
   const bool reuse = (flags & MG_REUSE_CHECKPOINTS) && M->ck_valid && M->ck_every == ckpt_every &&
                      M->ck_nt == nt && M->ck_S_pad == pp.S_pad && M->ck_nshots == pp.S &&
-                     M->ck_dt == dt;
+                     M->ck_dt == dt && M->ck_ev_gen == M->ev_gen;
   if ((flags & MG_REUSE_CHECKPOINTS) && !reuse) return MG_ERR_ARG;
   const int nck = (nt + ckpt_every - 1) / ckpt_every;
   if (!reuse) {
+    M->ck_valid = false;
     MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * state * sizeof(float)));
-    MG_TRY(run_forward(M, pp, nt, nullptr, ckpt_every, P<float>(M->ckpt), st));
+    MG_TRY(run_forward(M, pp, nt, nullptr, ckpt_every, P<float>(M->ckpt), st, flags));
   }
   float* ck = P<float>(M->ckpt);
-  // segment buffer: slots for p_{l0-1} .. p_{l0+K}
-  MG_TRY(ensure(M->seg, (size_t)(ckpt_every + 2) * state * sizeof(float)));
+  // segment buffer: slot j holds p_{l0-1+j}, j = 0..K+1
+  const int K = std::min(ckpt_every, nt);
+  MG_TRY(ensure(M->seg, (size_t)(K + 2) * state * sizeof(float)));
   float* seg = P<float>(M->seg);
   // adjoint states and accumulators
   MG_TRY(ensure(M->stC, state * sizeof(float)));
@@ -634,17 +775,62 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.ld = pp.S_pad;
   aa.w = wd;
   aa.nt = nt;
+  aa.step_base = nullptr;
+  aa.batch = M->batch;
   aa.G = G;
   aa.Gc = G + acc;
   aa.H = G + 2 * acc;
   aa.Hc = G + 3 * acc;
+  const bool use_graph = graphs_on(M, flags) && ckpt_every % 2 == 0 && ckpt_every <= nt;
+  int32_t* base = nullptr;
+  if (use_graph) {
+    MG_TRY(ensure(M->step_base, 16));
+    base = P<int32_t>(M->step_base);
+  }
   for (int a = nck - 1; a >= 0; --a) {
     const int l0 = a * ckpt_every;
     const int l1 = std::min(nt, l0 + ckpt_every);
-    // slot j holds p_{l0-1+j}
     MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state, seg + state, (int64_t)state, st));
     MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state + state, seg, (int64_t)state, st));
     M->launches += 2;
+    if (use_graph && l1 - l0 == ckpt_every) {
+      // whole segment: recompute p_{l0+1..l1}, then reverse steps k = l1..l0+1,
+      // each as one graph; indices relative to *base = l0
+      MG_TRY(mg::launch_set_int(base, l0, st));
+      M->launches += 1;
+      const std::string kr = key_of("rec", {seg, fa.wavelet, fa.coef, fa.ev.src_ptr, base},
+                                    {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n});
+      MG_TRY(run_graph(M, kr, ckpt_every, st, [&](cudaStream_t cs) {
+        mg::StepArgs b = fa;
+        b.step_base = base;
+        for (int j = 1; j <= ckpt_every; ++j) {
+          b.p = seg + (size_t)j * state;
+          b.pm = seg + (size_t)(j - 1) * state;
+          b.pout = seg + (size_t)(j + 1) * state;
+          b.step = j - 1;
+          MG_TRY(mg::launch_step(b, pp.S_pad, cs));
+        }
+        return MG_OK;
+      }));
+      const std::string ka = key_of("adj", {seg, mu, mu1, wd, aa.coef, aa.ev.rec_ptr, G, base},
+                                    {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n});
+      MG_TRY(run_graph(M, ka, ckpt_every, st, [&](cudaStream_t cs) {
+        mg::AdjointArgs b = aa;
+        b.step_base = base;
+        float* x = mu;
+        float* y = mu1;
+        for (int r = ckpt_every; r >= 1; --r) {   // k = l0 + r
+          b.mu = x;
+          b.mu1 = y;
+          b.pk = seg + (size_t)(r + 1) * state;
+          b.k = r;
+          MG_TRY(mg::launch_adjoint(b, pp.S_pad, cs));
+          std::swap(x, y);
+        }
+        return MG_OK;
+      }));
+      continue;   // even segment length: mu / mu1 are back in place
+    }
     for (int l = l0; l < l1; ++l) {
       const int j = l - l0 + 1;  // slot of p_l
       fa.p = seg + (size_t)j * state;
@@ -685,15 +871,11 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   ga.g_fine = P<double>(M->gfine);
   MG_TRY(mg::launch_cell_gradient(ga, st));
   const int64_t nc = M->hm.n_cells_level[level];
-  double* gout = g;
-  if (flags & MG_HOST_PTRS) {
-    MG_TRY(ensure(M->g_h, nc * sizeof(double)));
-    gout = P<double>(M->g_h);
-  }
+  MG_TRY(ensure(M->g_h, nc * sizeof(double)));
   MG_TRY(mg::launch_restrict(nc, P<int64_t>(M->lvl_ptr[level]), P<int32_t>(M->lvl_idx[level]),
-                             ga.g_fine, gout, st));
+                             ga.g_fine, P<double>(M->g_h), st));
   M->launches += 2;
-  return finish_out(M->g_h, g, nc * sizeof(double), flags, st);
+  return deliver(M->g_h, g, nc * sizeof(double), flags, st);
 }
 
 }  // extern "C"

@@ -46,54 +46,84 @@ __device__ __forceinline__ float get_comp(const float4& v, int d) {
   return d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w;
 }
 
-// acc = sum_k K_{row,k} p[k][src0..src0+3]; self = p[row][src0..].
-__device__ __forceinline__ float4 stiff_gather(const DevEll& K, int row,
-                                               const float* __restrict__ p,
-                                               int ld, int src0, float4& self) {
+// Row prologue: every load that depends only on the row index is issued
+// before the first dependent one, so a row costs three memory round trips
+// (row data, stiffness entries, neighbour gathers) instead of one per field.
+struct RowIn {
+  const int2* e;   // first ELL entry of the row (stride kSliceH)
+  int w;           // entries in the row's slice (diagonal first)
+};
+
+__device__ __forceinline__ RowIn row_in(const DevEll& K, int row) {
   const int slice = row / kSliceH;
   const int rl = row - slice * kSliceH;
-  const int2* __restrict__ e = K.ell + K.slice_off[slice] + rl;
-  const int w = K.slice_w[slice];
-  const int2 e0 = __ldg(e);                        // diagonal entry first
-  self = ld4(p + (size_t)row * ld + src0);
-  float4 acc;
-  const float v0 = __int_as_float(e0.y);
-  acc.x = v0 * self.x; acc.y = v0 * self.y; acc.z = v0 * self.z; acc.w = v0 * self.w;
-#pragma unroll 4
-  for (int k = 1; k < w; ++k) {
-    const int2 ek = __ldg(e + k * kSliceH);
-    const float4 x = ld4(p + (size_t)ek.x * ld + src0);
-    acc = fma4(__int_as_float(ek.y), x, acc);
+  RowIn r;
+  r.e = K.ell + __ldg(K.slice_off + slice) + rl;
+  r.w = __ldg(K.slice_w + slice);
+  return r;
+}
+
+// acc += sum_{k=1}^{w-1} K_k p[col_k][src0..src0+3], B entries per batch:
+// the batch's B stiffness entries are loaded together, then its B float4
+// gathers are all in flight before the first FMA.
+template <int B>
+__device__ __forceinline__ float4 gather_acc(RowIn r, const float* __restrict__ p, int ld,
+                                             int src0, float4 acc) {
+  for (int k0 = 1; k0 < r.w; k0 += B) {
+    int2 ek[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      ek[j] = (k0 + j < r.w) ? __ldg(r.e + (k0 + j) * kSliceH) : make_int2(-1, 0);
+    float4 x[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      x[j] = ek[j].x >= 0 ? ld4(p + (size_t)ek[j].x * ld + src0) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc = fma4(__int_as_float(ek[j].y), x[j], acc);
   }
   return acc;
 }
 
-__device__ __forceinline__ float4 stiff_gather2(const DevEll& K, int row,
-                                                const float* __restrict__ p,
-                                                const float* __restrict__ q,
-                                                int ld, int src0, float4& ps,
-                                                float4& qs, float4& qacc) {
-  const int slice = row / kSliceH;
-  const int rl = row - slice * kSliceH;
-  const int2* __restrict__ e = K.ell + K.slice_off[slice] + rl;
-  const int w = K.slice_w[slice];
-  const int2 e0 = __ldg(e);
-  ps = ld4(p + (size_t)row * ld + src0);
-  qs = ld4(q + (size_t)row * ld + src0);
-  const float v0 = __int_as_float(e0.y);
-  float4 acc = make_float4(v0 * ps.x, v0 * ps.y, v0 * ps.z, v0 * ps.w);
-  qacc = make_float4(v0 * qs.x, v0 * qs.y, v0 * qs.z, v0 * qs.w);
-#pragma unroll 4
-  for (int k = 1; k < w; ++k) {
-    const int2 ek = __ldg(e + k * kSliceH);
-    const float v = __int_as_float(ek.y);
-    acc = fma4(v, ld4(p + (size_t)ek.x * ld + src0), acc);
-    qacc = fma4(v, ld4(q + (size_t)ek.x * ld + src0), qacc);
+template <int B>
+__device__ __forceinline__ void gather_acc2(RowIn r, const float* __restrict__ p,
+                                            const float* __restrict__ q, int ld, int src0,
+                                            float4& pacc, float4& qacc) {
+  for (int k0 = 1; k0 < r.w; k0 += B) {
+    int2 ek[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      ek[j] = (k0 + j < r.w) ? __ldg(r.e + (k0 + j) * kSliceH) : make_int2(-1, 0);
+    float4 x[B], y[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const bool ok = ek[j].x >= 0;
+      const size_t o = (size_t)(ok ? ek[j].x : 0) * ld + src0;
+      x[j] = ok ? ld4(p + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      y[j] = ok ? ld4(q + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      pacc = fma4(__int_as_float(ek[j].y), x[j], pacc);
+      qacc = fma4(__int_as_float(ek[j].y), y[j], qacc);
+    }
   }
-  return acc;
 }
 
-template <int LPR>
+__device__ __forceinline__ float4 scale4(float a, float4 x) {
+  return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+}
+
+// out = alpha self - beta old - gamma acc
+__device__ __forceinline__ float4 leap(float4 c, float4 self, float4 old, float4 acc) {
+  float4 o;
+  o.x = c.x * self.x - c.y * old.x - c.z * acc.x;
+  o.y = c.x * self.y - c.y * old.y - c.z * acc.y;
+  o.z = c.x * self.z - c.y * old.z - c.z * acc.z;
+  o.w = c.x * self.w - c.y * old.w - c.z * acc.w;
+  return o;
+}
+
+template <int LPR, int B>
 __global__ void __launch_bounds__(kThreads) k_step(StepArgs a) {
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31;
@@ -101,17 +131,20 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs a) {
   const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
   if (row >= a.K.n) return;
   const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
-  float4 self;
-  const float4 acc = stiff_gather(a.K, row, a.p, a.ld, src0, self);
+  const size_t ro = (size_t)row * a.ld + src0;
+  // round trip 1: row-only data
+  const RowIn r = row_in(a.K, row);
+  const float4 self = ld4(a.p + ro);
+  const float4 old = ld4v(a.pm + ro);
   const float4 c = __ldg(a.coef + row);
-  const float4 old = ld4v(a.pm + (size_t)row * a.ld + src0);
-  float4 out;
-  out.x = c.x * self.x - c.y * old.x - c.z * acc.x;
-  out.y = c.x * self.y - c.y * old.y - c.z * acc.y;
-  out.z = c.x * self.z - c.y * old.z - c.z * acc.z;
-  out.w = c.x * self.w - c.y * old.w - c.z * acc.w;
-  const int l = a.step + (a.step_base ? *a.step_base : 0);
   const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
+  const int r0 = a.traces ? __ldg(a.ev.rec_ptr + row) : 0;
+  const int r1 = a.traces ? __ldg(a.ev.rec_ptr + row + 1) : 0;
+  const int l = a.step + (a.step_base ? *a.step_base : 0);
+  // rounds 2-3: stiffness entries, then neighbour gathers
+  float4 acc = scale4(__int_as_float(__ldg(r.e).y), self);
+  acc = gather_acc<B>(r, a.p, a.ld, src0, acc);
+  float4 out = leap(c, self, old, acc);
   if (s0 != s1) {
     const float sv = c.z * __ldg(a.wavelet + l);
     for (int q = s0; q < s1; ++q) {
@@ -119,14 +152,11 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs a) {
       if (d >= 0 && d < 4) add_comp(out, d, sv);
     }
   }
-  st4(a.pout + (size_t)row * a.ld + src0, out);
-  if (a.traces) {
-    const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
-    for (int q = r0; q < r1; ++q) {
-      const int d = __ldg(a.ev.rec_shot + q) - src0;
-      if (d >= 0 && d < 4)
-        a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = get_comp(out, d);
-    }
+  st4(a.pout + ro, out);
+  for (int q = r0; q < r1; ++q) {
+    const int d = __ldg(a.ev.rec_shot + q) - src0;
+    if (d >= 0 && d < 4)
+      a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = get_comp(out, d);
   }
 }
 
@@ -136,18 +166,16 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs a) {
 __global__ void __launch_bounds__(256) k_step_single(StepArgs a, int shot) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= a.K.n) return;
-  const int slice = row / kSliceH;
-  const int rl = row - slice * kSliceH;
-  const int2* __restrict__ e = a.K.ell + a.K.slice_off[slice] + rl;
-  const int w = a.K.slice_w[slice];
+  const RowIn r = row_in(a.K, row);
   const float self = __ldg(a.p + row);
-  float acc = __int_as_float(__ldg(e).y) * self;
-  for (int k = 1; k < w; ++k) {
-    const int2 ek = __ldg(e + k * kSliceH);
+  const float old = a.pm[row];
+  const float4 c = __ldg(a.coef + row);
+  float acc = __int_as_float(__ldg(r.e).y) * self;
+  for (int k = 1; k < r.w; ++k) {
+    const int2 ek = __ldg(r.e + k * kSliceH);
     acc = fmaf(__int_as_float(ek.y), __ldg(a.p + ek.x), acc);
   }
-  const float4 c = __ldg(a.coef + row);
-  float out = c.x * self - c.y * a.pm[row] - c.z * acc;
+  float out = c.x * self - c.y * old - c.z * acc;
   const int l = a.step + (a.step_base ? *a.step_base : 0);
   const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
   for (int q = s0; q < s1; ++q)
@@ -161,7 +189,7 @@ __global__ void __launch_bounds__(256) k_step_single(StepArgs a, int shot) {
   }
 }
 
-template <int LPR>
+template <int LPR, int B>
 __global__ void __launch_bounds__(kThreads) k_tangent(TangentArgs a) {
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31;
@@ -170,19 +198,19 @@ __global__ void __launch_bounds__(kThreads) k_tangent(TangentArgs a) {
   if (row >= a.f.K.n) return;
   const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
   const int ld = a.f.ld;
-  float4 ps, qs, qacc;
-  const float4 acc = stiff_gather2(a.f.K, row, a.f.p, a.q, ld, src0, ps, qs, qacc);
+  const size_t ro = (size_t)row * ld + src0;
+  const RowIn r = row_in(a.f.K, row);
+  const float4 ps = ld4(a.f.p + ro), qs = ld4(a.q + ro);
+  const float4 pold = ld4v(a.f.pm + ro), qold = ld4v(a.qm + ro);
   const float4 c = __ldg(a.f.coef + row);
   const float2 tc = __ldg(a.tcoef + row);
-  float* qmr = a.qm + (size_t)row * ld + src0;
-  const float4 pold = ld4v(a.f.pm + (size_t)row * ld + src0), qold = ld4v(qmr);
-  float4 pn, qn;
-  pn.x = c.x * ps.x - c.y * pold.x - c.z * acc.x;
-  pn.y = c.x * ps.y - c.y * pold.y - c.z * acc.y;
-  pn.z = c.x * ps.z - c.y * pold.z - c.z * acc.z;
-  pn.w = c.x * ps.w - c.y * pold.w - c.z * acc.w;
-  const int l = a.f.step + (a.f.step_base ? *a.f.step_base : 0);
   const int s0 = __ldg(a.f.ev.src_ptr + row), s1 = __ldg(a.f.ev.src_ptr + row + 1);
+  const int r0 = __ldg(a.f.ev.rec_ptr + row), r1 = __ldg(a.f.ev.rec_ptr + row + 1);
+  const int l = a.f.step + (a.f.step_base ? *a.f.step_base : 0);
+  const float v0 = __int_as_float(__ldg(r.e).y);
+  float4 acc = scale4(v0, ps), qacc = scale4(v0, qs);
+  gather_acc2<B>(r, a.f.p, a.q, ld, src0, acc, qacc);
+  float4 pn = leap(c, ps, pold, acc);
   if (s0 != s1) {
     const float sv = c.z * __ldg(a.f.wavelet + l);
     for (int q = s0; q < s1; ++q) {
@@ -191,14 +219,12 @@ __global__ void __launch_bounds__(kThreads) k_tangent(TangentArgs a) {
     }
   }
   // dp+ = alpha dp - beta dp- - gamma K dp - cm (p+ - 2p + p-) - cd (p+ - p-)
-#define MG_TAN(X)                                                              \
-  qn.X = c.x * qs.X - c.y * qold.X - c.z * qacc.X -                            \
-         tc.x * (pn.X - 2.0f * ps.X + pold.X) - tc.y * (pn.X - pold.X);
+  float4 qn = leap(c, qs, qold, qacc);
+#define MG_TAN(X) qn.X -= tc.x * ((pn.X - 2.0f * ps.X) + pold.X) + tc.y * (pn.X - pold.X);
   MG_TAN(x) MG_TAN(y) MG_TAN(z) MG_TAN(w)
 #undef MG_TAN
-  st4(a.f.pout + (size_t)row * ld + src0, pn);
-  st4(qmr, qn);
-  const int r0 = __ldg(a.f.ev.rec_ptr + row), r1 = __ldg(a.f.ev.rec_ptr + row + 1);
+  st4(a.f.pout + ro, pn);
+  st4(a.qm + ro, qn);
   for (int q = r0; q < r1; ++q) {
     const int d = __ldg(a.f.ev.rec_shot + q) - src0;
     if (d >= 0 && d < 4)
@@ -213,7 +239,7 @@ __device__ __forceinline__ void kahan_add(float* s, float* c, float term) {
   *s = t;
 }
 
-template <int LPR>
+template <int LPR, int B>
 __global__ void __launch_bounds__(kThreads) k_adjoint(AdjointArgs a) {
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31;
@@ -223,24 +249,23 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjointArgs a) {
   const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
   float t1 = 0.0f, t2 = 0.0f;
   if (valid) {
-    float4 self;
-    const float4 acc = stiff_gather(a.K, row, a.mu, a.ld, src0, self);
+    const size_t ro = (size_t)row * a.ld + src0;
+    const RowIn r = row_in(a.K, row);
+    const float4 self = ld4(a.mu + ro);
+    const float4 old = ld4v(a.mu1 + ro);  // mu_{k+1}
+    const float4 pk = ld4(a.pk + ro);
     const float4 c = __ldg(a.coef + row);
-    float* m1 = a.mu1 + (size_t)row * a.ld + src0;
-    const float4 old = ld4v(m1);  // mu_{k+1}
-    float4 out;
-    out.x = c.x * self.x - c.y * old.x - c.z * acc.x;
-    out.y = c.x * self.y - c.y * old.y - c.z * acc.y;
-    out.z = c.x * self.z - c.y * old.z - c.z * acc.z;
-    out.w = c.x * self.w - c.y * old.w - c.z * acc.w;
     const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
+    const int k = a.k + (a.step_base ? *a.step_base : 0);
+    float4 acc = scale4(__int_as_float(__ldg(r.e).y), self);
+    acc = gather_acc<B>(r, a.mu, a.ld, src0, acc);
+    float4 out = leap(c, self, old, acc);
     for (int q = r0; q < r1; ++q) {
       const int d = __ldg(a.ev.rec_shot + q) - src0;
       if (d >= 0 && d < 4)
-        add_comp(out, d, c.w * __ldg(a.w + (size_t)__ldg(a.ev.rec_trace + q) * a.nt + (a.k - 1)));
+        add_comp(out, d, c.w * __ldg(a.w + (size_t)__ldg(a.ev.rec_trace + q) * a.nt + (k - 1)));
     }
-    st4(m1, out);
-    const float4 pk = ld4(a.pk + (size_t)row * a.ld + src0);
+    st4(a.mu1 + ro, out);
 #define MG_ACC(X)                                                              \
   t1 = fmaf(pk.X, (out.X - 2.0f * self.X) + old.X, t1);                        \
   t2 = fmaf(pk.X, out.X - old.X, t2);
@@ -297,18 +322,19 @@ __global__ void k_tangent_coefs(TangentCoefArgs a) {
   a.tcoef[r] = t;
 }
 
+// max_i row_abs_i / m_i; positive doubles order like their bit patterns,
+// so blocks combine with an integer atomicMax (out zeroed beforehand).
 __global__ void k_cfl_reduce(int32_t n, const double* row_abs, const double* mass,
-                             double* out) {
-  __shared__ double sm[1024];
-  double mx = 0.0;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) mx = fmax(mx, row_abs[r] / mass[r]);
-  sm[threadIdx.x] = mx;
+                             unsigned long long* out) {
+  __shared__ double sm[256];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  sm[threadIdx.x] = r < n ? row_abs[r] / mass[r] : 0.0;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if ((int)threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sm[0];
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sm[0]));
 }
 
 __device__ __forceinline__ double total(const float* s, const float* c, int n,
@@ -351,6 +377,7 @@ __global__ void k_d2f(const double* in, float* out, int64_t n) {
 }
 
 __global__ void k_add_int(int32_t* p, int32_t v) { *p += v; }
+__global__ void k_set_int(int32_t* p, int32_t v) { *p = v; }
 
 __global__ void k_copy_f4(const float4* __restrict__ src, float4* __restrict__ dst,
                           int64_t n4) {
@@ -371,13 +398,12 @@ int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
   const int lpr = lpr_of(S_pad);
   const int rows_per_block = kWarps * (32 / lpr);
   dim3 grid((a.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
-  switch (lpr) {
-    case 32: k_step<32><<<grid, kThreads, 0, st>>>(a); break;
-    case 16: k_step<16><<<grid, kThreads, 0, st>>>(a); break;
-    case 8: k_step<8><<<grid, kThreads, 0, st>>>(a); break;
-    case 4: k_step<4><<<grid, kThreads, 0, st>>>(a); break;
-    case 2: k_step<2><<<grid, kThreads, 0, st>>>(a); break;
-    case 1: k_step<1><<<grid, kThreads, 0, st>>>(a); break;
+  const int B = a.batch == 4 ? 4 : 8;
+  switch (lpr * 16 + B) {
+#define MG_CASE(L_, B_) case L_ * 16 + B_: k_step<L_, B_><<<grid, kThreads, 0, st>>>(a); break;
+    MG_CASE(32, 4) MG_CASE(32, 8) MG_CASE(16, 4) MG_CASE(16, 8) MG_CASE(8, 4) MG_CASE(8, 8)
+    MG_CASE(4, 4) MG_CASE(4, 8) MG_CASE(2, 4) MG_CASE(2, 8) MG_CASE(1, 4) MG_CASE(1, 8)
+#undef MG_CASE
     default: return MG_ERR_ARG;
   }
   return check_launch();
@@ -392,13 +418,12 @@ int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st) {
   const int lpr = lpr_of(S_pad);
   const int rows_per_block = kWarps * (32 / lpr);
   dim3 grid((a.f.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
-  switch (lpr) {
-    case 32: k_tangent<32><<<grid, kThreads, 0, st>>>(a); break;
-    case 16: k_tangent<16><<<grid, kThreads, 0, st>>>(a); break;
-    case 8: k_tangent<8><<<grid, kThreads, 0, st>>>(a); break;
-    case 4: k_tangent<4><<<grid, kThreads, 0, st>>>(a); break;
-    case 2: k_tangent<2><<<grid, kThreads, 0, st>>>(a); break;
-    case 1: k_tangent<1><<<grid, kThreads, 0, st>>>(a); break;
+  const int B = a.f.batch == 4 ? 4 : 8;
+  switch (lpr * 16 + B) {
+#define MG_CASE(L_, B_) case L_ * 16 + B_: k_tangent<L_, B_><<<grid, kThreads, 0, st>>>(a); break;
+    MG_CASE(32, 4) MG_CASE(32, 8) MG_CASE(16, 4) MG_CASE(16, 8) MG_CASE(8, 4) MG_CASE(8, 8)
+    MG_CASE(4, 4) MG_CASE(4, 8) MG_CASE(2, 4) MG_CASE(2, 8) MG_CASE(1, 4) MG_CASE(1, 8)
+#undef MG_CASE
     default: return MG_ERR_ARG;
   }
   return check_launch();
@@ -408,13 +433,12 @@ int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st) {
   const int lpr = lpr_of(S_pad);
   const int rows_per_block = kWarps * (32 / lpr);
   dim3 grid((a.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
-  switch (lpr) {
-    case 32: k_adjoint<32><<<grid, kThreads, 0, st>>>(a); break;
-    case 16: k_adjoint<16><<<grid, kThreads, 0, st>>>(a); break;
-    case 8: k_adjoint<8><<<grid, kThreads, 0, st>>>(a); break;
-    case 4: k_adjoint<4><<<grid, kThreads, 0, st>>>(a); break;
-    case 2: k_adjoint<2><<<grid, kThreads, 0, st>>>(a); break;
-    case 1: k_adjoint<1><<<grid, kThreads, 0, st>>>(a); break;
+  const int B = a.batch == 4 ? 4 : 8;
+  switch (lpr * 16 + B) {
+#define MG_CASE(L_, B_) case L_ * 16 + B_: k_adjoint<L_, B_><<<grid, kThreads, 0, st>>>(a); break;
+    MG_CASE(32, 4) MG_CASE(32, 8) MG_CASE(16, 4) MG_CASE(16, 8) MG_CASE(8, 4) MG_CASE(8, 8)
+    MG_CASE(4, 4) MG_CASE(4, 8) MG_CASE(2, 4) MG_CASE(2, 8) MG_CASE(1, 4) MG_CASE(1, 8)
+#undef MG_CASE
     default: return MG_ERR_ARG;
   }
   return check_launch();
@@ -432,7 +456,9 @@ int launch_tangent_coefs(const TangentCoefArgs& a, cudaStream_t st) {
 
 int launch_cfl_reduce(int32_t n, const double* row_abs, const double* mass,
                       double* out, cudaStream_t st) {
-  k_cfl_reduce<<<1, 1024, 0, st>>>(n, row_abs, mass, out);
+  if (cudaMemsetAsync(out, 0, sizeof(double), st) != cudaSuccess) return MG_ERR_CUDA;
+  k_cfl_reduce<<<(n + 255) / 256, 256, 0, st>>>(n, row_abs, mass,
+                                                 reinterpret_cast<unsigned long long*>(out));
   return check_launch();
 }
 
@@ -455,6 +481,11 @@ int launch_d2f(const double* in, float* out, int64_t n, cudaStream_t st) {
 
 int launch_add_int(int32_t* p, int32_t v, cudaStream_t st) {
   k_add_int<<<1, 1, 0, st>>>(p, v);
+  return check_launch();
+}
+
+int launch_set_int(int32_t* p, int32_t v, cudaStream_t st) {
+  k_set_int<<<1, 1, 0, st>>>(p, v);
   return check_launch();
 }
 

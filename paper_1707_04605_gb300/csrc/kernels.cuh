@@ -39,6 +39,7 @@ struct StepArgs {
   int32_t nt;
   int32_t step;             // l = step + (step_base ? *step_base : 0)
   const int32_t* step_base;
+  int32_t batch;            // stiffness entries gathered per batch (4 or 8)
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -63,7 +64,9 @@ struct AdjointArgs {
   int32_t ld;
   const float* w;           // [n_traces][nt] trace weights
   int32_t nt;
-  int32_t k;                // reverse step index (uses w[.][k-1])
+  int32_t k;                // reverse step index k + (step_base ? *step_base : 0)
+  const int32_t* step_base;
+  int32_t batch;
   float* G;                 // [tiles][n] sums
   float* Gc;                // compensations
   float* H;
@@ -127,6 +130,7 @@ int launch_restrict(int64_t nc, const int64_t* ptr, const int32_t* idx,
 // Small helpers.
 int launch_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
 int launch_add_int(int32_t* p, int32_t v, cudaStream_t st);
+int launch_set_int(int32_t* p, int32_t v, cudaStream_t st);
 int launch_copy_f4(const float* src, float* dst, int64_t n_floats, cudaStream_t st);
 
 }  // namespace mg

@@ -157,6 +157,26 @@ def test_adjoint_checkpoint_spacing_and_reuse(mg):
     assert np.array_equal(gh, g64.cpu().numpy())
 
 
+@pytest.mark.parametrize("chunk,batch", [(0, 8), (0, 4), (64, 4), (128, 8)])
+def test_launch_shapes_give_identical_results(mg, chunk, batch):
+    """Graph replay vs plain launches and both gather batch sizes: the same
+    arithmetic in the same order, so the same bits."""
+    w = configs.asteroid_2d(n_refine=1, S=20, nt=300)
+    eps, s = _dev(w.eps), None
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    v = _dev(np.random.default_rng(3).standard_normal(w.mesh.n_cells[1]))
+    W = _dev(np.random.default_rng(4).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    ref = (mg.forward(mesh, eps, w.shots, s, dt), mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+           mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+    mesh.set_tuning(chunk, batch)
+    out = (mg.forward(mesh, eps, w.shots, s, dt), mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+           mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+
+
 def test_jacobian_square_disc_2d(mg):
     """4225 nodes, 2000 steps: a level-1 column J e_j and J^T w vs oracle."""
     w = configs.square_disc_2d()
