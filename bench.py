@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed device steps (for profiler launch lists)")
+    ap.add_argument("--tile-rows", type=int, default=-1,
+                    help="rows per shared-memory tile (0 = untiled kernels)")
+    ap.add_argument("--src-tile", type=int, default=-1, help="shots per staged pass")
+    ap.add_argument("--chunk", type=int, default=-1, help="leapfrog steps per CUDA graph")
     return ap.parse_args()
 
 
@@ -223,6 +227,7 @@ def main():
 
     w = workload_for_rank(rank, args.nt)
     mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(args.chunk, -1, args.tile_rows, args.src_tile)
     n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
     eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)

@@ -186,13 +186,19 @@ int mg_jacobian_T_apply(mg_mesh* mesh, int level, const double* eps,
 int mg_mesh_trim(mg_mesh* mesh);
 
 /* Launch-shape tuning of a handle (no effect on results):
- *  chunk  leapfrog steps captured per CUDA graph; an even number >= 2, or 0
- *         for one plain launch per step.  Default 128.
- *  batch  stiffness entries whose neighbour rows are gathered together per
- *         row, 4 or 8.  Default 8.
- * Pass -1 to keep a value.  Drops the handle's cached graphs.
+ *  chunk      leapfrog steps captured per CUDA graph; an even number >= 2,
+ *             or 0 for one plain launch per step.  Default 128.
+ *  batch      untiled kernels: stiffness entries whose neighbour rows are
+ *             gathered together per row, 4 or 8.  Default 8.
+ *  tile_rows  rows per shared-memory tile (a multiple of 32, <= 8192), or 0
+ *             for the untiled kernels.  Default 0.  A tile stages its rows
+ *             and their off-tile neighbours once per step and source tile.
+ *  src_tile   shots staged per pass of a tile: 4, 8, 16, 32 or 64 (capped
+ *             by the padded shot count).  Default 32.
+ * A kernel whose tiled shared-memory footprint exceeds the device limit
+ * runs untiled.  Pass -1 to keep a value.  Drops the cached graphs.
  * Errors: MG_ERR_ARG for values outside these sets. */
-int mg_mesh_set_tuning(mg_mesh* mesh, int chunk, int batch);
+int mg_mesh_set_tuning(mg_mesh* mesh, int chunk, int batch, int tile_rows, int src_tile);
 
 /* Number of kernel launches the handle has issued so far (graph-launched
  * kernels counted per node).  Used to report launch counts. */

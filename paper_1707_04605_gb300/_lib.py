@@ -63,7 +63,7 @@ SIGNATURES = {
                                       C.c_void_p, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "mg_mesh_trim": (C.c_int, [C.c_void_p]),
-    "mg_mesh_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_mesh_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "mg_launch_count": (C.c_int64, [C.c_void_p]),
     "mg_strerror": (C.c_char_p, [C.c_int]),
     "mg_version": (C.c_int, []),

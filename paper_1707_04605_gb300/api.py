@@ -116,14 +116,18 @@ class Mesh:
     def launch_count(self) -> int:
         return int(self._lib.mg_launch_count(self.handle))
 
-    def set_tuning(self, chunk: int = -1, batch: int = -1):
-        """Graph chunk length (even, 0 = plain launches) and gather batch (4/8)."""
-        L.check(self._lib.mg_mesh_set_tuning(self.handle, int(chunk), int(batch)),
+    def set_tuning(self, chunk: int = -1, batch: int = -1, tile_rows: int = -1,
+                   src_tile: int = -1):
+        """Graph chunk length (even, 0 = plain launches), untiled gather batch
+        (4/8), shared-memory tile rows (multiple of 32, 0 = untiled) and shots
+        per staged pass (4..64); -1 keeps a value."""
+        L.check(self._lib.mg_mesh_set_tuning(self.handle, int(chunk), int(batch),
+                                             int(tile_rows), int(src_tile)),
                 "mg_mesh_set_tuning")
 
 
 def mesh_create(dim, coords, cells, cell_parent, n_cells_per_level, bnd, bc="abc",
-                order="rcm") -> Mesh:
+                order="morton") -> Mesh:
     lib = L.load()
     coords, pc = _host(coords, np.float64)
     cells, pcells = _host(cells, np.int32)
@@ -139,7 +143,7 @@ def mesh_create(dim, coords, cells, cell_parent, n_cells_per_level, bnd, bc="abc
     return Mesh(h, dim, ncl)
 
 
-def mesh_from_workload(w, order="rcm", bc=None) -> Mesh:
+def mesh_from_workload(w, order="morton", bc=None) -> Mesh:
     m = w.mesh
     return mesh_create(m.dim, m.coords, m.cells, m.cell_parent, m.n_cells, m.bnd,
                        bc or w.bc, order)

@@ -101,6 +101,14 @@ struct mg_mesh {
   // CUDA graphs of step chunks, keyed by kind, buffers and sizes
   int chunk = 128;                        // steps per graph (even), 0 = off
   int batch = 8;                          // stiffness entries per gather batch
+  // shared-memory row tiles (0 = untiled kernels)
+  int tile_rows = 0;
+  int src_tile = 32;
+  int tiles_P = 0;                        // P of the uploaded tile tables
+  Buf t_ell_off, t_ell_idx, t_ell_val, t_sinfo, t_halo_off, t_halo_cnt, t_halo;
+  int t_n_tiles = 0, t_max_ell = 0, t_max_halo = 0;
+  double t_ratio = 0.0;
+  int smem_optin = 0;
   cudaStream_t cap = nullptr;             // private capture stream
   std::map<std::string, cudaGraphExec_t> graphs;
   Buf tr;                                 // internal trace buffer [R][nt]
@@ -249,6 +257,8 @@ int cfl_lambda(mg_mesh* M, const double* eps_d, cudaStream_t st, double* lam) {
   return MG_OK;
 }
 
+int ensure_tiles(mg_mesh* M);
+
 // Common preparation of a propagation call: inputs on the device, per-row
 // coefficients, wavelet in FP32, event lists, dt check.
 struct Prep {
@@ -283,7 +293,73 @@ int prepare(mg_mesh* M, const double* eps, const mg_shots* shots, const double* 
   MG_TRY(mg::launch_d2f(pp.wav, P<float>(M->wavf), nt, st));
   M->launches += 2;
   MG_TRY(build_events(M, shots, pp.ev));
+  MG_TRY(ensure_tiles(M));
   return MG_OK;
+}
+
+// Tile tables for the current tile_rows, built on the host and uploaded on
+// first use.
+int ensure_tiles(mg_mesh* M) {
+  if (M->tile_rows <= 0 || M->tiles_P == M->tile_rows) return MG_OK;
+  mg::HostTiles T;
+  MG_TRY(mg::build_tiles(M->hm, M->tile_rows, T));
+  MG_TRY(upload(M->t_ell_off, T.ell_off));
+  MG_TRY(upload(M->t_ell_idx, T.ell_idx));
+  MG_TRY(upload(M->t_ell_val, T.ell_val));
+  MG_TRY(upload(M->t_sinfo, T.slice_info));
+  MG_TRY(upload(M->t_halo_off, T.halo_off));
+  MG_TRY(upload(M->t_halo_cnt, T.halo_cnt));
+  MG_TRY(upload(M->t_halo, T.halo));
+  M->t_n_tiles = (int)T.n_tiles;
+  M->t_max_ell = T.max_ell;
+  M->t_max_halo = T.max_halo;
+  M->t_ratio = T.halo_ratio;
+  M->tiles_P = M->tile_rows;
+  if (!M->smem_optin)
+    MG_CU(cudaDeviceGetAttribute(&M->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                 M->device));
+  return MG_OK;
+}
+
+// Tiled launch description for a padded shot count and kernel kind (0
+// forward, 1 tangent, 2 adjoint), or n_tiles = 0 when that kernel does not
+// fit in shared memory.  The tangent stages two states per pass, so it
+// passes half as many shots to stay within the one-state footprint.
+mg::DevTiles dev_tiles(mg_mesh* M, int S_pad, int kind) {
+  mg::DevTiles T{};
+  if (M->tile_rows <= 0 || M->tiles_P != M->tile_rows) return T;
+  T.P = M->tiles_P;
+  T.n_tiles = M->t_n_tiles;
+  T.ell_off = P<const int64_t>(M->t_ell_off);
+  T.ell_idx = P<const uint16_t>(M->t_ell_idx);
+  T.ell_val = P<const float>(M->t_ell_val);
+  T.slice_info = P<const int32_t>(M->t_sinfo);
+  T.halo_off = P<const int64_t>(M->t_halo_off);
+  T.halo_cnt = P<const int32_t>(M->t_halo_cnt);
+  T.halo = P<const int32_t>(M->t_halo);
+  T.max_ell = M->t_max_ell;
+  T.max_halo = M->t_max_halo;
+  T.st_w = std::min(M->src_tile, S_pad);
+  if (kind == 1) T.st_w = std::max(4, T.st_w / 2);
+  if (mg::tiled_smem_bytes(T, kind) > (size_t)M->smem_optin) T.n_tiles = 0;
+  return T;
+}
+
+int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
+  const mg::DevTiles T = dev_tiles(M, S_pad, 0);
+  return T.n_tiles ? mg::launch_step_tiled(a, T, st) : mg::launch_step(a, S_pad, st);
+}
+
+int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st) {
+  const mg::DevTiles T = dev_tiles(M, S_pad, 1);
+  return T.n_tiles ? mg::launch_tangent_tiled(a, T, st) : mg::launch_tangent(a, S_pad, st);
+}
+
+bool adjoint_tiled(mg_mesh* M, int S_pad) { return dev_tiles(M, S_pad, 2).n_tiles > 0; }
+
+int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st) {
+  const mg::DevTiles T = dev_tiles(M, S_pad, 2);
+  return T.n_tiles ? mg::launch_adjoint_tiled(a, T, st) : mg::launch_adjoint(a, S_pad, st);
 }
 
 mg::StepArgs step_args(mg_mesh* M, const Prep& pp, int ld, int nt) {
@@ -381,7 +457,7 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
           b.pm = y;
           b.pout = y;
           b.step = j;
-          MG_TRY(mg::launch_step(b, pp.S_pad, cs));
+          MG_TRY(do_step(M, b, pp.S_pad, cs));
           std::swap(x, y);
         }
         return mg::launch_add_int(base, C, cs);
@@ -399,7 +475,7 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
     a.pm = pm;
     a.pout = pm;
     a.step = l;
-    MG_TRY(mg::launch_step(a, pp.S_pad, st));
+    MG_TRY(do_step(M, a, pp.S_pad, st));
     M->launches += 1;
     std::swap(p, pm);
   }
@@ -498,10 +574,9 @@ int mg_mesh_create(int dim, int n_levels, const double* coords, int64_t n_nodes,
     mg_mesh_destroy(M);
     return rc;
   }
-  // free host copies not needed after upload
+  // the global ELL image is on the device now; (col, val) stay on the host
+  // for building row tiles on demand
   std::vector<mg::EllEntry>().swap(h.ell);
-  std::vector<int32_t>().swap(h.col);
-  std::vector<double>().swap(h.val);
   *out = M;
   return MG_OK;
 }
@@ -517,6 +592,10 @@ void mg_mesh_destroy(mg_mesh* M) {
   for (auto* v : {&M->anc, &M->lvl_ptr, &M->lvl_idx})
     for (Buf& b : *v)
       if (b.p) cudaFree(b.p);
+  Buf* tiles[] = {&M->t_ell_off, &M->t_ell_idx, &M->t_ell_val, &M->t_sinfo, &M->t_halo_off,
+                  &M->t_halo_cnt, &M->t_halo};
+  for (Buf* b : tiles)
+    if (b->p) cudaFree(b->p);
   mg_mesh_trim(M);
   if (M->cap) cudaStreamDestroy(M->cap);
   delete M;
@@ -541,15 +620,22 @@ int mg_mesh_trim(mg_mesh* M) {
   return MG_OK;
 }
 
-int mg_mesh_set_tuning(mg_mesh* M, int chunk, int batch) {
+int mg_mesh_set_tuning(mg_mesh* M, int chunk, int batch, int tile_rows, int src_tile) {
   if (!M) return MG_ERR_ARG;
   if (chunk != -1 && (chunk < 0 || chunk == 1 || chunk % 2 != 0 || chunk > 4096)) return MG_ERR_ARG;
   if (batch != -1 && batch != 4 && batch != 8) return MG_ERR_ARG;
+  if (tile_rows != -1 && (tile_rows < 0 || tile_rows % mg::kSliceH != 0 || tile_rows > 8192))
+    return MG_ERR_ARG;
+  if (src_tile != -1 && src_tile != 4 && src_tile != 8 && src_tile != 16 && src_tile != 32 &&
+      src_tile != 64)
+    return MG_ERR_ARG;
   DeviceGuard g(M->device);
   for (auto& kv : M->graphs) cudaGraphExecDestroy(kv.second);
   M->graphs.clear();
   if (chunk != -1) M->chunk = chunk;
   if (batch != -1) M->batch = batch;
+  if (tile_rows != -1) M->tile_rows = tile_rows;
+  if (src_tile != -1) M->src_tile = src_tile;
   return MG_OK;
 }
 
@@ -695,7 +781,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
           b.q = u;
           b.qm = z;
           b.f.step = j;
-          MG_TRY(mg::launch_tangent(b, pp.S_pad, cs));
+          MG_TRY(do_tangent(M, b, pp.S_pad, cs));
           std::swap(x, y);
           std::swap(u, z);
         }
@@ -710,7 +796,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
     a.q = q;
     a.qm = qm;
     a.f.step = l;
-    MG_TRY(mg::launch_tangent(a, pp.S_pad, st));
+    MG_TRY(do_tangent(M, a, pp.S_pad, st));
     M->launches += 1;
     std::swap(p, pm);
     std::swap(q, qm);
@@ -762,7 +848,10 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   float* mu1 = P<float>(M->stD);
   MG_CU(cudaMemsetAsync(mu, 0, state * sizeof(float), st));
   MG_CU(cudaMemsetAsync(mu1, 0, state * sizeof(float), st));
-  const size_t acc = (size_t)pp.tiles * n;
+  // accumulators: one set per source tile of the untiled kernel; the tiled
+  // kernel sums all shots of a row inside its CTA
+  const int acc_sets = adjoint_tiled(M, pp.S_pad) ? 1 : pp.tiles;
+  const size_t acc = (size_t)acc_sets * n;
   MG_TRY(ensure(M->G, 4 * acc * sizeof(float)));
   MG_CU(cudaMemsetAsync(M->G.p, 0, 4 * acc * sizeof(float), st));
   float* G = P<float>(M->G);
@@ -808,7 +897,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
           b.pm = seg + (size_t)(j - 1) * state;
           b.pout = seg + (size_t)(j + 1) * state;
           b.step = j - 1;
-          MG_TRY(mg::launch_step(b, pp.S_pad, cs));
+          MG_TRY(do_step(M, b, pp.S_pad, cs));
         }
         return MG_OK;
       }));
@@ -824,7 +913,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
           b.mu1 = y;
           b.pk = seg + (size_t)(r + 1) * state;
           b.k = r;
-          MG_TRY(mg::launch_adjoint(b, pp.S_pad, cs));
+          MG_TRY(do_adjoint(M, b, pp.S_pad, cs));
           std::swap(x, y);
         }
         return MG_OK;
@@ -837,7 +926,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       fa.pm = seg + (size_t)(j - 1) * state;
       fa.pout = seg + (size_t)(j + 1) * state;
       fa.step = l;
-      MG_TRY(mg::launch_step(fa, pp.S_pad, st));
+      MG_TRY(do_step(M, fa, pp.S_pad, st));
       M->launches += 1;
     }
     for (int k = l1; k > l0; --k) {
@@ -845,7 +934,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       aa.mu1 = mu1;
       aa.pk = seg + (size_t)(k - l0 + 1) * state;
       aa.k = k;
-      MG_TRY(mg::launch_adjoint(aa, pp.S_pad, st));
+      MG_TRY(do_adjoint(M, aa, pp.S_pad, st));
       M->launches += 1;
       std::swap(mu, mu1);
     }
@@ -866,7 +955,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   ga.dt = dt;
   ga.bc = M->hm.bc;
   ga.n = (int32_t)n;
-  ga.tiles = pp.tiles;
+  ga.tiles = acc_sets;
   ga.G = aa.G; ga.Gc = aa.Gc; ga.H = aa.H; ga.Hc = aa.Hc;
   ga.g_fine = P<double>(M->gfine);
   MG_TRY(mg::launch_cell_gradient(ga, st));

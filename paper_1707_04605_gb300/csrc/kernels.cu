@@ -14,37 +14,12 @@
 #include "../../include/mgwave.h"
 #include "kernels.cuh"
 #include "mg_internal.h"
+#include "device_util.cuh"
 
 namespace mg {
 namespace {
 
-constexpr int kWarps = 8;            // warps per block of the batched kernels
-constexpr int kThreads = 32 * kWarps;
-constexpr int kTile = 128;           // shots per source tile
-
-__device__ __forceinline__ float4 ld4(const float* p) {
-  return __ldg(reinterpret_cast<const float4*>(p));
-}
-__device__ __forceinline__ float4 ld4v(const float* p) {
-  return *reinterpret_cast<const float4*>(p);
-}
-__device__ __forceinline__ void st4(float* p, float4 v) {
-  *reinterpret_cast<float4*>(p) = v;
-}
-__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z),
-                     fmaf(a, x.w, y.w));
-}
-// Component d (0..3) of a float4 without dynamic register indexing.
-__device__ __forceinline__ void add_comp(float4& v, int d, float x) {
-  v.x += d == 0 ? x : 0.0f;
-  v.y += d == 1 ? x : 0.0f;
-  v.z += d == 2 ? x : 0.0f;
-  v.w += d == 3 ? x : 0.0f;
-}
-__device__ __forceinline__ float get_comp(const float4& v, int d) {
-  return d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w;
-}
+using namespace dev;
 
 // Row prologue: every load that depends only on the row index is issued
 // before the first dependent one, so a row costs three memory round trips
@@ -107,20 +82,6 @@ __device__ __forceinline__ void gather_acc2(RowIn r, const float* __restrict__ p
       qacc = fma4(__int_as_float(ek[j].y), y[j], qacc);
     }
   }
-}
-
-__device__ __forceinline__ float4 scale4(float a, float4 x) {
-  return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
-}
-
-// out = alpha self - beta old - gamma acc
-__device__ __forceinline__ float4 leap(float4 c, float4 self, float4 old, float4 acc) {
-  float4 o;
-  o.x = c.x * self.x - c.y * old.x - c.z * acc.x;
-  o.y = c.x * self.y - c.y * old.y - c.z * acc.y;
-  o.z = c.x * self.z - c.y * old.z - c.z * acc.z;
-  o.w = c.x * self.w - c.y * old.w - c.z * acc.w;
-  return o;
 }
 
 template <int LPR, int B>
@@ -230,13 +191,6 @@ __global__ void __launch_bounds__(kThreads) k_tangent(TangentArgs a) {
     if (d >= 0 && d < 4)
       a.dtraces[(size_t)__ldg(a.f.ev.rec_trace + q) * a.f.nt + l] = get_comp(qn, d);
   }
-}
-
-__device__ __forceinline__ void kahan_add(float* s, float* c, float term) {
-  const float y = term - *c;
-  const float t = *s + y;
-  *c = (t - *s) - y;
-  *s = t;
 }
 
 template <int LPR, int B>
@@ -386,9 +340,6 @@ __global__ void k_copy_f4(const float4* __restrict__ src, float4* __restrict__ d
     dst[i] = src[i];
 }
 
-int check_launch() {
-  return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
-}
 
 int lpr_of(int S_pad) { return S_pad >= kTile ? 32 : S_pad / 4; }
 

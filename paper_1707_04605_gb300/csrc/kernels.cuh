@@ -73,6 +73,32 @@ struct AdjointArgs {
   float* Hc;
 };
 
+// Row tiles staged in shared memory (see HostTiles): tile t owns rows
+// [t*P, t*P+P); its rows plus its halo rows are copied per source tile of
+// `st_w` shots into shared memory and every neighbour read of the step is
+// served from there through 16-bit local indices.
+struct DevTiles {
+  int32_t P;
+  int32_t n_tiles;
+  const int64_t* ell_off;
+  const uint16_t* ell_idx;
+  const float* ell_val;
+  const int32_t* slice_info;  // {offset within tile, width} per global slice
+  const int64_t* halo_off;
+  const int32_t* halo_cnt;
+  const int32_t* halo;
+  int32_t max_ell;
+  int32_t max_halo;
+  int32_t st_w;               // shots per source tile (4..64, divides ld)
+};
+
+// Shared memory bytes of a tiled launch: kind 0 forward, 1 tangent, 2 adjoint.
+size_t tiled_smem_bytes(const DevTiles& T, int kind);
+
+int launch_step_tiled(const StepArgs& a, const DevTiles& T, cudaStream_t st);
+int launch_tangent_tiled(const TangentArgs& a, const DevTiles& T, cudaStream_t st);
+int launch_adjoint_tiled(const AdjointArgs& a, const DevTiles& T, cudaStream_t st);
+
 int launch_step(const StepArgs& a, int S_pad, cudaStream_t st);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);
 int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st);

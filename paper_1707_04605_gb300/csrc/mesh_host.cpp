@@ -448,6 +448,88 @@ int build_host_mesh(int dim, int n_levels, const double* coords, int64_t n_nodes
   return MG_OK;
 }
 
+int build_tiles(const HostMesh& hm, int P, HostTiles& T) {
+  if (P <= 0 || P % kSliceH != 0 || P > 8192) return MG_ERR_ARG;
+  const int64_t n = hm.n;
+  T.P = P;
+  T.n_tiles = (n + P - 1) / P;
+  const int64_t spt = P / kSliceH;  // slices per tile
+  T.ell_off.assign(T.n_tiles + 1, 0);
+  T.halo_off.assign(T.n_tiles + 1, 0);
+  T.halo_cnt.assign(T.n_tiles, 0);
+  T.slice_info.assign(2 * hm.n_slices, 0);
+  std::vector<std::vector<int32_t>> halos(T.n_tiles);
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+  for (int64_t t = 0; t < T.n_tiles; ++t) {
+    const int64_t r0 = t * P, r1 = std::min<int64_t>(n, r0 + P);
+    auto& h = halos[t];
+    for (int64_t r = r0; r < r1; ++r)
+      for (int64_t q = hm.rowptr[r]; q < hm.rowptr[r + 1]; ++q)
+        if (hm.col[q] < r0 || hm.col[q] >= r1) h.push_back(hm.col[q]);
+    std::sort(h.begin(), h.end());
+    h.erase(std::unique(h.begin(), h.end()), h.end());
+    if ((int64_t)P + (int64_t)h.size() > 65535) bad++;
+  }
+  if (bad) return MG_ERR_ARG;
+  int64_t total_rows = 0;
+  for (int64_t t = 0; t < T.n_tiles; ++t) {
+    const int64_t r0 = t * P, r1 = std::min<int64_t>(n, r0 + P);
+    T.halo_cnt[t] = (int32_t)halos[t].size();
+    T.halo_off[t + 1] = T.halo_off[t] + (halos[t].size() + 3) / 4 * 4;
+    int64_t e = 0;
+    for (int64_t s = t * spt; s < std::min<int64_t>(hm.n_slices, (t + 1) * spt); ++s) {
+      T.slice_info[2 * s] = (int32_t)e;
+      T.slice_info[2 * s + 1] = hm.slice_w[s];
+      e += (int64_t)hm.slice_w[s] * kSliceH;
+    }
+    e = (e + 7) / 8 * 8;
+    T.ell_off[t + 1] = T.ell_off[t] + e;
+    T.max_ell = std::max<int>(T.max_ell, (int)e);
+    T.max_halo = std::max<int>(T.max_halo, (int)(T.halo_off[t + 1] - T.halo_off[t]));
+    total_rows += (r1 - r0) + (int64_t)halos[t].size();
+  }
+  T.halo_ratio = (double)total_rows / (double)n;
+  T.halo.assign(T.halo_off[T.n_tiles], 0);
+  T.ell_idx.assign(T.ell_off[T.n_tiles], 0);
+  T.ell_val.assign(T.ell_off[T.n_tiles], 0.0f);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t t = 0; t < T.n_tiles; ++t) {
+    const int64_t r0 = t * P, r1 = std::min<int64_t>(n, r0 + P);
+    const auto& h = halos[t];
+    std::copy(h.begin(), h.end(), T.halo.begin() + T.halo_off[t]);
+    // halo rows follow the tile's own rows (r1 - r0 of them; fewer than P
+    // in the last tile), matching the order in which they are staged
+    auto local = [&](int32_t c) -> uint16_t {
+      if (c >= r0 && c < r1) return (uint16_t)(c - r0);
+      return (uint16_t)((r1 - r0) + (std::lower_bound(h.begin(), h.end(), c) - h.begin()));
+    };
+    for (int64_t s = t * spt; s < std::min<int64_t>(hm.n_slices, (t + 1) * spt); ++s) {
+      const int w = hm.slice_w[s];
+      const int64_t base = T.ell_off[t] + T.slice_info[2 * s];
+      for (int rl = 0; rl < kSliceH; ++rl) {
+        const int64_t r = s * kSliceH + rl;
+        const int64_t vr = std::min<int64_t>(r, r1 - 1);  // padding rows point at a valid row
+        const int64_t nz = r < r1 ? hm.rowptr[r + 1] - hm.rowptr[r] : 0;
+        for (int k = 0; k < w; ++k) {
+          uint16_t li;
+          float v;
+          if (k < nz) {
+            li = local(hm.col[hm.rowptr[r] + k]);
+            v = (float)hm.val[hm.rowptr[r] + k];
+          } else {
+            li = (uint16_t)(vr - r0);
+            v = 0.0f;
+          }
+          T.ell_idx[base + (int64_t)k * kSliceH + rl] = li;
+          T.ell_val[base + (int64_t)k * kSliceH + rl] = v;
+        }
+      }
+    }
+  }
+  return MG_OK;
+}
+
 void level_children(const HostMesh& hm, int level, std::vector<int64_t>& ptr,
                     std::vector<int32_t>& idx) {
   const auto& anc = hm.ancestors[level];

@@ -79,4 +79,31 @@ int build_host_mesh(int dim, int n_levels, const double* coords, int64_t n_nodes
 void level_children(const HostMesh& hm, int level, std::vector<int64_t>& ptr,
                     std::vector<int32_t>& idx);
 
+// Row tiles for shared-memory staging.  Tile t owns rows [t*P, t*P + P) (P a
+// multiple of kSliceH).  Its halo is the sorted list of rows outside that
+// range that its stiffness rows reference.  The tile's stiffness entries are
+// re-indexed locally: index i < P_t is row t*P + i, index P_t + h is halo
+// row h, where P_t = min(P, n - t*P) is the tile's own row count.
+// Per tile, the entries of its slices are stored contiguously (same
+// column-major slice layout as the global ELL), padded to a multiple of 8
+// entries so that 16-byte copies can stage them.
+struct HostTiles {
+  int P = 0;
+  int64_t n_tiles = 0;
+  std::vector<int64_t> ell_off;     // [n_tiles+1] entry offset of each tile
+  std::vector<uint16_t> ell_idx;    // local indices
+  std::vector<float> ell_val;
+  std::vector<int32_t> slice_info;  // [n_slices][2]: {offset within tile, width}
+  std::vector<int64_t> halo_off;    // [n_tiles+1], padded to multiples of 4
+  std::vector<int32_t> halo_cnt;    // [n_tiles] real halo sizes
+  std::vector<int32_t> halo;        // global rows
+  int max_ell = 0;                  // max entries of a tile (padded)
+  int max_halo = 0;                 // max halo rows of a tile (padded)
+  double halo_ratio = 0.0;          // (sum of tile rows + halo rows) / n
+};
+
+// Returns MG_ERR_ARG if P is not a positive multiple of kSliceH or a tile's
+// local index space (P + halo) does not fit 16 bits.
+int build_tiles(const HostMesh& hm, int P, HostTiles& out);
+
 }  // namespace mg

@@ -157,24 +157,34 @@ def test_adjoint_checkpoint_spacing_and_reuse(mg):
     assert np.array_equal(gh, g64.cpu().numpy())
 
 
-@pytest.mark.parametrize("chunk,batch", [(0, 8), (0, 4), (64, 4), (128, 8)])
-def test_launch_shapes_give_identical_results(mg, chunk, batch):
-    """Graph replay vs plain launches and both gather batch sizes: the same
-    arithmetic in the same order, so the same bits."""
-    w = configs.asteroid_2d(n_refine=1, S=20, nt=300)
-    eps, s = _dev(w.eps), None
+@pytest.mark.parametrize("chunk,batch,tile_rows,src_tile", [
+    (0, 8, 0, 32), (0, 4, 0, 32), (128, 8, 0, 32), (64, 4, 256, 16), (128, 8, 128, 64),
+    (128, 8, 64, 8), (0, 8, 512, 4)])
+def test_launch_shapes_give_identical_results(mg, chunk, batch, tile_rows, src_tile):
+    """Graph replay vs plain launches, gather batches, shared-memory tiles of
+    several sizes (including a ragged last tile) vs the untiled kernels: the
+    forward and tangent steps do the same arithmetic in the same order, so
+    the same bits; the adjoint's per-row sum over shots is grouped by the
+    staged pass, so it agrees to FP32 rounding."""
+    w = configs.asteroid_2d(n_refine=1, S=100, nt=300)
+    eps = _dev(w.eps)
     mesh = mg.mesh_from_workload(w)
     dt = oracle_dt(w)
     s = _dev(w.wavelet(dt))
     v = _dev(np.random.default_rng(3).standard_normal(w.mesh.n_cells[1]))
     W = _dev(np.random.default_rng(4).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
-    ref = (mg.forward(mesh, eps, w.shots, s, dt), mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
-           mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
-    mesh.set_tuning(chunk, batch)
-    out = (mg.forward(mesh, eps, w.shots, s, dt), mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
-           mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
-    for a, b in zip(ref, out):
-        assert torch.equal(a, b)
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    mesh.set_tuning(chunk, batch, tile_rows, src_tile)
+    out = run()
+    assert torch.equal(ref[0], out[0])
+    assert torch.equal(ref[1], out[1])
+    assert rel_l2(out[2].cpu().numpy(), ref[2].cpu().numpy()) < 1e-5
 
 
 def test_jacobian_square_disc_2d(mg):
