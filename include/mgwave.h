@@ -160,6 +160,37 @@ int mg_forward(mg_mesh* mesh, const double* eps, const mg_shots* shots,
                const double* wavelet, double dt, int nt, float* traces,
                int ckpt_every, void* stream, int flags);
 
+/* Forward traces without any allocation (the paper has no counterpart; this
+ * is a service for callers that cannot let a library allocate).  Callers
+ * that hand the whole device to their own memory pool, that must not pay
+ * the implicit synchronisation of cudaMalloc/cudaFree inside a
+ * latency-critical loop, or that need the call's memory footprint fixed in
+ * advance can use it instead of mg_forward.  It computes the same traces as
+ * mg_forward (same step kernel, same arithmetic) for device pointers only.
+ *
+ * All scratch (node order, per-row source/receiver lists, coefficients,
+ * FP32 wavelet, two state buffers) lives in one file-scope device array of
+ * 64 MiB that every GPU loading the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree, graph instantiation or other allocating
+ * routine, on the device or the host.
+ *  - Size limit: 8 * n_nodes * S_pad + 44 * n_nodes + 4 * nt + 16 * shots
+ *    + 12 * receivers bytes, plus up to 255 bytes of alignment for each of
+ *    its 14 parts (S_pad = shot count rounded up to a power of two >= 4, or
+ *    to a multiple of 128 above 128), must fit in 64 MiB; larger work
+ *    returns MG_ERR_ARG before anything runs.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture is started.
+ *  - Every call on a device shares the one array, which keeps the previous
+ *    call's contents (the call clears what must start at zero).  Calls whose
+ *    work overlaps on the GPU (other streams, other threads, other handles)
+ *    race on it: serialise them.
+ *  - flags: 0 or MG_ALLOW_CFL; anything else returns MG_ERR_UNSUPPORTED.
+ *  - eps, wavelet, traces: device pointers as in mg_forward; shots: host. */
+int mg_forward_noalloc(mg_mesh* mesh, const double* eps, const mg_shots* shots,
+                       const double* wavelet, double dt, int nt, float* traces,
+                       void* stream, int flags);
+
 /* Tangent: jv = J v, the derivative of the traces in the direction
  * eps_fine = eps + t * v[anc_level(e)] (Eqs. (aku_ankka), (linearized1)-
  * (linearized2), exact for the lumped scheme).

@@ -56,6 +56,8 @@ SIGNATURES = {
                             C.POINTER(C.c_double)]),
     "mg_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mg_shots), C.c_void_p,
                              C.c_double, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "mg_forward_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mg_shots), C.c_void_p,
+                                     C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_jacobian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(mg_shots),
                                     C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int]),

@@ -15,6 +15,7 @@
 #include "../../include/mgwave.h"
 #include "kernels.cuh"
 #include "mg_internal.h"
+#include "mesh_view.h"
 
 namespace {
 
@@ -968,3 +969,23 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
 }
 
 }  // extern "C"
+
+namespace mg {
+
+int mesh_view(mg_mesh* M, MeshView* v) {
+  if (!M || !v) return MG_ERR_ARG;
+  v->device = M->device;
+  v->bc = M->hm.bc;
+  v->n = M->hm.n;
+  v->m = M->hm.m;
+  v->K = dev_ell(M);
+  v->coef_base = coef_args(M, nullptr, 0.0);
+  v->coef_base.coef = nullptr;
+  v->row_abs = P<const double>(M->row_abs);
+  v->perm_host = M->hm.perm.data();
+  v->launches = &M->launches;
+  v->batch = M->batch;
+  return MG_OK;
+}
+
+}  // namespace mg
