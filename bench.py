@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="override the step count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-leg", action="store_true",
+                    help="skip the 3D ellipsoid forward measurement")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed device steps (for profiler launch lists)")
     ap.add_argument("--tile-rows", type=int, default=-1,
@@ -134,6 +136,44 @@ def peaks():
     except Exception:
         pass
     return 6800.0, "fallback"
+
+
+def hbm_leg(mg, torch, dev, nt=300):
+    """The 3D ellipsoid workload (1,814,385 nodes, 64 shots; each state is
+    464 MB, far beyond L2): the batched forward step over `nt` leapfrog steps,
+    where the step kernel is bound by HBM bandwidth."""
+    w = configs.ellipsoid_3d(nt=nt)
+    mesh = mg.mesh_from_workload(w)
+    eps = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
+    dt = w.cfl_fraction * mg.cfl_dt(mesh, eps)
+    wav = torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
+    mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    mg.forward(mesh, eps, w.shots, wav, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    n, S = w.n_nodes, w.shots.n_shots
+    info = mesh.info()
+    S_pad = 64
+    bytes_step = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
+    peak, kind = peaks()
+    achieved = bytes_step / (s / nt) / 1e9
+    mesh.close()
+    return {"workload": f"ellipsoid_3d: {n} nodes, {w.mesh.cells.shape[0]} tets, {S} "
+                        f"backscatter shots, {nt} steps (forward only)",
+            "forward_updates_per_s": n * S * nt / s, "us_per_leapfrog_step": 1e6 * s / nt,
+            "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind_note(kind),
+                         "algorithmic_bytes_per_launch": bytes_step, "traffic": None}}
+
+
+def peak_kind_note(kind):
+    return "of measured" if kind == "measured" else "of fallback"
 
 
 def cpu_baseline(w, dt, budget_s=20.0):
@@ -368,6 +408,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if not args.no_hbm_leg:
+        out["hbm_workload"] = hbm_leg(mg, torch, dev)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, dt)
     print(json.dumps(out))

@@ -213,14 +213,39 @@ int mg_jacobian_T_apply(mg_mesh* mesh, int level, const double* eps,
                         int nt, const float* w, double* g, int ckpt_every,
                         void* stream, int flags);
 
+/* Uneven batches: n_inst independent problems, each with its own handle
+ * (distinct handles, one device), permittivity, shot batch, wavelet and dt,
+ * all with the same step count nt, advanced by ONE kernel launch per
+ * leapfrog step over a work list of (instance, row block, source tile)
+ * items.  Instance i computes exactly what mg_forward /
+ * mg_jacobian_T_apply would compute for it alone.
+ *  meshes, eps, wavelets, traces, w, g: arrays of n_inst pointers (host
+ *  arrays; the pointed-to data are device pointers, or host pointers with
+ *  MG_HOST_PTRS); shots, dts, levels: host arrays of n_inst entries.
+ *  flags: MG_HOST_PTRS and/or MG_ALLOW_CFL.
+ * Errors: MG_ERR_ARG (repeated handle, null entry), MG_ERR_UNSUPPORTED
+ * (handles on different devices, other flags), plus the per-instance errors
+ * of mg_forward. */
+int mg_forward_batch(int n_inst, mg_mesh* const* meshes, const double* const* eps,
+                     const mg_shots* shots, const double* const* wavelets, const double* dts,
+                     int nt, float* const* traces, void* stream, int flags);
+
+int mg_jacobian_T_apply_batch(int n_inst, mg_mesh* const* meshes, const int* levels,
+                              const double* const* eps, const mg_shots* shots,
+                              const double* const* wavelets, const double* dts, int nt,
+                              const float* const* w, double* const* g, int ckpt_every,
+                              void* stream, int flags);
+
 /* Release the handle's scratch (states, checkpoints, graphs). */
 int mg_mesh_trim(mg_mesh* mesh);
 
 /* Launch-shape tuning of a handle (no effect on results):
  *  chunk      leapfrog steps captured per CUDA graph; an even number >= 2,
  *             or 0 for one plain launch per step.  Default 128.
- *  batch      untiled kernels: stiffness entries whose neighbour rows are
- *             gathered together per row, 4 or 8.  Default 8.
+ *  batch      untiled kernels: float4 vectors (4 shots each) carried per
+ *             lane, 1, 2 or 4.  Default 1.  More vectors share each row's
+ *             stiffness loads among more shots and keep more neighbour
+ *             loads in flight per lane.
  *  tile_rows  rows per shared-memory tile (a multiple of 32, <= 8192), or 0
  *             for the untiled kernels.  Default 0.  A tile stages its rows
  *             and their off-tile neighbours once per step and source tile.

@@ -65,24 +65,21 @@ def lumped_mass(coords, cells, eps) -> np.ndarray:
 def facet_owner(cells: np.ndarray, bnd: np.ndarray) -> np.ndarray:
     """Index of the cell that owns each boundary facet."""
     m, k = cells.shape
-    n = int(cells.max()) + 1
-    assert float(n) ** (k - 1) < 2.0 ** 62, "facet key would overflow int64"
-
-    def key(f):
-        f = np.sort(f.astype(np.int64), axis=1)
-        out = f[:, 0]
-        for j in range(1, f.shape[1]):
-            out = out * n + f[:, j]
-        return out
-
-    faces = np.concatenate([np.delete(cells, j, axis=1) for j in range(k)])
-    fkey = key(faces)
+    faces = np.sort(np.concatenate([np.delete(cells, j, axis=1) for j in range(k)]), axis=1)
     fcell = np.tile(np.arange(m, dtype=np.int64), k)
-    order = np.argsort(fkey, kind="stable")
-    bkey = key(np.asarray(bnd))
-    pos = np.searchsorted(fkey[order], bkey)
-    assert np.all(fkey[order][pos] == bkey), "boundary facet is not a cell facet"
-    return fcell[order][pos]
+    bs = np.sort(np.asarray(bnd, dtype=faces.dtype), axis=1)
+    nf, nb = faces.shape[0], bs.shape[0]
+    allk = np.concatenate([faces, bs])
+    tag = np.concatenate([np.zeros(nf, np.int8), np.ones(nb, np.int8)])
+    # lexicographic order of the vertex triples (pairs in 2D); a boundary
+    # facet sorts right after the one cell facet with the same vertices
+    order = np.lexsort((tag,) + tuple(allk[:, j] for j in range(k - 2, -1, -1)))
+    pos_sorted = np.empty(nf + nb, dtype=np.int64)
+    pos_sorted[order] = np.arange(nf + nb)
+    pb = pos_sorted[nf:]
+    prev = order[pb - 1]
+    assert np.all(prev < nf) and np.all(allk[prev] == bs), "boundary facet is not a cell facet"
+    return fcell[prev]
 
 
 def facet_measure(coords: np.ndarray, bnd: np.ndarray) -> np.ndarray:

@@ -5,8 +5,9 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/mgwave.h``); this package only marshals arguments to it.
 """
 from . import _lib  # noqa: F401
-from .api import (Mesh, Shots, cfl_dt, forward, jacobian_T_apply,  # noqa: F401
-                  jacobian_apply, mesh_create, mesh_from_workload)
+from .api import (Mesh, Shots, cfl_dt, forward, forward_batch,  # noqa: F401
+                  jacobian_T_apply, jacobian_T_apply_batch, jacobian_apply, mesh_create,
+                  mesh_from_workload)
 
 __all__ = ["Mesh", "Shots", "mesh_create", "mesh_from_workload", "cfl_dt", "forward",
-           "jacobian_apply", "jacobian_T_apply"]
+           "jacobian_apply", "jacobian_T_apply", "forward_batch", "jacobian_T_apply_batch"]

@@ -64,6 +64,13 @@ SIGNATURES = {
     "mg_jacobian_T_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(mg_shots),
                                       C.c_void_p, C.c_double, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "mg_forward_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(mg_shots),
+                                   C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_int]),
+    "mg_jacobian_T_apply_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.POINTER(mg_shots), C.c_void_p, C.c_void_p,
+                                            C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                            C.c_void_p, C.c_int]),
     "mg_mesh_trim": (C.c_int, [C.c_void_p]),
     "mg_mesh_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "mg_launch_count": (C.c_int64, [C.c_void_p]),

@@ -242,3 +242,68 @@ def jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, w, nt=None, *,
                                  nt, pwt, _ptr(out), int(ckpt_every), st, f)
     L.check(rc, "mg_jacobian_T_apply")
     return out
+
+
+def _ptr_array(xs):
+    return (C.c_void_p * len(xs))(*[C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr")
+                                               else x.ctypes.data) for x in xs])
+
+
+def forward_batch(meshes, eps, shots, wavelets, dts, nt=None, *, allow_cfl=False, stream=None):
+    """Traces of several independent problems, one launch per step for all
+    (mg_forward_batch).  Returns a list of [n_traces_i, nt] arrays."""
+    lib = L.load()
+    n = len(meshes)
+    sh = [Shots.of(s) for s in shots]
+    nt = int(len(wavelets[0]) if nt is None else nt)
+    dev = _is_cuda(eps[0])
+    if dev:
+        ex = [_dev(e, "float64")[0] for e in eps]
+        wv = [_dev(x, "float64")[0] for x in wavelets]
+        st, f = _stream_ptr(stream), 0
+    else:
+        ex = [_host(e, np.float64)[0] for e in eps]
+        wv = [_host(x, np.float64)[0] for x in wavelets]
+        st, f = None, L.MG_HOST_PTRS
+    outs = [_alloc(dev, (s.n_traces, nt), "float32", ex[0]) for s in sh]
+    shot_arr = (L.mg_shots * n)(*[s.c for s in sh])
+    handles = (C.c_void_p * n)(*[m.handle for m in meshes])
+    dts_arr = np.ascontiguousarray(dts, dtype=np.float64)
+    rc = lib.mg_forward_batch(n, handles, _ptr_array(ex), shot_arr, _ptr_array(wv),
+                              C.c_void_p(dts_arr.ctypes.data), nt, _ptr_array(outs), st,
+                              f | (L.MG_ALLOW_CFL if allow_cfl else 0))
+    L.check(rc, "mg_forward_batch")
+    return outs
+
+
+def jacobian_T_apply_batch(meshes, levels, eps, shots, wavelets, dts, w, nt=None, *,
+                           ckpt_every=256, allow_cfl=False, stream=None):
+    """J^T w of several independent problems, batched (mg_jacobian_T_apply_batch).
+    Returns a list of per-instance level-cell gradients (float64)."""
+    lib = L.load()
+    n = len(meshes)
+    sh = [Shots.of(s) for s in shots]
+    nt = int(len(wavelets[0]) if nt is None else nt)
+    dev = _is_cuda(eps[0])
+    if dev:
+        ex = [_dev(e, "float64")[0] for e in eps]
+        wv = [_dev(x, "float64")[0] for x in wavelets]
+        ww = [_dev(x, "float32")[0] for x in w]
+        st, f = _stream_ptr(stream), 0
+    else:
+        ex = [_host(e, np.float64)[0] for e in eps]
+        wv = [_host(x, np.float64)[0] for x in wavelets]
+        ww = [_host(x, np.float32)[0] for x in w]
+        st, f = None, L.MG_HOST_PTRS
+    outs = [_alloc(dev, (m.n_cells_per_level[lv],), "float64", ex[0])
+            for m, lv in zip(meshes, levels)]
+    shot_arr = (L.mg_shots * n)(*[s.c for s in sh])
+    handles = (C.c_void_p * n)(*[m.handle for m in meshes])
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    dts_arr = np.ascontiguousarray(dts, dtype=np.float64)
+    rc = lib.mg_jacobian_T_apply_batch(n, handles, C.c_void_p(lv.ctypes.data), _ptr_array(ex),
+                                       shot_arr, _ptr_array(wv), C.c_void_p(dts_arr.ctypes.data),
+                                       nt, _ptr_array(ww), _ptr_array(outs), int(ckpt_every),
+                                       st, f | (L.MG_ALLOW_CFL if allow_cfl else 0))
+    L.check(rc, "mg_jacobian_T_apply_batch")
+    return outs

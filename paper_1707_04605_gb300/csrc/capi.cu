@@ -101,7 +101,7 @@ struct mg_mesh {
   int64_t launches = 0;
   // CUDA graphs of step chunks, keyed by kind, buffers and sizes
   int chunk = 128;                        // steps per graph (even), 0 = off
-  int batch = 8;                          // stiffness entries per gather batch
+  int batch = 1;                          // row kernels: float4 vectors per lane
   // shared-memory row tiles (0 = untiled kernels)
   int tile_rows = 0;
   int src_tile = 32;
@@ -624,7 +624,7 @@ int mg_mesh_trim(mg_mesh* M) {
 int mg_mesh_set_tuning(mg_mesh* M, int chunk, int batch, int tile_rows, int src_tile) {
   if (!M) return MG_ERR_ARG;
   if (chunk != -1 && (chunk < 0 || chunk == 1 || chunk % 2 != 0 || chunk > 4096)) return MG_ERR_ARG;
-  if (batch != -1 && batch != 4 && batch != 8) return MG_ERR_ARG;
+  if (batch != -1 && batch != 1 && batch != 2 && batch != 4) return MG_ERR_ARG;
   if (tile_rows != -1 && (tile_rows < 0 || tile_rows % mg::kSliceH != 0 || tile_rows > 8192))
     return MG_ERR_ARG;
   if (src_tile != -1 && src_tile != 4 && src_tile != 8 && src_tile != 16 && src_tile != 32 &&
@@ -851,7 +851,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   MG_CU(cudaMemsetAsync(mu1, 0, state * sizeof(float), st));
   // accumulators: one set per source tile of the untiled kernel; the tiled
   // kernel sums all shots of a row inside its CTA
-  const int acc_sets = adjoint_tiled(M, pp.S_pad) ? 1 : pp.tiles;
+  const int acc_sets = adjoint_tiled(M, pp.S_pad) ? 1 : mg::rows_tiles(pp.S_pad, M->batch);
   const size_t acc = (size_t)acc_sets * n;
   MG_TRY(ensure(M->G, 4 * acc * sizeof(float)));
   MG_CU(cudaMemsetAsync(M->G.p, 0, 4 * acc * sizeof(float), st));
@@ -986,6 +986,91 @@ int mesh_view(mg_mesh* M, MeshView* v) {
   v->launches = &M->launches;
   v->batch = M->batch;
   return MG_OK;
+}
+
+int prepare_instance(mg_mesh* M, const double* eps, const mg_shots* shots, const double* wavelet,
+                     double dt, int nt, int flags, void* stream, int ckpt_every, const float* w,
+                     InstanceView* v) {
+  if (!M || !v) return MG_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Prep pp;
+  MG_TRY(prepare(M, eps, shots, wavelet, dt, nt, flags, st, pp));
+  const int64_t n = M->hm.n;
+  const size_t state = (size_t)n * pp.S_pad;
+  for (Buf* b : {&M->stA, &M->stB, &M->stC, &M->stD}) MG_TRY(ensure(*b, state * sizeof(float)));
+  MG_TRY(ensure(M->tr, (size_t)pp.R * nt * sizeof(float)));
+  v->K = dev_ell(M);
+  v->ev = pp.ev;
+  v->coef = P<const float4>(M->coef);
+  v->wavelet = P<const float>(M->wavf);
+  v->eps = pp.eps;
+  v->S = pp.S;
+  v->S_pad = pp.S_pad;
+  v->tiles = pp.tiles;
+  v->R = pp.R;
+  v->n = n;
+  v->A = P<float>(M->stA);
+  v->B = P<float>(M->stB);
+  v->C = P<float>(M->stC);
+  v->D = P<float>(M->stD);
+  v->tr = P<float>(M->tr);
+  v->ckpt = v->seg = nullptr;
+  v->G = nullptr;
+  v->w = nullptr;
+  if (ckpt_every > 0) {
+    const int nck = (nt + ckpt_every - 1) / ckpt_every;
+    MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * state * sizeof(float)));
+    MG_TRY(ensure(M->seg, (size_t)(std::min(ckpt_every, nt) + 2) * state * sizeof(float)));
+    MG_TRY(ensure(M->G, 4 * (size_t)pp.tiles * n * sizeof(float)));
+    v->ckpt = P<float>(M->ckpt);
+    v->seg = P<float>(M->seg);
+    v->G = P<float>(M->G);
+    M->ck_valid = false;
+  }
+  if (w) {
+    const size_t wbytes = (size_t)pp.R * nt * sizeof(float);
+    MG_TRY(ensure(M->w_h, wbytes));
+    MG_CU(cudaMemcpyAsync(M->w_h.p, w, wbytes,
+                          (flags & MG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          st));
+    v->w = P<const float>(M->w_h);
+  }
+  v->launches = &M->launches;
+  return MG_OK;
+}
+
+int finish_gradient(mg_mesh* M, int level, const double* eps_dev, double dt, int tiles, double* g,
+                    int flags, void* stream) {
+  if (!M || !g || level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MG_TRY(ensure_level(M, level));
+  MG_TRY(ensure(M->gfine, M->hm.m * sizeof(double)));
+  const size_t acc = (size_t)tiles * M->hm.n;
+  float* G = P<float>(M->G);
+  mg::GradArgs ga;
+  ga.m = M->hm.m;
+  ga.k = M->hm.dim + 1;
+  ga.dim = M->hm.dim;
+  ga.cells = P<int32_t>(M->cells);
+  ga.vol = P<double>(M->vol);
+  ga.cf_ptr = P<int64_t>(M->cf_ptr);
+  ga.cf_facet = P<int32_t>(M->cf_facet);
+  ga.bnd = P<int32_t>(M->bnd);
+  ga.bnd_meas = P<double>(M->bnd_meas);
+  ga.eps = eps_dev;
+  ga.dt = dt;
+  ga.bc = M->hm.bc;
+  ga.n = (int32_t)M->hm.n;
+  ga.tiles = tiles;
+  ga.G = G; ga.Gc = G + acc; ga.H = G + 2 * acc; ga.Hc = G + 3 * acc;
+  ga.g_fine = P<double>(M->gfine);
+  MG_TRY(mg::launch_cell_gradient(ga, st));
+  const int64_t nc = M->hm.n_cells_level[level];
+  MG_TRY(ensure(M->g_h, nc * sizeof(double)));
+  MG_TRY(mg::launch_restrict(nc, P<int64_t>(M->lvl_ptr[level]), P<int32_t>(M->lvl_idx[level]),
+                             ga.g_fine, P<double>(M->g_h), st));
+  M->launches += 2;
+  return deliver(M->g_h, g, nc * sizeof(double), flags, st);
 }
 
 }  // namespace mg

@@ -38,89 +38,6 @@ __device__ __forceinline__ RowIn row_in(const DevEll& K, int row) {
   return r;
 }
 
-// acc += sum_{k=1}^{w-1} K_k p[col_k][src0..src0+3], B entries per batch:
-// the batch's B stiffness entries are loaded together, then its B float4
-// gathers are all in flight before the first FMA.
-template <int B>
-__device__ __forceinline__ float4 gather_acc(RowIn r, const float* __restrict__ p, int ld,
-                                             int src0, float4 acc) {
-  for (int k0 = 1; k0 < r.w; k0 += B) {
-    int2 ek[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j)
-      ek[j] = (k0 + j < r.w) ? __ldg(r.e + (k0 + j) * kSliceH) : make_int2(-1, 0);
-    float4 x[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j)
-      x[j] = ek[j].x >= 0 ? ld4(p + (size_t)ek[j].x * ld + src0) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < B; ++j) acc = fma4(__int_as_float(ek[j].y), x[j], acc);
-  }
-  return acc;
-}
-
-template <int B>
-__device__ __forceinline__ void gather_acc2(RowIn r, const float* __restrict__ p,
-                                            const float* __restrict__ q, int ld, int src0,
-                                            float4& pacc, float4& qacc) {
-  for (int k0 = 1; k0 < r.w; k0 += B) {
-    int2 ek[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j)
-      ek[j] = (k0 + j < r.w) ? __ldg(r.e + (k0 + j) * kSliceH) : make_int2(-1, 0);
-    float4 x[B], y[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      const bool ok = ek[j].x >= 0;
-      const size_t o = (size_t)(ok ? ek[j].x : 0) * ld + src0;
-      x[j] = ok ? ld4(p + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-      y[j] = ok ? ld4(q + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      pacc = fma4(__int_as_float(ek[j].y), x[j], pacc);
-      qacc = fma4(__int_as_float(ek[j].y), y[j], qacc);
-    }
-  }
-}
-
-template <int LPR, int B>
-__global__ void __launch_bounds__(kThreads) k_step(StepArgs a) {
-  constexpr int RPW = 32 / LPR;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
-  if (row >= a.K.n) return;
-  const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
-  const size_t ro = (size_t)row * a.ld + src0;
-  // round trip 1: row-only data
-  const RowIn r = row_in(a.K, row);
-  const float4 self = ld4(a.p + ro);
-  const float4 old = ld4v(a.pm + ro);
-  const float4 c = __ldg(a.coef + row);
-  const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
-  const int r0 = a.traces ? __ldg(a.ev.rec_ptr + row) : 0;
-  const int r1 = a.traces ? __ldg(a.ev.rec_ptr + row + 1) : 0;
-  const int l = a.step + (a.step_base ? *a.step_base : 0);
-  // rounds 2-3: stiffness entries, then neighbour gathers
-  float4 acc = scale4(__int_as_float(__ldg(r.e).y), self);
-  acc = gather_acc<B>(r, a.p, a.ld, src0, acc);
-  float4 out = leap(c, self, old, acc);
-  if (s0 != s1) {
-    const float sv = c.z * __ldg(a.wavelet + l);
-    for (int q = s0; q < s1; ++q) {
-      const int d = __ldg(a.ev.src_shot + q) - src0;
-      if (d >= 0 && d < 4) add_comp(out, d, sv);
-    }
-  }
-  st4(a.pout + ro, out);
-  for (int q = r0; q < r1; ++q) {
-    const int d = __ldg(a.ev.rec_shot + q) - src0;
-    if (d >= 0 && d < 4)
-      a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = get_comp(out, d);
-  }
-}
-
 // Plain single-shot step (the one-source comparator): one thread per row,
 // scalar state, sliced-ELL entries read coalesced across the warp (a warp is
 // one slice).
@@ -147,94 +64,6 @@ __global__ void __launch_bounds__(256) k_step_single(StepArgs a, int shot) {
     for (int q = r0; q < r1; ++q)
       if (__ldg(a.ev.rec_shot + q) == shot)
         a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = out;
-  }
-}
-
-template <int LPR, int B>
-__global__ void __launch_bounds__(kThreads) k_tangent(TangentArgs a) {
-  constexpr int RPW = 32 / LPR;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
-  if (row >= a.f.K.n) return;
-  const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
-  const int ld = a.f.ld;
-  const size_t ro = (size_t)row * ld + src0;
-  const RowIn r = row_in(a.f.K, row);
-  const float4 ps = ld4(a.f.p + ro), qs = ld4(a.q + ro);
-  const float4 pold = ld4v(a.f.pm + ro), qold = ld4v(a.qm + ro);
-  const float4 c = __ldg(a.f.coef + row);
-  const float2 tc = __ldg(a.tcoef + row);
-  const int s0 = __ldg(a.f.ev.src_ptr + row), s1 = __ldg(a.f.ev.src_ptr + row + 1);
-  const int r0 = __ldg(a.f.ev.rec_ptr + row), r1 = __ldg(a.f.ev.rec_ptr + row + 1);
-  const int l = a.f.step + (a.f.step_base ? *a.f.step_base : 0);
-  const float v0 = __int_as_float(__ldg(r.e).y);
-  float4 acc = scale4(v0, ps), qacc = scale4(v0, qs);
-  gather_acc2<B>(r, a.f.p, a.q, ld, src0, acc, qacc);
-  float4 pn = leap(c, ps, pold, acc);
-  if (s0 != s1) {
-    const float sv = c.z * __ldg(a.f.wavelet + l);
-    for (int q = s0; q < s1; ++q) {
-      const int d = __ldg(a.f.ev.src_shot + q) - src0;
-      if (d >= 0 && d < 4) add_comp(pn, d, sv);
-    }
-  }
-  // dp+ = alpha dp - beta dp- - gamma K dp - cm (p+ - 2p + p-) - cd (p+ - p-)
-  float4 qn = leap(c, qs, qold, qacc);
-#define MG_TAN(X) qn.X -= tc.x * ((pn.X - 2.0f * ps.X) + pold.X) + tc.y * (pn.X - pold.X);
-  MG_TAN(x) MG_TAN(y) MG_TAN(z) MG_TAN(w)
-#undef MG_TAN
-  st4(a.f.pout + ro, pn);
-  st4(a.qm + ro, qn);
-  for (int q = r0; q < r1; ++q) {
-    const int d = __ldg(a.f.ev.rec_shot + q) - src0;
-    if (d >= 0 && d < 4)
-      a.dtraces[(size_t)__ldg(a.f.ev.rec_trace + q) * a.f.nt + l] = get_comp(qn, d);
-  }
-}
-
-template <int LPR, int B>
-__global__ void __launch_bounds__(kThreads) k_adjoint(AdjointArgs a) {
-  constexpr int RPW = 32 / LPR;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
-  const bool valid = row < a.K.n;
-  const int src0 = blockIdx.y * kTile + (lane % LPR) * 4;
-  float t1 = 0.0f, t2 = 0.0f;
-  if (valid) {
-    const size_t ro = (size_t)row * a.ld + src0;
-    const RowIn r = row_in(a.K, row);
-    const float4 self = ld4(a.mu + ro);
-    const float4 old = ld4v(a.mu1 + ro);  // mu_{k+1}
-    const float4 pk = ld4(a.pk + ro);
-    const float4 c = __ldg(a.coef + row);
-    const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
-    const int k = a.k + (a.step_base ? *a.step_base : 0);
-    float4 acc = scale4(__int_as_float(__ldg(r.e).y), self);
-    acc = gather_acc<B>(r, a.mu, a.ld, src0, acc);
-    float4 out = leap(c, self, old, acc);
-    for (int q = r0; q < r1; ++q) {
-      const int d = __ldg(a.ev.rec_shot + q) - src0;
-      if (d >= 0 && d < 4)
-        add_comp(out, d, c.w * __ldg(a.w + (size_t)__ldg(a.ev.rec_trace + q) * a.nt + (k - 1)));
-    }
-    st4(a.mu1 + ro, out);
-#define MG_ACC(X)                                                              \
-  t1 = fmaf(pk.X, (out.X - 2.0f * self.X) + old.X, t1);                        \
-  t2 = fmaf(pk.X, out.X - old.X, t2);
-    MG_ACC(x) MG_ACC(y) MG_ACC(z) MG_ACC(w)
-#undef MG_ACC
-  }
-#pragma unroll
-  for (int off = LPR / 2; off > 0; off >>= 1) {
-    t1 += __shfl_xor_sync(0xffffffffu, t1, off);
-    t2 += __shfl_xor_sync(0xffffffffu, t2, off);
-  }
-  if (valid && (lane % LPR) == 0) {
-    const size_t gi = (size_t)blockIdx.y * a.K.n + row;
-    kahan_add(a.G + gi, a.Gc + gi, t1);
-    kahan_add(a.H + gi, a.Hc + gi, t2);
   }
 }
 
@@ -341,57 +170,10 @@ __global__ void k_copy_f4(const float4* __restrict__ src, float4* __restrict__ d
 }
 
 
-int lpr_of(int S_pad) { return S_pad >= kTile ? 32 : S_pad / 4; }
-
 }  // namespace
-
-int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
-  const int lpr = lpr_of(S_pad);
-  const int rows_per_block = kWarps * (32 / lpr);
-  dim3 grid((a.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
-  const int B = a.batch == 4 ? 4 : 8;
-  switch (lpr * 16 + B) {
-#define MG_CASE(L_, B_) case L_ * 16 + B_: k_step<L_, B_><<<grid, kThreads, 0, st>>>(a); break;
-    MG_CASE(32, 4) MG_CASE(32, 8) MG_CASE(16, 4) MG_CASE(16, 8) MG_CASE(8, 4) MG_CASE(8, 8)
-    MG_CASE(4, 4) MG_CASE(4, 8) MG_CASE(2, 4) MG_CASE(2, 8) MG_CASE(1, 4) MG_CASE(1, 8)
-#undef MG_CASE
-    default: return MG_ERR_ARG;
-  }
-  return check_launch();
-}
 
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st) {
   k_step_single<<<(a.K.n + 255) / 256, 256, 0, st>>>(a, shot);
-  return check_launch();
-}
-
-int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st) {
-  const int lpr = lpr_of(S_pad);
-  const int rows_per_block = kWarps * (32 / lpr);
-  dim3 grid((a.f.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
-  const int B = a.f.batch == 4 ? 4 : 8;
-  switch (lpr * 16 + B) {
-#define MG_CASE(L_, B_) case L_ * 16 + B_: k_tangent<L_, B_><<<grid, kThreads, 0, st>>>(a); break;
-    MG_CASE(32, 4) MG_CASE(32, 8) MG_CASE(16, 4) MG_CASE(16, 8) MG_CASE(8, 4) MG_CASE(8, 8)
-    MG_CASE(4, 4) MG_CASE(4, 8) MG_CASE(2, 4) MG_CASE(2, 8) MG_CASE(1, 4) MG_CASE(1, 8)
-#undef MG_CASE
-    default: return MG_ERR_ARG;
-  }
-  return check_launch();
-}
-
-int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st) {
-  const int lpr = lpr_of(S_pad);
-  const int rows_per_block = kWarps * (32 / lpr);
-  dim3 grid((a.K.n + rows_per_block - 1) / rows_per_block, S_pad >= kTile ? S_pad / kTile : 1);
-  const int B = a.batch == 4 ? 4 : 8;
-  switch (lpr * 16 + B) {
-#define MG_CASE(L_, B_) case L_ * 16 + B_: k_adjoint<L_, B_><<<grid, kThreads, 0, st>>>(a); break;
-    MG_CASE(32, 4) MG_CASE(32, 8) MG_CASE(16, 4) MG_CASE(16, 8) MG_CASE(8, 4) MG_CASE(8, 8)
-    MG_CASE(4, 4) MG_CASE(4, 8) MG_CASE(2, 4) MG_CASE(2, 8) MG_CASE(1, 4) MG_CASE(1, 8)
-#undef MG_CASE
-    default: return MG_ERR_ARG;
-  }
   return check_launch();
 }
 

@@ -39,7 +39,7 @@ struct StepArgs {
   int32_t nt;
   int32_t step;             // l = step + (step_base ? *step_base : 0)
   const int32_t* step_base;
-  int32_t batch;            // stiffness entries gathered per batch (4 or 8)
+  int32_t batch;            // row kernels: float4 vectors (4 shots each) per lane, 1/2/4
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -98,6 +98,10 @@ size_t tiled_smem_bytes(const DevTiles& T, int kind);
 int launch_step_tiled(const StepArgs& a, const DevTiles& T, cudaStream_t st);
 int launch_tangent_tiled(const TangentArgs& a, const DevTiles& T, cudaStream_t st);
 int launch_adjoint_tiled(const AdjointArgs& a, const DevTiles& T, cudaStream_t st);
+
+// Source tiles (grid.y) of the row kernels for a padded shot count and
+// `nv` float4 per lane; the adjoint keeps one accumulator set per tile.
+int rows_tiles(int S_pad, int nv);
 
 int launch_step(const StepArgs& a, int S_pad, cudaStream_t st);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);

@@ -24,4 +24,35 @@ struct MeshView {
 
 int mesh_view(mg_mesh* mesh, MeshView* out);
 
+// One problem of a multi-instance batch, prepared on its own handle: device
+// inputs staged, coefficients and FP32 wavelet computed, event lists built,
+// and the handle's state / checkpoint / accumulator buffers sized.
+struct InstanceView {
+  DevEll K;
+  DevEvents ev;
+  const float4* coef;
+  const float* wavelet;
+  const double* eps;        // device copy or caller pointer
+  int S, S_pad, tiles;
+  int64_t R, n;
+  float* A; float* B; float* C; float* D;  // n * S_pad floats each
+  float* ckpt;              // [nck][2][n][S_pad] when requested
+  float* seg;               // [K+2][n][S_pad] when requested
+  float* tr;                // [R][nt] internal trace buffer
+  float* G;                 // [4][tiles][n] Kahan accumulators when requested
+  const float* w;           // [R][nt] staged weights when given
+  int64_t* launches;
+};
+
+// ckpt_every > 0 sizes checkpoint and segment buffers; w (device or host
+// per flags) is staged when non-null.
+int prepare_instance(mg_mesh* mesh, const double* eps, const mg_shots* shots,
+                     const double* wavelet, double dt, int nt, int flags, void* stream,
+                     int ckpt_every, const float* w, InstanceView* out);
+
+// FP64 per-cell gradient from the instance's accumulators, restricted to
+// `level` into g (device pointer, or host pointer with MG_HOST_PTRS).
+int finish_gradient(mg_mesh* mesh, int level, const double* eps_dev, double dt, int tiles,
+                    double* g, int flags, void* stream);
+
 }  // namespace mg

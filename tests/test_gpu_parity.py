@@ -103,6 +103,70 @@ def test_forward_asteroid_2d_full_sampled(mg):
     assert rel_l2(y1, y[rows]) < 1e-6
 
 
+def test_forward_asteroid_2d_full_all_shots_early_samples(mg):
+    """Full workload, all 128 shots: the first 250 samples of every trace
+    depend only on the first 250 steps, so an oracle run of 250 steps checks
+    every trace of the full 8000-step launch."""
+    w = configs.asteroid_2d()
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    k = 250
+    ref = oracle_traces(w, dt, s[:k], w.shots)
+    assert rel_l2(y[:, :k], ref) < TRACE_TOL
+
+
+def test_forward_ellipsoid_3d_level2(mg):
+    """3D, 226,981 nodes (two refinements), 64 shots in one launch, 600
+    steps: shots 0 and 33 against the oracle."""
+    w = configs.ellipsoid_3d(n_refine=2, nt=600)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    pick = [0, 33]
+    sub = w.shots.subset(pick)
+    ref = oracle_traces(w, dt, s, sub)
+    assert rel_l2(y[w.shots.trace_rows(pick)], ref) < TRACE_TOL
+
+
+def test_forward_ellipsoid_3d_full(mg):
+    """Full 3D workload (1,814,385 nodes, 10.6M tets, 64 shots, 6000 steps,
+    one launch per step over all shots): the first 150 samples of shots 0
+    and 40 against the oracle (causality), and shot 40's whole trace
+    against the plain one-shot path (batching invariance)."""
+    w = configs.ellipsoid_3d()
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
+    assert np.isfinite(y).all() and np.abs(y).max() > 0
+    pick = [0, 40]
+    rows = w.shots.trace_rows(pick)
+    k = 150
+    ref = oracle_traces(w, dt, s[:k], w.shots.subset(pick))
+    assert rel_l2(y[rows, :k], ref) < TRACE_TOL
+    y1 = mg.forward(mesh, _dev(w.eps), w.shots.subset([40]), _dev(s), dt,
+                    single_source=True).cpu().numpy()
+    assert rel_l2(y1, y[w.shots.trace_rows([40])]) < 1e-6
+
+
+def test_jacobian_ellipsoid_3d_level1(mg):
+    w = configs.ellipsoid_3d(n_refine=1, S=6, nt=160)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(w.mesh.n_cells[0])
+    jv = mg.jacobian_apply(mesh, 0, _dev(w.eps), w.shots, _dev(s), dt, _dev(v)).cpu().numpy()
+    assert rel_l2(jv, oracle_tangent(w, dt, s, w.shots, v, 0)) < JAC_TOL
+    W = rng.standard_normal((w.shots.n_traces, len(s))).astype(np.float32)
+    g = mg.jacobian_T_apply(mesh, 0, _dev(w.eps), w.shots, _dev(s), dt,
+                            _dev(W, torch.float32), ckpt_every=32).cpu().numpy()
+    assert rel_l2(g, oracle_gradient(w, dt, s, w.shots, W.astype(np.float64), 0)) < JAC_TOL
+
+
 def test_cfl_violation_rejected(mg):
     from paper_1707_04605_gb300 import _lib as L
 
@@ -158,8 +222,8 @@ def test_adjoint_checkpoint_spacing_and_reuse(mg):
 
 
 @pytest.mark.parametrize("chunk,batch,tile_rows,src_tile", [
-    (0, 8, 0, 32), (0, 4, 0, 32), (128, 8, 0, 32), (64, 4, 256, 16), (128, 8, 128, 64),
-    (128, 8, 64, 8), (0, 8, 512, 4)])
+    (0, 1, 0, 32), (0, 2, 0, 32), (128, 4, 0, 32), (64, 2, 256, 16), (128, 1, 128, 64),
+    (128, 2, 64, 8), (0, 4, 512, 4)])
 def test_launch_shapes_give_identical_results(mg, chunk, batch, tile_rows, src_tile):
     """Graph replay vs plain launches, gather batches, shared-memory tiles of
     several sizes (including a ragged last tile) vs the untiled kernels: the
