@@ -54,6 +54,7 @@ def parse():
                     help="rows per shared-memory tile (0 = untiled kernels)")
     ap.add_argument("--src-tile", type=int, default=-1, help="shots per staged pass")
     ap.add_argument("--chunk", type=int, default=-1, help="leapfrog steps per CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -147,6 +148,8 @@ def hbm_leg(mg, torch, dev, nt=300):
     eps = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps)
     wav = torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
+    mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
+    tuning = mesh.tuning()
     mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -166,6 +169,7 @@ def hbm_leg(mg, torch, dev, nt=300):
     return {"workload": f"ellipsoid_3d: {n} nodes, {w.mesh.cells.shape[0]} tets, {S} "
                         f"backscatter shots, {nt} steps (forward only)",
             "forward_updates_per_s": n * S * nt / s, "us_per_leapfrog_step": 1e6 * s / nt,
+            "tuning": tuning["forward"],
             "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind_note(kind),
@@ -264,6 +268,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     import paper_1707_04605_gb300 as mg
+    from paper_1707_04605_gb300 import distributed as pdist
 
     w = workload_for_rank(rank, args.nt)
     mesh = mg.mesh_from_workload(w)
@@ -277,12 +282,16 @@ def main():
     v = np.zeros(nlev)
     v[np.random.default_rng(0).integers(nlev)] = 1.0
     v_d = torch.as_tensor(v, dtype=torch.float64, device=dev)
+    if args.tile_rows == -1 and args.src_tile == -1 and not args.no_autotune:
+        # launch shapes per kernel kind, timed on this problem (setup, untimed)
+        mesh.autotune(eps_d, w.shots, wav_d, dt, steps=128, level=LEVEL)
+    tuning = mesh.tuning()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def allreduce(g):
         if ws > 1:
-            torch.distributed.all_reduce(g)
+            pdist.gradient_allreduce(g)
         return g
 
     phase_ev = {}
@@ -391,6 +400,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": describe(w), "nodes": n, "shots": S, "nt": nt,
                    "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
+                   "tuning": tuning,
                    "l2": "flushed between timed steps (256 MB write)"},
         "phases_ms": {"forward": statistics.mean(fwd_ms), "adjoint": statistics.mean(adj_ms),
                       "tangent": statistics.mean(tan_ms)},

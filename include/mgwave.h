@@ -236,6 +236,37 @@ int mg_jacobian_T_apply_batch(int n_inst, mg_mesh* const* meshes, const int* lev
                               const float* const* w, double* const* g, int ckpt_every,
                               void* stream, int flags);
 
+/* Per-kernel tuning.  kind: MG_KERNEL_FORWARD (forward and recompute steps),
+ * MG_KERNEL_TANGENT, MG_KERNEL_ADJOINT; batch / tile_rows / src_tile as in
+ * mg_mesh_set_tuning (which sets all three kinds at once). */
+#define MG_KERNEL_FORWARD 0
+#define MG_KERNEL_TANGENT 1
+#define MG_KERNEL_ADJOINT 2
+int mg_mesh_set_kernel_tuning(mg_mesh* mesh, int kind, int batch, int tile_rows, int src_tile);
+
+/* Current tuning into out[10]: chunk, then (batch, tile_rows, src_tile) for
+ * the forward, tangent and adjoint kinds. */
+int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
+
+/* Autotuner: times every candidate launch shape of each kernel kind on the
+ * caller's problem (steps leapfrog steps of mg_forward, mg_jacobian_apply
+ * and mg_jacobian_T_apply on `level`, device pointers; wavelet must hold at
+ * least `steps` samples), keeps the fastest per kind on the handle and
+ * returns it in chosen[10] (may be NULL).  Candidates: row kernels with 1,
+ * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
+ * per pass.  The choice is cached on the handle per padded shot count; a
+ * later call with the same count only re-applies it.  Synchronous.
+ * flags: 0 or MG_ALLOW_CFL. */
+int mg_autotune(mg_mesh* mesh, const double* eps, const mg_shots* shots, const double* wavelet,
+                double dt, int steps, int level, void* stream, int flags, int32_t* chosen);
+
+/* Nested prolongation of level-cell values to the finest cells (Sec. II-B:
+ * eps_r = sum_j c_j chi'_j): out[e] = base[e] + v[anc_level(e)] for every
+ * finest cell e (base may be NULL for 0).  v: [cells of level], base, out:
+ * [n_cells]; data pointers (float64). */
+int mg_prolong(mg_mesh* mesh, int level, const double* v, const double* base, double* out,
+               void* stream, int flags);
+
 /* Release the handle's scratch (states, checkpoints, graphs). */
 int mg_mesh_trim(mg_mesh* mesh);
 

@@ -71,6 +71,12 @@ SIGNATURES = {
                                             C.POINTER(mg_shots), C.c_void_p, C.c_void_p,
                                             C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                             C.c_void_p, C.c_int]),
+    "mg_prolong": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_int]),
+    "mg_mesh_set_kernel_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "mg_mesh_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mg_shots), C.c_void_p,
+                              C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "mg_mesh_trim": (C.c_int, [C.c_void_p]),
     "mg_mesh_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "mg_launch_count": (C.c_int64, [C.c_void_p]),

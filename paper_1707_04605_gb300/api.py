@@ -116,6 +116,38 @@ class Mesh:
     def launch_count(self) -> int:
         return int(self._lib.mg_launch_count(self.handle))
 
+    KINDS = {"forward": 0, "tangent": 1, "adjoint": 2}
+
+    def set_kernel_tuning(self, kind: str, batch: int = -1, tile_rows: int = -1,
+                          src_tile: int = -1):
+        L.check(self._lib.mg_mesh_set_kernel_tuning(self.handle, self.KINDS[kind], int(batch),
+                                                    int(tile_rows), int(src_tile)),
+                "mg_mesh_set_kernel_tuning")
+
+    def tuning(self) -> dict:
+        out = np.zeros(10, dtype=np.int32)
+        L.check(self._lib.mg_mesh_get_tuning(self.handle, C.c_void_p(out.ctypes.data)),
+                "mg_mesh_get_tuning")
+        d = {"chunk": int(out[0])}
+        for name, k in self.KINDS.items():
+            d[name] = {"batch": int(out[1 + 3 * k]), "tile_rows": int(out[2 + 3 * k]),
+                       "src_tile": int(out[3 + 3 * k])}
+        return d
+
+    def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,
+                 stream=None) -> dict:
+        """Time the candidate launch shapes per kernel kind (mg_autotune) on
+        CUDA inputs and keep the fastest; returns the chosen tuning."""
+        sh = Shots.of(shots)
+        eps, pe = _dev(eps, "float64")
+        wavelet, pw = _dev(wavelet, "float64")
+        out = np.zeros(10, dtype=np.int32)
+        L.check(self._lib.mg_autotune(self.handle, pe, C.byref(sh.c), pw, float(dt), int(steps),
+                                      int(level), _stream_ptr(stream),
+                                      L.MG_ALLOW_CFL if allow_cfl else 0,
+                                      C.c_void_p(out.ctypes.data)), "mg_autotune")
+        return self.tuning()
+
     def set_tuning(self, chunk: int = -1, batch: int = -1, tile_rows: int = -1,
                    src_tile: int = -1):
         """Graph chunk length (even, 0 = plain launches), untiled gather batch
@@ -241,6 +273,24 @@ def jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, w, nt=None, *,
     rc = lib.mg_jacobian_T_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
                                  nt, pwt, _ptr(out), int(ckpt_every), st, f)
     L.check(rc, "mg_jacobian_T_apply")
+    return out
+
+
+def prolong(mesh: Mesh, level, v, base=None, stream=None):
+    """Finest-cell values base[e] + v[anc_level(e)] (mg_prolong)."""
+    lib = L.load()
+    m = mesh.n_cells_per_level[-1]
+    if _is_cuda(v):
+        v, pv = _dev(v, "float64")
+        pb = _dev(base, "float64")[1] if base is not None else None
+        out = _alloc(True, (m,), "float64", v)
+        rc = lib.mg_prolong(mesh.handle, int(level), pv, pb, _ptr(out), _stream_ptr(stream), 0)
+    else:
+        v, pv = _host(v, np.float64)
+        bh = _host(base, np.float64) if base is not None else (None, None)
+        out = np.empty(m, dtype=np.float64)
+        rc = lib.mg_prolong(mesh.handle, int(level), pv, bh[1], _ptr(out), None, L.MG_HOST_PTRS)
+    L.check(rc, "mg_prolong")
     return out
 
 

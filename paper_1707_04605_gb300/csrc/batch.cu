@@ -138,11 +138,7 @@ __global__ void __launch_bounds__(32 * kBW) k_adjoint_multi(const Inst* __restri
         add_comp(out, d, c.w * __ldg(I.w + (size_t)__ldg(I.ev.rec_trace + q) * nt + (k - 1)));
     }
     st4(mu1 + ro, out);
-#define MG_ACC(X)                                                              \
-  t1 = fmaf(pk.X, (out.X - 2.0f * self.X) + old.X, t1);                        \
-  t2 = fmaf(pk.X, out.X - old.X, t2);
-    MG_ACC(x) MG_ACC(y) MG_ACC(z) MG_ACC(w)
-#undef MG_ACC
+    adj_terms(pk, out, self, old, t1, t2);
   }
   // sum over the lanes of a row (lpr is a power of two, groups are aligned)
   for (int off = 16; off > 0; off >>= 1) {

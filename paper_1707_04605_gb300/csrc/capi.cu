@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -49,6 +50,8 @@ int upload(Buf& b, const std::vector<T>& v) {
 
 template <class T>
 T* P(Buf& b) { return static_cast<T*>(b.p); }
+template <class T>
+T* P_(const Buf& b) { return static_cast<T*>(b.p); }
 
 int round_pad(int S) {
   if (S <= 4) return 4;
@@ -101,18 +104,27 @@ struct mg_mesh {
   int64_t launches = 0;
   // CUDA graphs of step chunks, keyed by kind, buffers and sizes
   int chunk = 128;                        // steps per graph (even), 0 = off
-  int batch = 1;                          // row kernels: float4 vectors per lane
-  // shared-memory row tiles (0 = untiled kernels)
-  int tile_rows = 0;
-  int src_tile = 32;
-  int tiles_P = 0;                        // P of the uploaded tile tables
-  Buf t_ell_off, t_ell_idx, t_ell_val, t_sinfo, t_halo_off, t_halo_cnt, t_halo;
-  int t_n_tiles = 0, t_max_ell = 0, t_max_halo = 0;
-  double t_ratio = 0.0;
+  // per kernel kind (0 forward/recompute, 1 tangent, 2 adjoint): row-kernel
+  // float4 vectors per lane, shared-memory tile rows (0 = row kernel), shots
+  // per staged pass
+  struct Tuning {
+    int batch = 1;
+    int tile_rows = 0;
+    int src_tile = 32;
+  } tune[3];
+  struct TileTables {
+    Buf ell_off, ell_idx, ell_val, sinfo, halo_off, halo_cnt, halo;
+    int n_tiles = 0, max_ell = 0, max_halo = 0;
+    double ratio = 0.0;
+  };
+  std::map<int, TileTables> tiles;        // by rows per tile
   int smem_optin = 0;
+  // autotuned choices by (n_shots padded), so repeated calls skip the search
+  std::map<int, std::array<Tuning, 3>> tuned;
   cudaStream_t cap = nullptr;             // private capture stream
   std::map<std::string, cudaGraphExec_t> graphs;
   Buf tr;                                 // internal trace buffer [R][nt]
+  Buf tune_scratch;                       // autotuner inputs/outputs
 };
 
 namespace {
@@ -298,24 +310,27 @@ int prepare(mg_mesh* M, const double* eps, const mg_shots* shots, const double* 
   return MG_OK;
 }
 
-// Tile tables for the current tile_rows, built on the host and uploaded on
-// first use.
+// Tile tables for every tile size the kernel kinds use, built on the host
+// and uploaded on first use.
 int ensure_tiles(mg_mesh* M) {
-  if (M->tile_rows <= 0 || M->tiles_P == M->tile_rows) return MG_OK;
-  mg::HostTiles T;
-  MG_TRY(mg::build_tiles(M->hm, M->tile_rows, T));
-  MG_TRY(upload(M->t_ell_off, T.ell_off));
-  MG_TRY(upload(M->t_ell_idx, T.ell_idx));
-  MG_TRY(upload(M->t_ell_val, T.ell_val));
-  MG_TRY(upload(M->t_sinfo, T.slice_info));
-  MG_TRY(upload(M->t_halo_off, T.halo_off));
-  MG_TRY(upload(M->t_halo_cnt, T.halo_cnt));
-  MG_TRY(upload(M->t_halo, T.halo));
-  M->t_n_tiles = (int)T.n_tiles;
-  M->t_max_ell = T.max_ell;
-  M->t_max_halo = T.max_halo;
-  M->t_ratio = T.halo_ratio;
-  M->tiles_P = M->tile_rows;
+  for (const auto& t : M->tune) {
+    const int P = t.tile_rows;
+    if (P <= 0 || M->tiles.count(P)) continue;
+    mg::HostTiles T;
+    MG_TRY(mg::build_tiles(M->hm, P, T));
+    mg_mesh::TileTables& D = M->tiles[P];
+    MG_TRY(upload(D.ell_off, T.ell_off));
+    MG_TRY(upload(D.ell_idx, T.ell_idx));
+    MG_TRY(upload(D.ell_val, T.ell_val));
+    MG_TRY(upload(D.sinfo, T.slice_info));
+    MG_TRY(upload(D.halo_off, T.halo_off));
+    MG_TRY(upload(D.halo_cnt, T.halo_cnt));
+    MG_TRY(upload(D.halo, T.halo));
+    D.n_tiles = (int)T.n_tiles;
+    D.max_ell = T.max_ell;
+    D.max_halo = T.max_halo;
+    D.ratio = T.halo_ratio;
+  }
   if (!M->smem_optin)
     MG_CU(cudaDeviceGetAttribute(&M->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                  M->device));
@@ -323,24 +338,28 @@ int ensure_tiles(mg_mesh* M) {
 }
 
 // Tiled launch description for a padded shot count and kernel kind (0
-// forward, 1 tangent, 2 adjoint), or n_tiles = 0 when that kernel does not
-// fit in shared memory.  The tangent stages two states per pass, so it
-// passes half as many shots to stay within the one-state footprint.
+// forward, 1 tangent, 2 adjoint), or n_tiles = 0 when that kind runs the
+// row kernel (no tiles, or the tiled footprint exceeds shared memory).  The
+// tangent stages two states per pass, so it passes half as many shots to
+// stay within the one-state footprint.
 mg::DevTiles dev_tiles(mg_mesh* M, int S_pad, int kind) {
   mg::DevTiles T{};
-  if (M->tile_rows <= 0 || M->tiles_P != M->tile_rows) return T;
-  T.P = M->tiles_P;
-  T.n_tiles = M->t_n_tiles;
-  T.ell_off = P<const int64_t>(M->t_ell_off);
-  T.ell_idx = P<const uint16_t>(M->t_ell_idx);
-  T.ell_val = P<const float>(M->t_ell_val);
-  T.slice_info = P<const int32_t>(M->t_sinfo);
-  T.halo_off = P<const int64_t>(M->t_halo_off);
-  T.halo_cnt = P<const int32_t>(M->t_halo_cnt);
-  T.halo = P<const int32_t>(M->t_halo);
-  T.max_ell = M->t_max_ell;
-  T.max_halo = M->t_max_halo;
-  T.st_w = std::min(M->src_tile, S_pad);
+  const int P = M->tune[kind].tile_rows;
+  auto it = M->tiles.find(P);
+  if (P <= 0 || it == M->tiles.end()) return T;
+  const mg_mesh::TileTables& D = it->second;
+  T.P = P;
+  T.n_tiles = D.n_tiles;
+  T.ell_off = P_<const int64_t>(D.ell_off);
+  T.ell_idx = P_<const uint16_t>(D.ell_idx);
+  T.ell_val = P_<const float>(D.ell_val);
+  T.slice_info = P_<const int32_t>(D.sinfo);
+  T.halo_off = P_<const int64_t>(D.halo_off);
+  T.halo_cnt = P_<const int32_t>(D.halo_cnt);
+  T.halo = P_<const int32_t>(D.halo);
+  T.max_ell = D.max_ell;
+  T.max_halo = D.max_halo;
+  T.st_w = std::min(M->tune[kind].src_tile, S_pad);
   if (kind == 1) T.st_w = std::max(4, T.st_w / 2);
   if (mg::tiled_smem_bytes(T, kind) > (size_t)M->smem_optin) T.n_tiles = 0;
   return T;
@@ -348,19 +367,28 @@ mg::DevTiles dev_tiles(mg_mesh* M, int S_pad, int kind) {
 
 int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   const mg::DevTiles T = dev_tiles(M, S_pad, 0);
-  return T.n_tiles ? mg::launch_step_tiled(a, T, st) : mg::launch_step(a, S_pad, st);
+  if (T.n_tiles) return mg::launch_step_tiled(a, T, st);
+  mg::StepArgs b = a;
+  b.batch = M->tune[0].batch;
+  return mg::launch_step(b, S_pad, st);
 }
 
 int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st) {
   const mg::DevTiles T = dev_tiles(M, S_pad, 1);
-  return T.n_tiles ? mg::launch_tangent_tiled(a, T, st) : mg::launch_tangent(a, S_pad, st);
+  if (T.n_tiles) return mg::launch_tangent_tiled(a, T, st);
+  mg::TangentArgs b = a;
+  b.f.batch = M->tune[1].batch;
+  return mg::launch_tangent(b, S_pad, st);
 }
 
 bool adjoint_tiled(mg_mesh* M, int S_pad) { return dev_tiles(M, S_pad, 2).n_tiles > 0; }
 
 int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st) {
   const mg::DevTiles T = dev_tiles(M, S_pad, 2);
-  return T.n_tiles ? mg::launch_adjoint_tiled(a, T, st) : mg::launch_adjoint(a, S_pad, st);
+  if (T.n_tiles) return mg::launch_adjoint_tiled(a, T, st);
+  mg::AdjointArgs b = a;
+  b.batch = M->tune[2].batch;
+  return mg::launch_adjoint(b, S_pad, st);
 }
 
 mg::StepArgs step_args(mg_mesh* M, const Prep& pp, int ld, int nt) {
@@ -372,7 +400,7 @@ mg::StepArgs step_args(mg_mesh* M, const Prep& pp, int ld, int nt) {
   a.wavelet = P<const float>(M->wavf);
   a.nt = nt;
   a.step_base = nullptr;
-  a.batch = M->batch;
+  a.batch = M->tune[0].batch;
   return a;
 }
 
@@ -593,10 +621,11 @@ void mg_mesh_destroy(mg_mesh* M) {
   for (auto* v : {&M->anc, &M->lvl_ptr, &M->lvl_idx})
     for (Buf& b : *v)
       if (b.p) cudaFree(b.p);
-  Buf* tiles[] = {&M->t_ell_off, &M->t_ell_idx, &M->t_ell_val, &M->t_sinfo, &M->t_halo_off,
-                  &M->t_halo_cnt, &M->t_halo};
-  for (Buf* b : tiles)
-    if (b->p) cudaFree(b->p);
+  for (auto& kv : M->tiles) {
+    mg_mesh::TileTables& D = kv.second;
+    for (Buf* b : {&D.ell_off, &D.ell_idx, &D.ell_val, &D.sinfo, &D.halo_off, &D.halo_cnt, &D.halo})
+      if (b->p) cudaFree(b->p);
+  }
   mg_mesh_trim(M);
   if (M->cap) cudaStreamDestroy(M->cap);
   delete M;
@@ -610,7 +639,8 @@ int mg_mesh_trim(mg_mesh* M) {
   M->graphs.clear();
   Buf* all[] = {&M->eps_h, &M->wav_h, &M->wavf, &M->coef, &M->tcoef, &M->mass, &M->scal,
                 &M->stA, &M->stB, &M->stC, &M->stD, &M->out_h, &M->w_h, &M->v_h, &M->g_h,
-                &M->ev, &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base, &M->tr};
+                &M->ev, &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base, &M->tr,
+                &M->tune_scratch};
   for (Buf* b : all) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -621,22 +651,76 @@ int mg_mesh_trim(mg_mesh* M) {
   return MG_OK;
 }
 
-int mg_mesh_set_tuning(mg_mesh* M, int chunk, int batch, int tile_rows, int src_tile) {
-  if (!M) return MG_ERR_ARG;
-  if (chunk != -1 && (chunk < 0 || chunk == 1 || chunk % 2 != 0 || chunk > 4096)) return MG_ERR_ARG;
-  if (batch != -1 && batch != 1 && batch != 2 && batch != 4) return MG_ERR_ARG;
+int mg_prolong(mg_mesh* M, int level, const double* v, const double* base, double* out,
+               void* stream, int flags) {
+  if (!M || !v || !out || level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
+  DeviceGuard g(M->device);
+  if (!g.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MG_TRY(ensure_level(M, level));
+  const int64_t m = M->hm.m;
+  const void* dv;
+  MG_TRY(stage_in(M->v_h, v, M->hm.n_cells_level[level] * sizeof(double), flags, st, &dv));
+  const void* db = nullptr;
+  if (base) MG_TRY(stage_in(M->eps_h, base, m * sizeof(double), flags, st, &db));
+  double* o = out;
+  if (flags & MG_HOST_PTRS) {
+    MG_TRY(ensure(M->g_h, m * sizeof(double)));
+    o = P<double>(M->g_h);
+  }
+  MG_TRY(mg::launch_prolong(m, P<int32_t>(M->anc[level]), static_cast<const double*>(dv),
+                            static_cast<const double*>(db), o, st));
+  M->launches += 1;
+  return (flags & MG_HOST_PTRS) ? deliver(M->g_h, out, m * sizeof(double), flags, st) : MG_OK;
+}
+
+static bool tuning_ok(int batch, int tile_rows, int src_tile) {
+  if (batch != -1 && batch != 1 && batch != 2 && batch != 4) return false;
   if (tile_rows != -1 && (tile_rows < 0 || tile_rows % mg::kSliceH != 0 || tile_rows > 8192))
-    return MG_ERR_ARG;
+    return false;
   if (src_tile != -1 && src_tile != 4 && src_tile != 8 && src_tile != 16 && src_tile != 32 &&
       src_tile != 64)
-    return MG_ERR_ARG;
+    return false;
+  return true;
+}
+
+static void drop_graphs(mg_mesh* M) {
   DeviceGuard g(M->device);
   for (auto& kv : M->graphs) cudaGraphExecDestroy(kv.second);
   M->graphs.clear();
+}
+
+static void apply_tuning(mg_mesh::Tuning& t, int batch, int tile_rows, int src_tile) {
+  if (batch != -1) t.batch = batch;
+  if (tile_rows != -1) t.tile_rows = tile_rows;
+  if (src_tile != -1) t.src_tile = src_tile;
+}
+
+int mg_mesh_set_tuning(mg_mesh* M, int chunk, int batch, int tile_rows, int src_tile) {
+  if (!M) return MG_ERR_ARG;
+  if (chunk != -1 && (chunk < 0 || chunk == 1 || chunk % 2 != 0 || chunk > 4096)) return MG_ERR_ARG;
+  if (!tuning_ok(batch, tile_rows, src_tile)) return MG_ERR_ARG;
+  drop_graphs(M);
   if (chunk != -1) M->chunk = chunk;
-  if (batch != -1) M->batch = batch;
-  if (tile_rows != -1) M->tile_rows = tile_rows;
-  if (src_tile != -1) M->src_tile = src_tile;
+  for (auto& t : M->tune) apply_tuning(t, batch, tile_rows, src_tile);
+  return MG_OK;
+}
+
+int mg_mesh_set_kernel_tuning(mg_mesh* M, int kind, int batch, int tile_rows, int src_tile) {
+  if (!M || kind < 0 || kind > 2 || !tuning_ok(batch, tile_rows, src_tile)) return MG_ERR_ARG;
+  drop_graphs(M);
+  apply_tuning(M->tune[kind], batch, tile_rows, src_tile);
+  return MG_OK;
+}
+
+int mg_mesh_get_tuning(const mg_mesh* M, int32_t* out) {
+  if (!M || !out) return MG_ERR_ARG;
+  out[0] = M->chunk;
+  for (int k = 0; k < 3; ++k) {
+    out[1 + 3 * k] = M->tune[k].batch;
+    out[2 + 3 * k] = M->tune[k].tile_rows;
+    out[3 + 3 * k] = M->tune[k].src_tile;
+  }
   return MG_OK;
 }
 
@@ -851,7 +935,8 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   MG_CU(cudaMemsetAsync(mu1, 0, state * sizeof(float), st));
   // accumulators: one set per source tile of the untiled kernel; the tiled
   // kernel sums all shots of a row inside its CTA
-  const int acc_sets = adjoint_tiled(M, pp.S_pad) ? 1 : mg::rows_tiles(pp.S_pad, M->batch);
+  const int acc_sets =
+      adjoint_tiled(M, pp.S_pad) ? 1 : mg::rows_tiles(pp.S_pad, M->tune[2].batch);
   const size_t acc = (size_t)acc_sets * n;
   MG_TRY(ensure(M->G, 4 * acc * sizeof(float)));
   MG_CU(cudaMemsetAsync(M->G.p, 0, 4 * acc * sizeof(float), st));
@@ -866,7 +951,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.w = wd;
   aa.nt = nt;
   aa.step_base = nullptr;
-  aa.batch = M->batch;
+  aa.batch = M->tune[2].batch;
   aa.G = G;
   aa.Gc = G + acc;
   aa.H = G + 2 * acc;
@@ -968,6 +1053,79 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   return deliver(M->g_h, g, nc * sizeof(double), flags, st);
 }
 
+int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const double* wavelet,
+                double dt, int steps, int level, void* stream, int flags, int32_t* chosen) {
+  if (!M || !eps || !shots || !wavelet || steps < 2 || level < 0 || level >= M->hm.n_levels)
+    return MG_ERR_ARG;
+  if (flags & ~MG_ALLOW_CFL) return MG_ERR_UNSUPPORTED;
+  MG_TRY(validate_shots(M, shots));
+  DeviceGuard guard(M->device);
+  if (!guard.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int S_pad = round_pad(shots->n_shots);
+  auto hit = M->tuned.find(S_pad);
+  if (hit != M->tuned.end()) {
+    drop_graphs(M);
+    for (int k = 0; k < 3; ++k) M->tune[k] = hit->second[k];
+    return chosen ? mg_mesh_get_tuning(M, chosen) : MG_OK;
+  }
+  // scratch: traces / weights [R][steps] and level vectors
+  const int64_t R = shots->rec_ptr[shots->n_shots];
+  const int64_t nl = M->hm.n_cells_level[level];
+  const size_t tb = ((size_t)R * steps * sizeof(float) + 255) / 256 * 256;
+  const size_t vb = ((size_t)nl * sizeof(double) + 255) / 256 * 256;
+  MG_TRY(ensure(M->tune_scratch, 2 * tb + 2 * vb));
+  unsigned char* base = P<unsigned char>(M->tune_scratch);
+  MG_CU(cudaMemsetAsync(base, 0, 2 * tb + 2 * vb, st));
+  float* tr = reinterpret_cast<float*>(base);
+  const float* w0 = reinterpret_cast<const float*>(base + tb);
+  const double* v0 = reinterpret_cast<const double*>(base + 2 * tb);
+  double* g0 = reinterpret_cast<double*>(base + 2 * tb + vb);
+  const int K = steps;  // one checkpoint segment
+  auto run = [&](int kind) -> int {
+    switch (kind) {
+      case 0: return mg_forward(M, eps, shots, wavelet, dt, steps, tr, 0, stream, flags);
+      case 1: return mg_jacobian_apply(M, level, eps, shots, wavelet, dt, steps, v0, tr, stream,
+                                       flags);
+      default: return mg_jacobian_T_apply(M, level, eps, shots, wavelet, dt, steps, w0, g0, K,
+                                          stream, flags);
+    }
+  };
+  const mg_mesh::Tuning cands[] = {{1, 0, 32},  {2, 0, 32},  {4, 0, 32},  {1, 64, 32},
+                                   {1, 64, 16}, {1, 128, 32}, {1, 128, 16}, {1, 256, 32},
+                                   {1, 256, 16}};
+  cudaEvent_t e0, e1;
+  MG_CU(cudaEventCreate(&e0));
+  MG_CU(cudaEventCreate(&e1));
+  int rc = MG_OK;
+  for (int kind = 0; kind < 3 && rc == MG_OK; ++kind) {
+    float best = 1e30f;
+    mg_mesh::Tuning pick = M->tune[kind];
+    for (const auto& c : cands) {
+      drop_graphs(M);
+      M->tune[kind] = c;
+      rc = run(kind);  // warm-up: tile tables, buffers, graphs
+      if (rc == MG_OK) {
+        cudaEventRecord(e0, st);
+        rc = run(kind);
+        cudaEventRecord(e1, st);
+      }
+      if (rc != MG_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MG_ERR_CUDA; break; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; pick = c; }
+    }
+    M->tune[kind] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graphs(M);
+  if (rc != MG_OK) return rc;
+  M->tuned[S_pad] = {M->tune[0], M->tune[1], M->tune[2]};
+  return chosen ? mg_mesh_get_tuning(M, chosen) : MG_OK;
+}
+
 }  // extern "C"
 
 namespace mg {
@@ -984,7 +1142,7 @@ int mesh_view(mg_mesh* M, MeshView* v) {
   v->row_abs = P<const double>(M->row_abs);
   v->perm_host = M->hm.perm.data();
   v->launches = &M->launches;
-  v->batch = M->batch;
+  v->batch = M->tune[0].batch;
   return MG_OK;
 }
 

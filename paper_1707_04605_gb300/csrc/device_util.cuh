@@ -41,13 +41,49 @@ __device__ __forceinline__ float4 scale4(float a, float4 x) {
 }
 
 // out = alpha self - beta old - gamma acc
+// The per-row combinations below are written with explicit round-to-nearest
+// intrinsics so that every kernel variant (row, tiled, multi-instance; any
+// launch shape) performs the same floating-point operations in the same
+// order, leaving the compiler no freedom to contract them differently.
+
+// out = alpha self - beta old - gamma acc, evaluated as
+// fma(-gamma, acc, fma(alpha, self, -(beta old))).
+__device__ __forceinline__ float leap1(float a, float b, float g, float self, float old,
+                                       float acc) {
+  return __fmaf_rn(-g, acc, __fmaf_rn(a, self, -__fmul_rn(b, old)));
+}
 __device__ __forceinline__ float4 leap(float4 c, float4 self, float4 old, float4 acc) {
-  float4 o;
-  o.x = c.x * self.x - c.y * old.x - c.z * acc.x;
-  o.y = c.x * self.y - c.y * old.y - c.z * acc.y;
-  o.z = c.x * self.z - c.y * old.z - c.z * acc.z;
-  o.w = c.x * self.w - c.y * old.w - c.z * acc.w;
-  return o;
+  return make_float4(leap1(c.x, c.y, c.z, self.x, old.x, acc.x),
+                     leap1(c.x, c.y, c.z, self.y, old.y, acc.y),
+                     leap1(c.x, c.y, c.z, self.z, old.z, acc.z),
+                     leap1(c.x, c.y, c.z, self.w, old.w, acc.w));
+}
+
+// Second and centred time differences of a state at one node.
+__device__ __forceinline__ float d2t(float next, float cur, float prev) {
+  return __fadd_rn(__fmaf_rn(-2.0f, cur, next), prev);
+}
+__device__ __forceinline__ float d1t(float next, float prev) { return __fsub_rn(next, prev); }
+
+// Tangent correction: dq+ -= cm (p+ - 2p + p-) + cd (p+ - p-).
+__device__ __forceinline__ float4 tangent_fix(float4 qn, float4 pn, float4 ps, float4 pold,
+                                              float2 tc) {
+#define MG_TF(X) \
+  qn.X = __fsub_rn(qn.X, __fmaf_rn(tc.x, d2t(pn.X, ps.X, pold.X), __fmul_rn(tc.y, d1t(pn.X, pold.X))));
+  MG_TF(x) MG_TF(y) MG_TF(z) MG_TF(w)
+#undef MG_TF
+  return qn;
+}
+
+// Adjoint time-sum terms of one float4 of shots:
+// t1 += p_k (mu_{k-1} - 2 mu_k + mu_{k+1}),  t2 += p_k (mu_{k-1} - mu_{k+1}).
+__device__ __forceinline__ void adj_terms(float4 pk, float4 out, float4 self, float4 old,
+                                          float& t1, float& t2) {
+#define MG_AT(X) \
+  t1 = __fmaf_rn(pk.X, d2t(out.X, self.X, old.X), t1); \
+  t2 = __fmaf_rn(pk.X, d1t(out.X, old.X), t2);
+  MG_AT(x) MG_AT(y) MG_AT(z) MG_AT(w)
+#undef MG_AT
 }
 
 __device__ __forceinline__ void kahan_add(float* s, float* c, float term) {

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_step_single(StepArgs a, int shot) {
     const int2 ek = __ldg(r.e + k * kSliceH);
     acc = fmaf(__int_as_float(ek.y), __ldg(a.p + ek.x), acc);
   }
-  float out = c.x * self - c.y * old - c.z * acc;
+  float out = leap1(c.x, c.y, c.z, self, old, acc);
   const int l = a.step + (a.step_base ? *a.step_base : 0);
   const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
   for (int q = s0; q < s1; ++q)
@@ -171,6 +171,20 @@ __global__ void k_copy_f4(const float4* __restrict__ src, float4* __restrict__ d
 
 
 }  // namespace
+
+namespace {
+__global__ void k_prolong(int64_t m, const int32_t* anc, const double* v, const double* base,
+                          double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) out[e] = (base ? base[e] : 0.0) + v[anc[e]];
+}
+}  // namespace
+
+int launch_prolong(int64_t m, const int32_t* anc, const double* v, const double* base,
+                   double* out, cudaStream_t st) {
+  k_prolong<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, anc, v, base, out);
+  return check_launch();
+}
 
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st) {
   k_step_single<<<(a.K.n + 255) / 256, 256, 0, st>>>(a, shot);

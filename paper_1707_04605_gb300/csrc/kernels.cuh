@@ -157,6 +157,10 @@ int launch_cell_gradient(const GradArgs& a, cudaStream_t st);
 int launch_restrict(int64_t nc, const int64_t* ptr, const int32_t* idx,
                     const double* g_fine, double* g_out, cudaStream_t st);
 
+// out[e] = (base ? base[e] : 0) + v[anc[e]], e < m.
+int launch_prolong(int64_t m, const int32_t* anc, const double* v, const double* base,
+                   double* out, cudaStream_t st);
+
 // Small helpers.
 int launch_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
 int launch_add_int(int32_t* p, int32_t v, cudaStream_t st);

@@ -199,11 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
   // dp+ = alpha dp - beta dp- - gamma K dp - cm (p+ - 2p + p-) - cd (p+ - p-)
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
-    qn[j] = leap(c, qs[j], qold[j], qacc[j]);
-#define MG_TAN(X) \
-  qn[j].X -= tc.x * ((pn[j].X - 2.0f * ps[j].X) + pold[j].X) + tc.y * (pn[j].X - pold[j].X);
-    MG_TAN(x) MG_TAN(y) MG_TAN(z) MG_TAN(w)
-#undef MG_TAN
+    qn[j] = tangent_fix(leap(c, qs[j], qold[j], qacc[j]), pn[j], ps[j], pold[j], tc);
     st4(a.f.pout + ro + 4 * LPR * j, pn[j]);
     st4(a.qm + ro + 4 * LPR * j, qn[j]);
   }
@@ -250,11 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       st4(a.mu1 + ro + 4 * LPR * j, out[j]);
-#define MG_ACC(X)                                                                \
-  t1 = fmaf(pk[j].X, (out[j].X - 2.0f * self[j].X) + old[j].X, t1);              \
-  t2 = fmaf(pk[j].X, out[j].X - old[j].X, t2);
-      MG_ACC(x) MG_ACC(y) MG_ACC(z) MG_ACC(w)
-#undef MG_ACC
+      adj_terms(pk[j], out[j], self[j], old[j], t1, t2);
     }
   }
 #pragma unroll

@@ -298,10 +298,7 @@ __global__ void __launch_bounds__(kTThreads) k_tangent_tiled(TangentArgs a, DevT
         }
       }
       // dp+ = alpha dp - beta dp- - gamma K dp - cm (p+ - 2p + p-) - cd (p+ - p-)
-      float4 qn = leap(c, qs, qold, qacc);
-#define MG_TAN(X) qn.X -= tc.x * ((pn.X - 2.0f * ps.X) + pold.X) + tc.y * (pn.X - pold.X);
-      MG_TAN(x) MG_TAN(y) MG_TAN(z) MG_TAN(w)
-#undef MG_TAN
+      const float4 qn = tangent_fix(leap(c, qs, qold, qacc), pn, ps, pold, tc);
       const size_t ro = (size_t)row * ld + src0;
       st4(a.f.pout + ro, pn);
       st4(a.qm + ro, qn);
@@ -375,11 +372,7 @@ __global__ void __launch_bounds__(kTThreads) k_adjoint_tiled(AdjointArgs a, DevT
             add_comp(out, d, c.w * __ldg(a.w + (size_t)__ldg(a.ev.rec_trace + q) * a.nt + (k - 1)));
         }
         st4(a.mu1 + (size_t)(tl.t0 + li) * a.ld + src0, out);
-#define MG_ACC(X)                                                              \
-  t1 = fmaf(pk.X, (out.X - 2.0f * self.X) + old.X, t1);                        \
-  t2 = fmaf(pk.X, out.X - old.X, t2);
-        MG_ACC(x) MG_ACC(y) MG_ACC(z) MG_ACC(w)
-#undef MG_ACC
+        adj_terms(pk, out, self, old, t1, t2);
       }
 #pragma unroll
       for (int off = LPR / 2; off > 0; off >>= 1) {

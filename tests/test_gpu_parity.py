@@ -251,6 +251,32 @@ def test_launch_shapes_give_identical_results(mg, chunk, batch, tile_rows, src_t
     assert rel_l2(out[2].cpu().numpy(), ref[2].cpu().numpy()) < 1e-5
 
 
+def test_autotune_picks_valid_shapes_and_keeps_results(mg):
+    w = configs.asteroid_2d(n_refine=2, S=64, nt=256)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    v = _dev(np.random.default_rng(5).standard_normal(w.mesh.n_cells[1]))
+    W = _dev(np.random.default_rng(6).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    t = mesh.autotune(eps, w.shots, s, dt, steps=64, level=1)
+    for kind in ("forward", "tangent", "adjoint"):
+        assert t[kind]["batch"] in (1, 2, 4)
+        assert t[kind]["tile_rows"] in (0, 64, 128, 256)
+    assert mesh.autotune(eps, w.shots, s, dt, steps=64, level=1) == t   # cached
+    out = run()
+    assert torch.equal(ref[0], out[0])
+    assert torch.equal(ref[1], out[1])
+    assert rel_l2(out[2].cpu().numpy(), ref[2].cpu().numpy()) < 1e-5
+
+
 def test_jacobian_square_disc_2d(mg):
     """4225 nodes, 2000 steps: a level-1 column J e_j and J^T w vs oracle."""
     w = configs.square_disc_2d()
