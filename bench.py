@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--src-tile", type=int, default=-1, help="shots per staged pass")
     ap.add_argument("--chunk", type=int, default=-1, help="leapfrog steps per CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--lane-vec", type=int, default=-1,
+                    help="row kernels: float4 vectors of shots per lane (1, 2, 4)")
+    ap.add_argument("--hbm-only", action="store_true",
+                    help="only the 3D ellipsoid forward measurement")
     return ap.parse_args()
 
 
@@ -139,7 +143,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def hbm_leg(mg, torch, dev, nt=300):
+def hbm_leg(mg, torch, dev, nt=300, args=None):
     """The 3D ellipsoid workload (1,814,385 nodes, 64 shots; each state is
     464 MB, far beyond L2): the batched forward step over `nt` leapfrog steps,
     where the step kernel is bound by HBM bandwidth."""
@@ -148,16 +152,23 @@ def hbm_leg(mg, torch, dev, nt=300):
     eps = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps)
     wav = torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
-    mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
+    if args is not None and (args.tile_rows != -1 or args.src_tile != -1 or args.lane_vec != -1):
+        mesh.set_kernel_tuning("forward", args.lane_vec, args.tile_rows, args.src_tile)
+    else:
+        mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
     tuning = mesh.tuning()
     mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
+    if args is not None and args.profile:
+        torch.cuda.profiler.start()
     e0.record(stream)
     mg.forward(mesh, eps, w.shots, wav, dt)
     e1.record(stream)
     torch.cuda.synchronize()
+    if args is not None and args.profile:
+        torch.cuda.profiler.stop()
     s = e0.elapsed_time(e1) / 1e3
     n, S = w.n_nodes, w.shots.n_shots
     info = mesh.info()
@@ -260,6 +271,15 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
+    if args.hbm_only:
+        from paper_1707_04605_gb300 import build as _b
+
+        _b.build()
+        import paper_1707_04605_gb300 as mg
+
+        torch.cuda.set_device(dev)
+        print(json.dumps(hbm_leg(mg, torch, dev, nt=args.nt or 300, args=args)))
+        return 0
     torch.cuda.set_device(dev)
     from paper_1707_04605_gb300 import build as _build
 
@@ -272,7 +292,7 @@ def main():
 
     w = workload_for_rank(rank, args.nt)
     mesh = mg.mesh_from_workload(w)
-    mesh.set_tuning(args.chunk, -1, args.tile_rows, args.src_tile)
+    mesh.set_tuning(args.chunk, args.lane_vec, args.tile_rows, args.src_tile)
     n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
     eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)
@@ -282,7 +302,8 @@ def main():
     v = np.zeros(nlev)
     v[np.random.default_rng(0).integers(nlev)] = 1.0
     v_d = torch.as_tensor(v, dtype=torch.float64, device=dev)
-    if args.tile_rows == -1 and args.src_tile == -1 and not args.no_autotune:
+    if (args.tile_rows == -1 and args.src_tile == -1 and args.lane_vec == -1
+            and not args.no_autotune):
         # launch shapes per kernel kind, timed on this problem (setup, untimed)
         mesh.autotune(eps_d, w.shots, wav_d, dt, steps=128, level=LEVEL)
     tuning = mesh.tuning()
@@ -319,11 +340,15 @@ def main():
     clk = clocks_start() if rank == 0 else None
     launches0 = mesh.launch_count()
     times = []
+    if args.profile:
+        torch.cuda.profiler.start()            # profilers capture the timed steps only
     for _ in range(args.steps):
         flush.fill_(1.0)                       # evict L2 between timed steps
         evs = step(record=True)
         times.append(evs)
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
     if ws > 1:
         torch.distributed.barrier()
     launches = mesh.launch_count() - launches0

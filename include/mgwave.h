@@ -254,7 +254,9 @@ int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
  * least `steps` samples), keeps the fastest per kind on the handle and
  * returns it in chosen[10] (may be NULL).  Candidates: row kernels with 1,
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
- * per pass.  The choice is cached on the handle per padded shot count; a
+ * per pass.  Each candidate is timed as the best of three runs after the GPU
+ * has been warmed up.  The choice is cached on
+ * the handle per padded shot count; a
  * later call with the same count only re-applies it.  Synchronous.
  * flags: 0 or MG_ALLOW_CFL. */
 int mg_autotune(mg_mesh* mesh, const double* eps, const mg_shots* shots, const double* wavelet,

@@ -223,7 +223,7 @@ def test_adjoint_checkpoint_spacing_and_reuse(mg):
 
 @pytest.mark.parametrize("chunk,batch,tile_rows,src_tile", [
     (0, 1, 0, 32), (0, 2, 0, 32), (128, 4, 0, 32), (64, 2, 256, 16), (128, 1, 128, 64),
-    (128, 2, 64, 8), (0, 4, 512, 4)])
+    (128, 2, 64, 8), (0, 4, 512, 4), (128, 2, 128, 32), (0, 2, 64, 16)])
 def test_launch_shapes_give_identical_results(mg, chunk, batch, tile_rows, src_tile):
     """Graph replay vs plain launches, gather batches, shared-memory tiles of
     several sizes (including a ragged last tile) vs the untiled kernels: the
