@@ -11,6 +11,8 @@ Modules:
           CFL bound.
   wave  - forward traces, tangent (directional derivative), adjoint gradient,
           restriction to a coarse nested level.
+  projected - the time inner products of Sec. II ("Projected data"), the
+          projected data and the weights of its Jacobian transpose.
 
 Every function here is pinned by tests against facts that do not come from
 the oracle itself (tests/test_oracle_pins.py): exact discrete energy balance,
@@ -18,4 +20,4 @@ the closed-form leapfrog evolution of a Dirichlet eigenmode, the straight-ray
 travel time, complex-step and central finite differences, reciprocity, and
 the source's mass balance.
 """
-from . import fem, wave  # noqa: F401
+from . import fem, projected, wave  # noqa: F401
