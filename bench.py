@@ -409,6 +409,30 @@ def main():
     single_rate = n * 4 * nt / (e0.elapsed_time(e1) / 1e3)
     fwd_rate = n * S * nt / (statistics.mean(fwd_ms) / 1e3)
 
+    # projected data (Sec. II): the two time inner products of every trace
+    # pair and the adjoint weights of the projected Jacobian, on this step's
+    # traces (device-resident, timed with CUDA events)
+    yd = torch.as_tensor(np.ascontiguousarray(y), dtype=torch.float32, device=dev)
+    zd = torch.ones((2, R), dtype=torch.float64, device=dev)
+    proj = {}
+    for name, fn, nbytes in (
+            ("project", lambda: mg.project(yd, yd, dt), 8 * R * nt + 16 * R),
+            ("projected_weights", lambda: mg.projected_weights(yd, zd, dt), 8 * R * nt + 16 * R)):
+        for _ in range(3):
+            fn()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(20):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        us = a0.elapsed_time(a1) * 1e3 / 20
+        proj[name] = {"us": us, "GB_per_s": nbytes / (us * 1e-6) / 1e9,
+                      "bytes_per_launch": nbytes}
+    proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
+                    "the projected Jacobian products cost one jacobian_apply / "
+                    "jacobian_T_apply each (the forward and adjoint phases above)")
+
     if rank != 0:
         return 0
     # roofline of the batched forward step kernel: algorithmic bytes per launch
@@ -442,6 +466,7 @@ def main():
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "projected_data": proj,
     }
     if not args.no_hbm_leg:
         out["hbm_workload"] = hbm_leg(mg, torch, dev)

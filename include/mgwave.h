@@ -244,23 +244,69 @@ int mg_jacobian_T_apply_batch(int n_inst, mg_mesh* const* meshes, const int* lev
 #define MG_KERNEL_ADJOINT 2
 int mg_mesh_set_kernel_tuning(mg_mesh* mesh, int kind, int batch, int tile_rows, int src_tile);
 
-/* Current tuning into out[10]: chunk, then (batch, tile_rows, src_tile) for
- * the forward, tangent and adjoint kinds. */
+/* Shot groups of a kernel kind (kind = -1: all kinds): the padded shot
+ * columns are split into `groups` equal groups (1, 2, 4 or 8) and, inside
+ * each CUDA-graph chunk of steps (forward, tangent) and each checkpoint
+ * segment (recompute, reverse), every group advances through all the steps
+ * before the next group starts.  The shots are independent, so the results
+ * are the same; the states a step touches shrink by the group count, which
+ * lets them stay in L2 across consecutive steps.  A count whose group width
+ * is not a power of two >= 4 up to 128 or a multiple of 128 runs as one
+ * group; steps outside graphs run ungrouped.  Default 1.  Drops the cached
+ * graphs.  Errors: MG_ERR_ARG for other values. */
+int mg_mesh_set_shot_groups(mg_mesh* mesh, int kind, int groups);
+
+/* Current tuning into out[13]: chunk, then (batch, tile_rows, src_tile,
+ * groups) for the forward, tangent and adjoint kinds. */
 int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
 
 /* Autotuner: times every candidate launch shape of each kernel kind on the
  * caller's problem (steps leapfrog steps of mg_forward, mg_jacobian_apply
  * and mg_jacobian_T_apply on `level`, device pointers; wavelet must hold at
  * least `steps` samples), keeps the fastest per kind on the handle and
- * returns it in chosen[10] (may be NULL).  Candidates: row kernels with 1,
+ * returns it in chosen[13] (may be NULL).  Candidates: row kernels with 1,
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
- * per pass.  Each candidate is timed as the best of three runs after the GPU
- * has been warmed up.  The choice is cached on
+ * per pass; then 2, 4 and 8 shot groups on the two fastest of those.  Each
+ * candidate is timed as the best of three runs after the GPU has been
+ * warmed up.  The choice is cached on
  * the handle per padded shot count; a
  * later call with the same count only re-applies it.  Synchronous.
  * flags: 0 or MG_ALLOW_CFL. */
 int mg_autotune(mg_mesh* mesh, const double* eps, const mg_shots* shots, const double* wavelet,
                 double dt, int steps, int level, void* stream, int flags, int32_t* chosen);
+
+/* Projected data (Sec. II, "Projected data"): the time inner products
+ *   <a, b>_1 = int_0^T a b dt,   <a, b>_2 = (1/T) int_0^T t a b dt
+ * of every trace pair, with sample l of a trace at t_l = (l + 1) dt (the
+ * state p_{l+1}), T = nt dt and the right-endpoint rectangle rule
+ * (sum_l dt a_l b_l, and (1/T) sum_l dt t_l a_l b_l).  y^(j)_i = <u_i, u_i>_j
+ * gives the projected data of traces u, y0^(j)_i = <u_i, u0_i>_j their
+ * projection on simulated traces u0; y^(2)/y^(1) is the relative integrated
+ * travel time of a pulse.  Since the measured u does not depend on the
+ * parameters, the projected Jacobian is d<u, u0>_j / dc = <u, J_c u0>_j:
+ * mg_project(u, J v) applies it, and mg_jacobian_T_apply with the weights of
+ * mg_projected_weights applies its transpose.
+ *   a, b: [n_traces][nt] FP32 traces; y: [2][n_traces] FP64 out (row 0
+ *   <a_i, b_i>_1, row 1 <a_i, b_i>_2), accumulated in FP64 from the FP32
+ *   samples in an order fixed by nt alone.
+ *   flags: 0 (device pointers, asynchronous on `stream`) or MG_HOST_PTRS
+ *   (host pointers; the call copies in and out and returns when y is on the
+ *   host).
+ * n_traces = 0 does nothing and succeeds (the pointers may then be NULL).
+ * Errors: MG_ERR_ARG (null pointer, n_traces < 0, nt < 1, dt <= 0),
+ * MG_ERR_UNSUPPORTED (other flags), MG_ERR_OOM, MG_ERR_CUDA. */
+int mg_project(const float* a, const float* b, int64_t n_traces, int nt, double dt, double* y,
+               void* stream, int flags);
+
+/* Trace weights of the projected Jacobian transpose: for a cotangent z
+ * ([2][n_traces] FP64) of the projected data <u_i, .>_j, the weights
+ *   w_i(t_l) = dt (z[0][i] + z[1][i] t_l / T) u_i(t_l)
+ * satisfy <w, d> = sum_{i,j} z[j][i] <u_i, d_i>_j for every trace
+ * perturbation d, so mg_jacobian_T_apply(..., w, ...) returns J_proj^T z.
+ *   u: [n_traces][nt] FP32; w: [n_traces][nt] FP32 out (FP64 arithmetic,
+ *   rounded once).  flags, errors: as mg_project. */
+int mg_projected_weights(const float* u, const double* z, int64_t n_traces, int nt, double dt,
+                         float* w, void* stream, int flags);
 
 /* Nested prolongation of level-cell values to the finest cells (Sec. II-B:
  * eps_r = sum_j c_j chi'_j): out[e] = base[e] + v[anc_level(e)] for every

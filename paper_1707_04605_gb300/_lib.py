@@ -74,6 +74,11 @@ SIGNATURES = {
     "mg_prolong": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int]),
     "mg_mesh_set_kernel_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
+                             C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_projected_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                       C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_mesh_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mg_shots), C.c_void_p,
                               C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),

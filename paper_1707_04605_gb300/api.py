@@ -124,14 +124,21 @@ class Mesh:
                                                     int(tile_rows), int(src_tile)),
                 "mg_mesh_set_kernel_tuning")
 
+    def set_shot_groups(self, groups: int, kind: str = None):
+        """Shot groups advanced one after another per graph chunk / checkpoint
+        segment (mg_mesh_set_shot_groups); kind None sets all kinds."""
+        k = -1 if kind is None else self.KINDS[kind]
+        L.check(self._lib.mg_mesh_set_shot_groups(self.handle, k, int(groups)),
+                "mg_mesh_set_shot_groups")
+
     def tuning(self) -> dict:
-        out = np.zeros(10, dtype=np.int32)
+        out = np.zeros(13, dtype=np.int32)
         L.check(self._lib.mg_mesh_get_tuning(self.handle, C.c_void_p(out.ctypes.data)),
                 "mg_mesh_get_tuning")
         d = {"chunk": int(out[0])}
         for name, k in self.KINDS.items():
-            d[name] = {"batch": int(out[1 + 3 * k]), "tile_rows": int(out[2 + 3 * k]),
-                       "src_tile": int(out[3 + 3 * k])}
+            d[name] = {"batch": int(out[1 + 4 * k]), "tile_rows": int(out[2 + 4 * k]),
+                       "src_tile": int(out[3 + 4 * k]), "groups": int(out[4 + 4 * k])}
         return d
 
     def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,
@@ -141,7 +148,7 @@ class Mesh:
         sh = Shots.of(shots)
         eps, pe = _dev(eps, "float64")
         wavelet, pw = _dev(wavelet, "float64")
-        out = np.zeros(10, dtype=np.int32)
+        out = np.zeros(13, dtype=np.int32)
         L.check(self._lib.mg_autotune(self.handle, pe, C.byref(sh.c), pw, float(dt), int(steps),
                                       int(level), _stream_ptr(stream),
                                       L.MG_ALLOW_CFL if allow_cfl else 0,
@@ -292,6 +299,59 @@ def prolong(mesh: Mesh, level, v, base=None, stream=None):
         rc = lib.mg_prolong(mesh.handle, int(level), pv, bh[1], _ptr(out), None, L.MG_HOST_PTRS)
     L.check(rc, "mg_prolong")
     return out
+
+
+def _traces_pair(a, b, b_dtype):
+    """Marshal a [R, nt] float32 and a second array of dtype b_dtype."""
+    if _is_cuda(a):
+        a, pa = _dev(a, "float32")
+        b, pb = _dev(b, b_dtype)
+        return True, (a, pa), (b, pb)
+    a, pa = _host(a, np.float32)
+    b, pb = _host(b, np.dtype(b_dtype))
+    return False, (a, pa), (b, pb)
+
+
+def project(a, b, dt, stream=None):
+    """Projected data [2, n_traces] float64 of trace pairs (mg_project): row 0
+    <a_i, b_i>_1, row 1 <a_i, b_i>_2."""
+    lib = L.load()
+    dev, (a, pa), (b, pb) = _traces_pair(a, b, "float32")
+    if tuple(a.shape) != tuple(b.shape) or len(a.shape) != 2:
+        raise ValueError("a and b must both be [n_traces, nt]")
+    R, nt = int(a.shape[0]), int(a.shape[1])
+    out = _alloc(dev, (2, R), "float64", a)
+    rc = lib.mg_project(pa, pb, R, nt, float(dt), _ptr(out),
+                        _stream_ptr(stream) if dev else None, 0 if dev else L.MG_HOST_PTRS)
+    L.check(rc, "mg_project")
+    return out
+
+
+def projected_weights(u, z, dt, stream=None):
+    """Trace weights [n_traces, nt] float32 (mg_projected_weights) whose
+    jacobian_T_apply is the projected-data Jacobian transpose of z [2, n_traces]."""
+    lib = L.load()
+    dev, (u, pu), (z, pz) = _traces_pair(u, z, "float64")
+    R, nt = int(u.shape[0]), int(u.shape[1])
+    if tuple(z.shape) != (2, R):
+        raise ValueError("z must be [2, n_traces]")
+    out = _alloc(dev, (R, nt), "float32", u)
+    rc = lib.mg_projected_weights(pu, pz, R, nt, float(dt), _ptr(out),
+                                  _stream_ptr(stream) if dev else None,
+                                  0 if dev else L.MG_HOST_PTRS)
+    L.check(rc, "mg_projected_weights")
+    return out
+
+
+def projected_jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, u, nt=None, **kw):
+    """Projected Jacobian times v: [2, n_traces] <u_i, (J v)_i>_j."""
+    return project(u, jacobian_apply(mesh, level, eps, shots, wavelet, dt, v, nt, **kw), dt)
+
+
+def projected_jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, z, u, nt=None, **kw):
+    """Projected Jacobian transpose times z [2, n_traces]: level-cell gradient."""
+    return jacobian_T_apply(mesh, level, eps, shots, wavelet, dt, projected_weights(u, z, dt),
+                            nt, **kw)
 
 
 def _ptr_array(xs):

@@ -106,11 +106,13 @@ struct mg_mesh {
   int chunk = 128;                        // steps per graph (even), 0 = off
   // per kernel kind (0 forward/recompute, 1 tangent, 2 adjoint): row-kernel
   // float4 vectors per lane, shared-memory tile rows (0 = row kernel), shots
-  // per staged pass
+  // per staged pass, shot groups advanced one after another inside a graph
+  // chunk or checkpoint segment
   struct Tuning {
     int batch = 1;
     int tile_rows = 0;
     int src_tile = 32;
+    int groups = 1;
   } tune[3];
   struct TileTables {
     Buf ell_off, ell_idx, ell_val, sinfo, halo_off, halo_cnt, halo;
@@ -337,12 +339,23 @@ int ensure_tiles(mg_mesh* M) {
   return MG_OK;
 }
 
-// Tiled launch description for a padded shot count and kernel kind (0
-// forward, 1 tangent, 2 adjoint), or n_tiles = 0 when that kind runs the
-// row kernel (no tiles, or the tiled footprint exceeds shared memory).  The
-// tangent stages two states per pass, so it passes half as many shots to
-// stay within the one-state footprint.
-mg::DevTiles dev_tiles(mg_mesh* M, int S_pad, int kind) {
+// Shot columns per group of a kernel kind: S_pad / groups when that is a
+// valid launch width (a power of two >= 4 up to 128, or a multiple of 128),
+// else S_pad (one group).
+int group_cols(const mg_mesh* M, int kind, int S_pad) {
+  const int G = M->tune[kind].groups;
+  if (G <= 1 || S_pad % G) return S_pad;
+  const int W = S_pad / G;
+  const bool ok = W >= 4 && (W % 128 == 0 || (W <= 128 && (W & (W - 1)) == 0));
+  return ok ? W : S_pad;
+}
+
+// Tiled launch description for `cols` shot columns per launch and a kernel
+// kind (0 forward, 1 tangent, 2 adjoint), or n_tiles = 0 when that kind runs
+// the row kernel (no tiles, or the tiled footprint exceeds shared memory).
+// The tangent stages two states per pass, so it passes half as many shots
+// to stay within the one-state footprint.
+mg::DevTiles dev_tiles(mg_mesh* M, int cols, int kind) {
   mg::DevTiles T{};
   const int P = M->tune[kind].tile_rows;
   auto it = M->tiles.find(P);
@@ -359,14 +372,16 @@ mg::DevTiles dev_tiles(mg_mesh* M, int S_pad, int kind) {
   T.halo = P_<const int32_t>(D.halo);
   T.max_ell = D.max_ell;
   T.max_halo = D.max_halo;
-  T.st_w = std::min(M->tune[kind].src_tile, S_pad);
+  T.st_w = std::min(M->tune[kind].src_tile, cols);
   if (kind == 1) T.st_w = std::max(4, T.st_w / 2);
   if (mg::tiled_smem_bytes(T, kind) > (size_t)M->smem_optin) T.n_tiles = 0;
   return T;
 }
 
+// One launch over the shot columns [a.col0, a.col0 + a.cols) (cols = 0:
+// all S_pad columns).
 int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
-  const mg::DevTiles T = dev_tiles(M, S_pad, 0);
+  const mg::DevTiles T = dev_tiles(M, a.cols ? a.cols : S_pad, 0);
   if (T.n_tiles) return mg::launch_step_tiled(a, T, st);
   mg::StepArgs b = a;
   b.batch = M->tune[0].batch;
@@ -374,21 +389,27 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
 }
 
 int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st) {
-  const mg::DevTiles T = dev_tiles(M, S_pad, 1);
+  const mg::DevTiles T = dev_tiles(M, a.f.cols ? a.f.cols : S_pad, 1);
   if (T.n_tiles) return mg::launch_tangent_tiled(a, T, st);
   mg::TangentArgs b = a;
   b.f.batch = M->tune[1].batch;
   return mg::launch_tangent(b, S_pad, st);
 }
 
-bool adjoint_tiled(mg_mesh* M, int S_pad) { return dev_tiles(M, S_pad, 2).n_tiles > 0; }
-
 int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st) {
-  const mg::DevTiles T = dev_tiles(M, S_pad, 2);
+  const mg::DevTiles T = dev_tiles(M, a.cols ? a.cols : S_pad, 2);
   if (T.n_tiles) return mg::launch_adjoint_tiled(a, T, st);
   mg::AdjointArgs b = a;
   b.batch = M->tune[2].batch;
   return mg::launch_adjoint(b, S_pad, st);
+}
+
+// Accumulator sets of the adjoint when every launch covers `cols` columns:
+// one for the tiled kernel (a CTA sums all shots of its rows, launches run
+// one after another), else one per source tile of the whole shot range.
+int adjoint_sets(mg_mesh* M, int S_pad, int cols) {
+  if (dev_tiles(M, cols, 2).n_tiles) return 1;
+  return (S_pad / cols) * mg::rows_tiles(cols, M->tune[2].batch);
 }
 
 mg::StepArgs step_args(mg_mesh* M, const Prep& pp, int ld, int nt) {
@@ -467,8 +488,9 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
     int32_t* base = P<int32_t>(M->step_base);
     MG_TRY(mg::launch_set_int(base, 0, st));
     M->launches += 1;
+    const int W = group_cols(M, 0, pp.S_pad), NG = pp.S_pad / W;
     const std::string key = key_of("fwd", {p, pm, traces, a.wavelet, a.coef, a.ev.src_ptr, base},
-                                   {pp.S_pad, pp.S, pp.R, nt, C, n});
+                                   {pp.S_pad, pp.S, pp.R, nt, C, n, W});
     for (; l + C <= nt; l += C) {
       if (ckpt && l % ckpt_every == 0) {
         float* slot = ckpt + (size_t)(l / ckpt_every) * 2 * state;
@@ -476,18 +498,22 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
         MG_TRY(mg::launch_copy_f4(pm, slot + state, (int64_t)state, st));
         M->launches += 2;
       }
-      MG_TRY(run_graph(M, key, C + 1, st, [&](cudaStream_t cs) {
+      MG_TRY(run_graph(M, key, NG * C + 1, st, [&](cudaStream_t cs) {
         mg::StepArgs b = a;
         b.step_base = base;
-        float* x = p;
-        float* y = pm;
-        for (int j = 0; j < C; ++j) {
-          b.p = x;
-          b.pm = y;
-          b.pout = y;
-          b.step = j;
-          MG_TRY(do_step(M, b, pp.S_pad, cs));
-          std::swap(x, y);
+        b.cols = W;
+        for (int g = 0; g < NG; ++g) {   // each shot group runs the whole chunk
+          b.col0 = g * W;
+          float* x = p;
+          float* y = pm;
+          for (int j = 0; j < C; ++j) {
+            b.p = x;
+            b.pm = y;
+            b.pout = y;
+            b.step = j;
+            MG_TRY(do_step(M, b, pp.S_pad, cs));
+            std::swap(x, y);
+          }
         }
         return mg::launch_add_int(base, C, cs);
       }));
@@ -713,13 +739,23 @@ int mg_mesh_set_kernel_tuning(mg_mesh* M, int kind, int batch, int tile_rows, in
   return MG_OK;
 }
 
+int mg_mesh_set_shot_groups(mg_mesh* M, int kind, int groups) {
+  if (!M || kind < -1 || kind > 2 || (groups != 1 && groups != 2 && groups != 4 && groups != 8))
+    return MG_ERR_ARG;
+  drop_graphs(M);
+  for (int k = 0; k < 3; ++k)
+    if (kind == -1 || kind == k) M->tune[k].groups = groups;
+  return MG_OK;
+}
+
 int mg_mesh_get_tuning(const mg_mesh* M, int32_t* out) {
   if (!M || !out) return MG_ERR_ARG;
   out[0] = M->chunk;
   for (int k = 0; k < 3; ++k) {
-    out[1 + 3 * k] = M->tune[k].batch;
-    out[2 + 3 * k] = M->tune[k].tile_rows;
-    out[3 + 3 * k] = M->tune[k].src_tile;
+    out[1 + 4 * k] = M->tune[k].batch;
+    out[2 + 4 * k] = M->tune[k].tile_rows;
+    out[3 + 4 * k] = M->tune[k].src_tile;
+    out[4 + 4 * k] = M->tune[k].groups;
   }
   return MG_OK;
 }
@@ -852,23 +888,29 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
     int32_t* base = P<int32_t>(M->step_base);
     MG_TRY(mg::launch_set_int(base, 0, st));
     M->launches += 1;
+    const int W = group_cols(M, 1, pp.S_pad), NG = pp.S_pad / W;
     const std::string key = key_of("tan", {p, pm, q, qm, tr, a.f.wavelet, a.f.coef, a.tcoef,
-                                           a.f.ev.src_ptr, base}, {pp.S_pad, pp.S, pp.R, nt, C, n});
+                                           a.f.ev.src_ptr, base},
+                                   {pp.S_pad, pp.S, pp.R, nt, C, n, W});
     for (; l + C <= nt; l += C) {
-      MG_TRY(run_graph(M, key, C + 1, st, [&](cudaStream_t cs) {
+      MG_TRY(run_graph(M, key, NG * C + 1, st, [&](cudaStream_t cs) {
         mg::TangentArgs b = a;
         b.f.step_base = base;
-        float *x = p, *y = pm, *u = q, *z = qm;
-        for (int j = 0; j < C; ++j) {
-          b.f.p = x;
-          b.f.pm = y;
-          b.f.pout = y;
-          b.q = u;
-          b.qm = z;
-          b.f.step = j;
-          MG_TRY(do_tangent(M, b, pp.S_pad, cs));
-          std::swap(x, y);
-          std::swap(u, z);
+        b.f.cols = W;
+        for (int g = 0; g < NG; ++g) {   // each shot group runs the whole chunk
+          b.f.col0 = g * W;
+          float *x = p, *y = pm, *u = q, *z = qm;
+          for (int j = 0; j < C; ++j) {
+            b.f.p = x;
+            b.f.pm = y;
+            b.f.pout = y;
+            b.q = u;
+            b.qm = z;
+            b.f.step = j;
+            MG_TRY(do_tangent(M, b, pp.S_pad, cs));
+            std::swap(x, y);
+            std::swap(u, z);
+          }
         }
         return mg::launch_add_int(base, C, cs);
       }));
@@ -933,10 +975,15 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   float* mu1 = P<float>(M->stD);
   MG_CU(cudaMemsetAsync(mu, 0, state * sizeof(float), st));
   MG_CU(cudaMemsetAsync(mu1, 0, state * sizeof(float), st));
+  // Shot groups: every recompute and reverse launch covers the columns of
+  // one group; each group runs a whole segment before the next one (the
+  // forward kind's grouping for the recompute, the adjoint's for the
+  // reverse steps).
+  const int Wf = group_cols(M, 0, pp.S_pad), NGf = pp.S_pad / Wf;
+  const int Wa = group_cols(M, 2, pp.S_pad), NGa = pp.S_pad / Wa;
   // accumulators: one set per source tile of the untiled kernel; the tiled
   // kernel sums all shots of a row inside its CTA
-  const int acc_sets =
-      adjoint_tiled(M, pp.S_pad) ? 1 : mg::rows_tiles(pp.S_pad, M->tune[2].batch);
+  const int acc_sets = adjoint_sets(M, pp.S_pad, Wa);
   const size_t acc = (size_t)acc_sets * n;
   MG_TRY(ensure(M->G, 4 * acc * sizeof(float)));
   MG_CU(cudaMemsetAsync(M->G.p, 0, 4 * acc * sizeof(float), st));
@@ -974,33 +1021,41 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       MG_TRY(mg::launch_set_int(base, l0, st));
       M->launches += 1;
       const std::string kr = key_of("rec", {seg, fa.wavelet, fa.coef, fa.ev.src_ptr, base},
-                                    {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n});
-      MG_TRY(run_graph(M, kr, ckpt_every, st, [&](cudaStream_t cs) {
+                                    {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n, Wf});
+      MG_TRY(run_graph(M, kr, NGf * ckpt_every, st, [&](cudaStream_t cs) {
         mg::StepArgs b = fa;
         b.step_base = base;
-        for (int j = 1; j <= ckpt_every; ++j) {
-          b.p = seg + (size_t)j * state;
-          b.pm = seg + (size_t)(j - 1) * state;
-          b.pout = seg + (size_t)(j + 1) * state;
-          b.step = j - 1;
-          MG_TRY(do_step(M, b, pp.S_pad, cs));
+        b.cols = Wf;
+        for (int g = 0; g < NGf; ++g) {
+          b.col0 = g * Wf;
+          for (int j = 1; j <= ckpt_every; ++j) {
+            b.p = seg + (size_t)j * state;
+            b.pm = seg + (size_t)(j - 1) * state;
+            b.pout = seg + (size_t)(j + 1) * state;
+            b.step = j - 1;
+            MG_TRY(do_step(M, b, pp.S_pad, cs));
+          }
         }
         return MG_OK;
       }));
       const std::string ka = key_of("adj", {seg, mu, mu1, wd, aa.coef, aa.ev.rec_ptr, G, base},
-                                    {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n});
-      MG_TRY(run_graph(M, ka, ckpt_every, st, [&](cudaStream_t cs) {
+                                    {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n, Wa});
+      MG_TRY(run_graph(M, ka, NGa * ckpt_every, st, [&](cudaStream_t cs) {
         mg::AdjointArgs b = aa;
         b.step_base = base;
-        float* x = mu;
-        float* y = mu1;
-        for (int r = ckpt_every; r >= 1; --r) {   // k = l0 + r
-          b.mu = x;
-          b.mu1 = y;
-          b.pk = seg + (size_t)(r + 1) * state;
-          b.k = r;
-          MG_TRY(do_adjoint(M, b, pp.S_pad, cs));
-          std::swap(x, y);
+        b.cols = Wa;
+        for (int g = 0; g < NGa; ++g) {
+          b.col0 = g * Wa;
+          float* x = mu;
+          float* y = mu1;
+          for (int r = ckpt_every; r >= 1; --r) {   // k = l0 + r
+            b.mu = x;
+            b.mu1 = y;
+            b.pk = seg + (size_t)(r + 1) * state;
+            b.k = r;
+            MG_TRY(do_adjoint(M, b, pp.S_pad, cs));
+            std::swap(x, y);
+          }
         }
         return MG_OK;
       }));
@@ -1015,15 +1070,23 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       MG_TRY(do_step(M, fa, pp.S_pad, st));
       M->launches += 1;
     }
-    for (int k = l1; k > l0; --k) {
-      aa.mu = mu;
-      aa.mu1 = mu1;
-      aa.pk = seg + (size_t)(k - l0 + 1) * state;
-      aa.k = k;
-      MG_TRY(do_adjoint(M, aa, pp.S_pad, st));
-      M->launches += 1;
-      std::swap(mu, mu1);
+    for (int g = 0; g < NGa; ++g) {
+      mg::AdjointArgs b = aa;
+      b.col0 = g * Wa;
+      b.cols = Wa;
+      float* x = mu;
+      float* y = mu1;
+      for (int k = l1; k > l0; --k) {
+        b.mu = x;
+        b.mu1 = y;
+        b.pk = seg + (size_t)(k - l0 + 1) * state;
+        b.k = k;
+        MG_TRY(do_adjoint(M, b, pp.S_pad, st));
+        M->launches += 1;
+        std::swap(x, y);
+      }
     }
+    if ((l1 - l0) % 2) std::swap(mu, mu1);
   }
   // per-cell gradient (FP64), then restriction to the level
   MG_TRY(ensure(M->gfine, M->hm.m * sizeof(double)));
@@ -1091,9 +1154,10 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
                                           stream, flags);
     }
   };
-  const mg_mesh::Tuning cands[] = {{1, 0, 32},  {2, 0, 32},   {4, 0, 32},   {1, 64, 32},
-                                   {1, 64, 16}, {1, 128, 32}, {1, 128, 16}, {1, 256, 32},
-                                   {1, 256, 16}};
+  const mg_mesh::Tuning shapes[] = {{1, 0, 32},  {2, 0, 32},   {4, 0, 32},   {1, 64, 32},
+                                    {1, 64, 16}, {1, 128, 32}, {1, 128, 16}, {1, 256, 32},
+                                    {1, 256, 16}};
+  const int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
   cudaEvent_t e0, e1;
   MG_CU(cudaEventCreate(&e0));
   MG_CU(cudaEventCreate(&e1));
@@ -1102,26 +1166,46 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
   // would otherwise bias against the first candidates
   for (int i = 0; i < 4 && rc == MG_OK; ++i) rc = run(2);
   if (rc == MG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MG_ERR_CUDA;
+  auto time_of = [&](int kind, const mg_mesh::Tuning& c, float* out) -> int {
+    drop_graphs(M);
+    M->tune[kind] = c;
+    int r = run(kind);  // warm-up: tile tables, buffers, graphs
+    float cand = 1e30f;
+    for (int rep = 0; rep < 3 && r == MG_OK; ++rep) {  // best of three
+      cudaEventRecord(e0, st);
+      r = run(kind);
+      cudaEventRecord(e1, st);
+      if (r != MG_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { r = MG_ERR_CUDA; break; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cand = std::min(cand, ms);
+    }
+    *out = cand;
+    return r;
+  };
   for (int kind = 0; kind < 3 && rc == MG_OK; ++kind) {
-    float best = 1e30f;
-    mg_mesh::Tuning pick = M->tune[kind];
-    for (const auto& c : cands) {
-      drop_graphs(M);
-      M->tune[kind] = c;
-      rc = run(kind);  // warm-up: tile tables, buffers, graphs
-      float cand = 1e30f;
-      for (int rep = 0; rep < 3 && rc == MG_OK; ++rep) {  // best of three
-        cudaEventRecord(e0, st);
-        rc = run(kind);
-        cudaEventRecord(e1, st);
+    // launch shapes with one shot group, then 2, 4 and 8 groups on the two
+    // fastest shapes (groups that do not give a valid width are skipped)
+    float ms[n_shapes];
+    for (int i = 0; i < n_shapes && rc == MG_OK; ++i) rc = time_of(kind, shapes[i], &ms[i]);
+    if (rc != MG_OK) break;
+    int order[n_shapes];
+    for (int i = 0; i < n_shapes; ++i) order[i] = i;
+    std::stable_sort(order, order + n_shapes, [&](int x, int y) { return ms[x] < ms[y]; });
+    float best = ms[order[0]];
+    mg_mesh::Tuning pick = shapes[order[0]];
+    for (int top = 0; top < 2 && rc == MG_OK; ++top) {
+      for (int G : {2, 4, 8}) {
+        mg_mesh::Tuning c = shapes[order[top]];
+        c.groups = G;
+        M->tune[kind] = c;
+        if (group_cols(M, kind, S_pad) == S_pad) continue;
+        float t = 0.0f;
+        rc = time_of(kind, c, &t);
         if (rc != MG_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MG_ERR_CUDA; break; }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cand = std::min(cand, ms);
+        if (t < best) { best = t; pick = c; }
       }
-      if (rc != MG_OK) break;
-      if (cand < best) { best = cand; pick = c; }
     }
     M->tune[kind] = pick;
   }

@@ -40,6 +40,8 @@ struct StepArgs {
   int32_t step;             // l = step + (step_base ? *step_base : 0)
   const int32_t* step_base;
   int32_t batch;            // row kernels: float4 vectors (4 shots each) per lane, 1/2/4
+  int32_t col0 = 0;         // first shot column advanced (multiple of the launch's shot tile)
+  int32_t cols = 0;         // shot columns advanced, [col0, col0 + cols); 0 = all ld
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -67,7 +69,9 @@ struct AdjointArgs {
   int32_t k;                // reverse step index k + (step_base ? *step_base : 0)
   const int32_t* step_base;
   int32_t batch;
-  float* G;                 // [tiles][n] sums
+  int32_t col0 = 0;         // shot columns [col0, col0 + cols) as in StepArgs
+  int32_t cols = 0;
+  float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;
   float* Hc;
@@ -99,9 +103,11 @@ int launch_step_tiled(const StepArgs& a, const DevTiles& T, cudaStream_t st);
 int launch_tangent_tiled(const TangentArgs& a, const DevTiles& T, cudaStream_t st);
 int launch_adjoint_tiled(const AdjointArgs& a, const DevTiles& T, cudaStream_t st);
 
-// Source tiles (grid.y) of the row kernels for a padded shot count and
-// `nv` float4 per lane; the adjoint keeps one accumulator set per tile.
-int rows_tiles(int S_pad, int nv);
+// Source tiles (grid.y) of the row kernels for `cols` shot columns per
+// launch and `nv` float4 per lane; the adjoint keeps one accumulator set per
+// source tile of the whole padded shot range (S_pad / cols launches of
+// rows_tiles(cols, nv) tiles each).
+int rows_tiles(int cols, int nv);
 
 int launch_step(const StepArgs& a, int S_pad, cudaStream_t st);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);

@@ -189,11 +189,11 @@ __global__ void __launch_bounds__(kTThreads) k_step_tiled(StepArgs a, DevTiles T
   const size_t hrows = (size_t)(T.P + T.max_halo) * ST;  // offset of the row-only state
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lr = lane % LPR;
   const int l = a.step + (a.step_base ? *a.step_base : 0);
-  const int NST = a.ld / ST;
+  const int NST = (a.cols ? a.cols : a.ld) / ST;
   auto issue = [&](int st) {
     float* b = PASS_BUF(st & 1);
-    stage_rows<ST>(tl, halo, tl.nrows, a.p, a.ld, st, b);
-    stage_rows<ST>(tl, halo, tl.Pt, a.pm, a.ld, st, b + hrows);
+    stage_rows<ST>(tl, halo, tl.nrows, a.p + a.col0, a.ld, st, b);
+    stage_rows<ST>(tl, halo, tl.Pt, a.pm + a.col0, a.ld, st, b + hrows);
     cp_commit();
   };
   issue(0);
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kTThreads) k_step_tiled(StepArgs a, DevTiles T
     __syncthreads();
     const float* cur = PASS_BUF(st & 1);
     const float* pmr = cur + hrows;
-    const int src0 = st * ST + lr * 4;
+    const int src0 = a.col0 + st * ST + lr * 4;
     for (int li = warp * RPW + lane / LPR; li < tl.Pt; li += kTWarps * RPW) {
       float4 self;
       const float4 acc = row_acc<ST>(sinfo, idx, val, cur, li, lr, self);
@@ -256,14 +256,15 @@ __global__ void __launch_bounds__(kTThreads) k_tangent_tiled(TangentArgs a, DevT
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lr = lane % LPR;
   const int ld = a.f.ld;
   const int l = a.f.step + (a.f.step_base ? *a.f.step_base : 0);
-  const int NST = ld / ST;
+  const int c0 = a.f.col0;
+  const int NST = (a.f.cols ? a.f.cols : ld) / ST;
   // pass buffer: [p rows+halo][q rows+halo][p_{l-1} rows][q_{l-1} rows]
   auto issue = [&](int st) {
     float* b = PASS_BUF(st & 1);
-    stage_rows<ST>(tl, halo, tl.nrows, a.f.p, ld, st, b);
-    stage_rows<ST>(tl, halo, tl.nrows, a.q, ld, st, b + hrows);
-    stage_rows<ST>(tl, halo, tl.Pt, a.f.pm, ld, st, b + 2 * hrows);
-    stage_rows<ST>(tl, halo, tl.Pt, a.qm, ld, st, b + 2 * hrows + prow);
+    stage_rows<ST>(tl, halo, tl.nrows, a.f.p + c0, ld, st, b);
+    stage_rows<ST>(tl, halo, tl.nrows, a.q + c0, ld, st, b + hrows);
+    stage_rows<ST>(tl, halo, tl.Pt, a.f.pm + c0, ld, st, b + 2 * hrows);
+    stage_rows<ST>(tl, halo, tl.Pt, a.qm + c0, ld, st, b + 2 * hrows + prow);
     cp_commit();
   };
   issue(0);
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kTThreads) k_tangent_tiled(TangentArgs a, DevT
     const float* bq = bp + hrows;
     const float* bpm = bp + 2 * hrows;
     const float* bqm = bpm + prow;
-    const int src0 = st * ST + lr * 4;
+    const int src0 = c0 + st * ST + lr * 4;
     for (int li = warp * RPW + lane / LPR; li < tl.Pt; li += kTWarps * RPW) {
       float4 ps, qs, acc, qacc;
       row_acc2<ST>(sinfo, idx, val, bp, bq, li, lr, ps, qs, acc, qacc);
@@ -333,13 +334,13 @@ __global__ void __launch_bounds__(kTThreads) k_adjoint_tiled(AdjointArgs a, DevT
   const size_t prow = (size_t)T.P * ST;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lr = lane % LPR;
   const int k = a.k + (a.step_base ? *a.step_base : 0);
-  const int NST = a.ld / ST;
+  const int NST = (a.cols ? a.cols : a.ld) / ST;
   // pass buffer: [mu_k rows+halo][mu_{k+1} rows][p_k rows]
   auto issue = [&](int st) {
     float* b = PASS_BUF(st & 1);
-    stage_rows<ST>(tl, halo, tl.nrows, a.mu, a.ld, st, b);
-    stage_rows<ST>(tl, halo, tl.Pt, a.mu1, a.ld, st, b + hrows);
-    stage_rows<ST>(tl, halo, tl.Pt, a.pk, a.ld, st, b + hrows + prow);
+    stage_rows<ST>(tl, halo, tl.nrows, a.mu + a.col0, a.ld, st, b);
+    stage_rows<ST>(tl, halo, tl.Pt, a.mu1 + a.col0, a.ld, st, b + hrows);
+    stage_rows<ST>(tl, halo, tl.Pt, a.pk + a.col0, a.ld, st, b + hrows + prow);
     cp_commit();
   };
   issue(0);
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kTThreads) k_adjoint_tiled(AdjointArgs a, DevT
     const float* cur = PASS_BUF(st & 1);
     const float* b1 = cur + hrows;
     const float* bk = b1 + prow;
-    const int src0 = st * ST + lr * 4;
+    const int src0 = a.col0 + st * ST + lr * 4;
     for (int base = 0; base < tl.Pt; base += kTWarps * RPW) {
       const int li = base + warp * RPW + lane / LPR;
       float t1 = 0.0f, t2 = 0.0f;
@@ -435,8 +436,15 @@ size_t tiled_smem_bytes(const DevTiles& T, int kind) {
     default: return MG_ERR_ARG;                                                       \
   }
 
+// The passes cover shot columns [col0, col0 + cols): whole passes of st_w
+// shots inside ld, starting on a 16-byte boundary.
+bool tiled_range_ok(int col0, int cols, int ld, int st_w) {
+  if (!cols) cols = ld;
+  return col0 >= 0 && col0 % 4 == 0 && cols > 0 && col0 + cols <= ld && cols % st_w == 0;
+}
+
 int launch_step_tiled(const StepArgs& a, const DevTiles& T, cudaStream_t st) {
-  if (a.ld % T.st_w) return MG_ERR_ARG;
+  if (!tiled_range_ok(a.col0, a.cols, a.ld, T.st_w)) return MG_ERR_ARG;
   int rc = MG_OK;
   const size_t smem = tiled_smem_bytes(T, 0);
   MG_TILED_SWITCH(k_step_tiled, a, smem)
@@ -444,7 +452,7 @@ int launch_step_tiled(const StepArgs& a, const DevTiles& T, cudaStream_t st) {
 }
 
 int launch_tangent_tiled(const TangentArgs& a, const DevTiles& T, cudaStream_t st) {
-  if (a.f.ld % T.st_w) return MG_ERR_ARG;
+  if (!tiled_range_ok(a.f.col0, a.f.cols, a.f.ld, T.st_w)) return MG_ERR_ARG;
   int rc = MG_OK;
   const size_t smem = tiled_smem_bytes(T, 1);
   MG_TILED_SWITCH(k_tangent_tiled, a, smem)
@@ -452,7 +460,7 @@ int launch_tangent_tiled(const TangentArgs& a, const DevTiles& T, cudaStream_t s
 }
 
 int launch_adjoint_tiled(const AdjointArgs& a, const DevTiles& T, cudaStream_t st) {
-  if (a.ld % T.st_w) return MG_ERR_ARG;
+  if (!tiled_range_ok(a.col0, a.cols, a.ld, T.st_w)) return MG_ERR_ARG;
   int rc = MG_OK;
   const size_t smem = tiled_smem_bytes(T, 2);
   MG_TILED_SWITCH(k_adjoint_tiled, a, smem)

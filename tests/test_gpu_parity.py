@@ -251,6 +251,56 @@ def test_launch_shapes_give_identical_results(mg, chunk, batch, tile_rows, src_t
     assert rel_l2(out[2].cpu().numpy(), ref[2].cpu().numpy()) < 1e-5
 
 
+@pytest.mark.parametrize("groups,batch,tile_rows,src_tile", [
+    (2, 2, 0, 32), (4, 1, 0, 32), (8, 4, 0, 32), (2, 1, 64, 16), (4, 1, 128, 32), (8, 1, 64, 32),
+])
+def test_shot_groups_give_identical_results(mg, groups, batch, tile_rows, src_tile):
+    """Shot groups advanced one after another inside each graph chunk and
+    checkpoint segment: every shot sees the same arithmetic as in one group,
+    so forward and tangent traces carry the same bits; the adjoint's per-row
+    sums over shots are grouped differently (FP32 rounding)."""
+    w = configs.asteroid_2d(n_refine=1, S=100, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(64, batch, tile_rows, src_tile)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    v = _dev(np.random.default_rng(3).standard_normal(w.mesh.n_cells[1]))
+    W = _dev(np.random.default_rng(4).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    mesh.set_shot_groups(groups)
+    assert all(mesh.tuning()[k]["groups"] == groups for k in ("forward", "tangent", "adjoint"))
+    out = run()
+    assert torch.equal(ref[0], out[0])
+    assert torch.equal(ref[1], out[1])
+    assert rel_l2(out[2].cpu().numpy(), ref[2].cpu().numpy()) < 1e-5
+
+
+def test_wide_batch_row_shapes_cover_every_shot(mg):
+    """300 shots pad to 384 columns, which two float4 per lane (256-shot
+    source tiles) cannot divide: the row kernels fall back to a tile that
+    does, so every shot is advanced and matches the oracle."""
+    w = configs.asteroid_2d(n_refine=1, S=300, nt=200)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    ref = mg.forward(mesh, eps, w.shots, s, dt)
+    mesh.set_tuning(-1, 2, 0, 32)
+    out = mg.forward(mesh, eps, w.shots, s, dt)
+    assert torch.equal(ref, out)
+    picks = [0, 150, 299]
+    rows = w.shots.trace_rows(picks)
+    y = oracle_traces(w, dt, w.wavelet(dt), w.shots.subset(picks))
+    assert rel_l2(out.cpu().numpy()[rows], y) < TRACE_TOL
+
+
 def test_autotune_picks_valid_shapes_and_keeps_results(mg):
     w = configs.asteroid_2d(n_refine=2, S=64, nt=256)
     eps = _dev(w.eps)
