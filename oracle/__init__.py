@@ -13,6 +13,8 @@ Modules:
           restriction to a coarse nested level.
   projected - the time inner products of Sec. II ("Projected data"), the
           projected data and the weights of its Jacobian transpose.
+  inversion - the TV-regularised iteration, coarse-to-fine steps and
+          compression of Sec. II, dense on tiny problems.
 
 Every function here is pinned by tests against facts that do not come from
 the oracle itself (tests/test_oracle_pins.py): exact discrete energy balance,
@@ -20,4 +22,4 @@ the closed-form leapfrog evolution of a Dirichlet eigenmode, the straight-ray
 travel time, complex-step and central finite differences, reciprocity, and
 the source's mass balance.
 """
-from . import fem, projected, wave  # noqa: F401
+from . import fem, inversion, projected, wave  # noqa: F401
