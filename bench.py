@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--src-tile", type=int, default=-1, help="shots per staged pass")
     ap.add_argument("--chunk", type=int, default=-1, help="leapfrog steps per CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-inversion-leg", action="store_true",
+                    help="skip the TV-reconstruction timing")
     ap.add_argument("--lane-vec", type=int, default=-1,
                     help="row kernels: float4 vectors of shots per lane (1, 2, 4)")
     ap.add_argument("--hbm-only", action="store_true",
@@ -189,6 +191,48 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
 
 def peak_kind_note(kind):
     return "of measured" if kind == "measured" else "of fallback"
+
+
+def inversion_leg(mg, torch, mesh, w, eps_d, wav_d, dt, y, nt=1000, n_cg=3):
+    """One outer step of the coarse-to-fine TV reconstruction (levels 0 -> 1)
+    on the bench mesh over the first `nt` steps, n_cg CG iterations per
+    solve, against the cost of the J and J^T products it is made of."""
+    stream = torch.cuda.current_stream()
+    wav = wav_d[:nt].contiguous()
+    dy = torch.as_tensor(np.ascontiguousarray(y[:, :nt]), dtype=torch.float32,
+                         device=eps_d.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    kw = dict(level_f=1, alpha=1.0, beta=1.0, n_outer=1, n_cg=n_cg, cg_rtol=0.0,
+              ckpt_every=200)
+    mg.tv_reconstruct(mesh, 0, eps_d, w.shots, wav, dt, dy, **kw)       # warm-up
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    x, hist = mg.tv_reconstruct(mesh, 0, eps_d, w.shots, wav, dt, dy, **kw)
+    ev[1].record(stream)
+    v = torch.zeros(w.mesh.n_cells[1], dtype=torch.float64, device=eps_d.device)
+    v[0] = 1.0
+    mg.forward(mesh, eps_d, w.shots, wav, dt, ckpt_every=200, keep_checkpoints=True)
+    ev[2].record(stream)
+    jv = mg.jacobian_apply(mesh, 1, eps_d, w.shots, wav, dt, v)
+    ev[3].record(stream)
+    mg.jacobian_T_apply(mesh, 1, eps_d, w.shots, wav, dt, jv, ckpt_every=200,
+                        reuse_checkpoints=True)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0].elapsed_time(ev[1]) / 1e3
+    t_fwd = ev[1].elapsed_time(ev[2]) / 1e3
+    t_j = ev[2].elapsed_time(ev[3]) / 1e3
+    t_jt = ev[3].elapsed_time(ev[4]) / 1e3
+    it = int(hist[0, 0] + hist[0, 2])
+    # one forward with checkpoints; J: one per CG iteration + the fine residual;
+    # J^T: one per CG iteration + the two right-hand sides
+    parts = t_fwd + (it + 1) * t_j + (it + 2) * t_jt
+    return {"workload": f"{w.name} levels 0->1 ({w.mesh.n_cells[0]} -> {w.mesh.n_cells[1]} "
+                        f"cells), {nt} steps, 1 outer step, {n_cg} CG iterations per solve",
+            "seconds": total, "cg_iterations": [int(hist[0, 0]), int(hist[0, 2])],
+            "forward_J_JT_seconds": [t_fwd, t_j, t_jt],
+            "seconds_per_cg_iteration": total / max(1, it),
+            "overhead_vs_its_wave_solves": total / parts - 1.0}
 
 
 def cpu_baseline(w, dt, budget_s=20.0):
@@ -429,6 +473,8 @@ def main():
         us = a0.elapsed_time(a1) * 1e3 / 20
         proj[name] = {"us": us, "GB_per_s": nbytes / (us * 1e-6) / 1e9,
                       "bytes_per_launch": nbytes}
+    inversion = None if args.no_inversion_leg else inversion_leg(
+        mg, torch, mesh, w, eps_d, wav_d, dt, y)
     proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
                     "the projected Jacobian products cost one jacobian_apply / "
                     "jacobian_T_apply each (the forward and adjoint phases above)")
@@ -467,6 +513,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
         "projected_data": proj,
+        "tv_reconstruction": inversion,
     }
     if not args.no_hbm_leg:
         out["hbm_workload"] = hbm_leg(mg, torch, dev)

@@ -268,7 +268,8 @@ int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
  * per pass; then 2, 4 and 8 shot groups on the two fastest of those.  Each
  * candidate is timed as the best of three runs after the GPU has been
- * warmed up.  The choice is cached on
+ * warmed up; shapes within 1% of the fastest count as equal (the earliest
+ * listed wins) and shot groups must win by more than 1%.  The choice is cached on
  * the handle per padded shot count; a
  * later call with the same count only re-applies it.  Synchronous.
  * flags: 0 or MG_ALLOW_CFL. */
@@ -307,6 +308,59 @@ int mg_project(const float* a, const float* b, int64_t n_traces, int nt, double 
  *   rounded once).  flags, errors: as mg_project. */
 int mg_projected_weights(const float* u, const double* z, int64_t n_traces, int nt, double dt,
                          float* w, void* stream, int flags);
+
+/* TV-regularised reconstruction (Sec. II: reconstruction procedure,
+ * Eq. (tv_iteration) with the regularisation matrix (d_mat); coarse-to-fine
+ * approach, steps (1)-(5) with Eqs. (tv_iteration_0), (tv_iteration_2);
+ * compression of coefficients) on the exact Jacobian of the data at eps0.
+ *
+ * Solves, for the level-cell perturbation x of the permittivity (x0 = 0),
+ *   x_{l+1} = (L^T L + alpha D^T G_l D)^{-1} L^T dy,   G_0 = I,
+ *   G_l = diag(|D x_l|)^{-1} (entries below 1e-8 max |D x_l| raised to it),
+ * where L is the Jacobian of the data (traces, or projected data) with
+ * respect to the cell values and D has D_ij = -s_ij / s_max for cells
+ * sharing boundary measure s_ij and D_ii = beta + sum_j s_ij / s_max.
+ * Every linear system is solved matrix-free by conjugate gradients with
+ * FP64 vectors and inner products; each CG iteration applies L and L^T once
+ * (mg_jacobian_apply, mg_jacobian_T_apply on checkpoints written once by
+ * mg_forward at the start).
+ *
+ * level_f < 0: the single-level iteration on the cells of level_c.
+ * level_f > level_c: coarse-to-fine; every outer step updates the level_c
+ * cells, then solves for a correction in the fine fluctuations of level_f
+ * (basis: +1/-1 on adjacent children of a coarse cell along a breadth-first
+ * spanning tree of the children's facet adjacency rooted at the child with
+ * most sibling neighbours; in 2D the centre-corner pairs), restricted to
+ * the fluctuations of the ceil(keep_frac n_c) coarse cells with the largest
+ * |x_c| and regularised by D_level_f applied to the fluctuation.
+ *   data_mode  MG_DATA_TRACES: dy is [n_traces][nt] FP32 (y - y0), u unused.
+ *              MG_DATA_PROJECTED: dy is [2][n_traces] FP64 projected data
+ *              (see mg_project) and u the [n_traces][nt] FP32 traces they
+ *              are projected on.
+ *   x_out      [cells of level_f] (or of level_c) FP64: the final x.
+ *   history    optional host array [n_outer][4]: CG iterations and final
+ *              relative residual of the coarse and of the fine solve.
+ *   flags      MG_HOST_PTRS (eps0, wavelet, dy, u, x_out on the host),
+ *              MG_ALLOW_CFL.  Synchronous.
+ * Errors: MG_ERR_ARG (levels, params out of range, null pointers),
+ * MG_ERR_NESTING (children of a coarse cell not facet-connected), plus
+ * those of the Jacobian calls. */
+#define MG_DATA_TRACES    0
+#define MG_DATA_PROJECTED 1
+typedef struct {
+  double alpha;      /* regularisation weight, > 0 */
+  double beta;       /* diagonal weight of D, >= 0 */
+  int n_outer;       /* outer iterations, >= 1 */
+  int n_cg;          /* conjugate-gradient iterations per solve (upper bound), >= 1 */
+  double cg_rtol;    /* CG stops at ||r|| <= cg_rtol ||b|| */
+  double keep_frac;  /* compression: fraction of coarse cells kept, (0, 1] (paper: 1/3) */
+  int ckpt_every;    /* checkpoint spacing of the adjoint, >= 1 */
+} mg_tv_params;
+int mg_tv_reconstruct(mg_mesh* mesh, int level_c, int level_f, const double* eps0,
+                      const mg_shots* shots, const double* wavelet, double dt, int nt,
+                      int data_mode, const void* dy, const float* u,
+                      const mg_tv_params* params, double* x_out, double* history,
+                      void* stream, int flags);
 
 /* Nested prolongation of level-cell values to the finest cells (Sec. II-B:
  * eps_r = sum_j c_j chi'_j): out[e] = base[e] + v[anc_level(e)] for every

@@ -37,6 +37,16 @@ class mg_shots(C.Structure):
                 ("rec_ptr", C.POINTER(C.c_int64)), ("rec", C.POINTER(C.c_int32))]
 
 
+MG_DATA_TRACES = 0
+MG_DATA_PROJECTED = 1
+
+
+class mg_tv_params(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("n_outer", C.c_int),
+                ("n_cg", C.c_int), ("cg_rtol", C.c_double), ("keep_frac", C.c_double),
+                ("ckpt_every", C.c_int)]
+
+
 class mg_mesh_info_t(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_levels", C.c_int32), ("n_nodes", C.c_int64),
                 ("n_cells", C.c_int64), ("n_bnd", C.c_int64), ("nnz", C.c_int64),
@@ -75,6 +85,10 @@ SIGNATURES = {
                              C.c_void_p, C.c_int]),
     "mg_mesh_set_kernel_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int]),
     "mg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
                              C.c_void_p, C.c_void_p, C.c_int]),
     "mg_projected_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,

@@ -354,6 +354,38 @@ def projected_jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, z, u,
                             nt, **kw)
 
 
+def tv_reconstruct(mesh: Mesh, level_c, eps0, shots, wavelet, dt, dy, *, level_f=-1, u=None,
+                   alpha, beta=0.0, n_outer=3, n_cg=50, cg_rtol=1e-8, keep_frac=1.0 / 3.0,
+                   ckpt_every=256, nt=None, allow_cfl=False, stream=None):
+    """TV-regularised reconstruction (mg_tv_reconstruct): the level-cell
+    perturbation x (level_f cells when level_f >= 0, else level_c cells) and
+    the per-outer-step history [n_outer, 4] (CG iterations and relative
+    residual of the coarse and fine solves).  dy: trace residual [n_traces,
+    nt] float32, or projected data [2, n_traces] float64 with the traces u."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    projected = u is not None
+    extra = [(dy, "float64" if projected else "float32")]
+    if projected:
+        extra.append((u, "float32"))
+    dev, (eps0, pe), (wav, pw), ex, st, f0 = _prep(eps0, wavelet, extra, stream)
+    pdy = ex[0][1]
+    pu = ex[1][1] if projected else None
+    lev = level_f if level_f >= 0 else level_c
+    x = _alloc(dev, (mesh.n_cells_per_level[lev],), "float64", eps0)
+    hist = np.zeros((int(n_outer), 4), dtype=np.float64)
+    prm = L.mg_tv_params(float(alpha), float(beta), int(n_outer), int(n_cg), float(cg_rtol),
+                         float(keep_frac), int(ckpt_every))
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_tv_reconstruct(mesh.handle, int(level_c), int(level_f), pe, C.byref(sh.c), pw,
+                               float(dt), nt, L.MG_DATA_PROJECTED if projected else
+                               L.MG_DATA_TRACES, pdy, pu, C.byref(prm), _ptr(x),
+                               C.c_void_p(hist.ctypes.data), st, f)
+    L.check(rc, "mg_tv_reconstruct")
+    return x, hist
+
+
 def _ptr_array(xs):
     return (C.c_void_p * len(xs))(*[C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr")
                                                else x.ctypes.data) for x in xs])

@@ -323,6 +323,9 @@ int build_host_mesh(int dim, int n_levels, const double* coords, int64_t n_nodes
   hm.iperm = ord;
   hm.perm.assign(n_nodes, -1);
   for (int64_t r = 0; r < n_nodes; ++r) hm.perm[ord[r]] = (int32_t)r;
+  hm.coords.resize((size_t)n_nodes * dim);
+  for (int64_t r = 0; r < n_nodes; ++r)
+    for (int a = 0; a < dim; ++a) hm.coords[(size_t)r * dim + a] = coords[(size_t)ord[r] * dim + a];
 
   // ---- stiffness in row order, diagonal first -----------------------------
   hm.rowptr.assign(n_nodes + 1, 0);

@@ -24,6 +24,13 @@ struct MeshView {
 
 int mesh_view(mg_mesh* mesh, MeshView* out);
 
+struct HostMesh;
+// Host image of a handle's mesh (read-only), its device, and a way to count
+// launches made on its behalf by entry points outside capi.cu.
+const HostMesh* host_mesh(const mg_mesh* mesh);
+int mesh_device(const mg_mesh* mesh);
+void add_launches(mg_mesh* mesh, int64_t n);
+
 // One problem of a multi-instance batch, prepared on its own handle: device
 // inputs staged, coefficients and FP32 wavelet computed, event lists built,
 // and the handle's state / checkpoint / accumulator buffers sized.

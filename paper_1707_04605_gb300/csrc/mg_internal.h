@@ -33,6 +33,7 @@ struct HostMesh {
 
   std::vector<int32_t> perm;   // caller node -> row
   std::vector<int32_t> iperm;  // row -> caller node
+  std::vector<double> coords;  // [n][dim] node coordinates, rows
 
   // stiffness (rows/cols internal, diagonal first), FP64
   std::vector<int64_t> rowptr;

@@ -5,11 +5,11 @@
 // A trace holds one sample per leapfrog step, sample l being the field at
 // t_l = (l + 1) dt; T = nt dt.  The integrals are the right-endpoint sums
 //   <a, b>_1 = sum_l dt a_l b_l,   <a, b>_2 = (1/T) sum_l dt t_l a_l b_l,
-// accumulated in FP64 from FP32 samples.  One warp per trace: lane k sums
-// samples k, k + 32, ...; the 32 partial sums are combined by a fixed
-// butterfly, so the result does not depend on the launch.
+// accumulated in FP64 from FP32 samples.  One block per trace; the partial
+// sums are combined in a fixed order, so the result depends on nt alone.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/mgwave.h"
@@ -17,66 +17,72 @@
 namespace mg {
 namespace {
 
-constexpr int kProjWarps = 8;
+constexpr int kProjThreads = 256;
 
-__global__ void __launch_bounds__(32 * kProjWarps)
+// One block per trace: thread k sums samples k, k + 256, ... in FP64, then a
+// fixed shared-memory tree combines the 256 partial sums.
+__global__ void __launch_bounds__(kProjThreads)
     k_project(const float* __restrict__ a, const float* __restrict__ b, int64_t R, int nt,
               double dt, double* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * kProjWarps + (threadIdx.x >> 5);
-  if (i >= R) return;  // whole warps leave together (R is per warp)
+  __shared__ double s1s[kProjThreads], s2s[kProjThreads];
+  const int64_t i = blockIdx.x;
   const float* ai = a + i * nt;
   const float* bi = b + i * nt;
   double s1 = 0.0, s2 = 0.0;
-  for (int l = lane; l < nt; l += 32) {
+  for (int l = threadIdx.x; l < nt; l += kProjThreads) {
     const double ab = (double)__ldg(ai + l) * (double)__ldg(bi + l);
     s1 += ab;
     s2 += (double)(l + 1) * ab;  // t_l / dt
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  s1s[threadIdx.x] = s1;
+  s2s[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = kProjThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s1s[threadIdx.x] += s1s[threadIdx.x + w];
+      s2s[threadIdx.x] += s2s[threadIdx.x + w];
+    }
+    __syncthreads();
   }
-  if (lane == 0) {
+  if (threadIdx.x == 0) {
     const double T = (double)nt * dt;
-    y[i] = dt * s1;
-    y[R + i] = dt * (dt * s2) / T;
+    y[i] = dt * s1s[0];
+    y[R + i] = dt * (dt * s2s[0]) / T;
   }
 }
 
-// w_i(t_l) = dt (z1_i + z2_i t_l / T) u_i(t_l), evaluated in FP64, stored FP32.
+// w_i(t_l) = dt (z1_i + z2_i t_l / T) u_i(t_l), evaluated in FP64, stored FP32;
+// blockIdx.y strides over the traces.
 __global__ void k_projected_weights(const float* __restrict__ u, const double* __restrict__ z,
                                     int64_t R, int nt, double dt, float* __restrict__ w) {
-  const int64_t total = R * (int64_t)nt;
   const double T = (double)nt * dt;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = q / nt;
-    const int l = (int)(q - i * nt);
-    const double t = (double)(l + 1) * dt;
-    w[q] = (float)(dt * (__ldg(z + i) + __ldg(z + R + i) * t / T) * (double)__ldg(u + q));
+  for (int64_t i = blockIdx.y; i < R; i += gridDim.y) {
+    const double z1 = __ldg(z + i), z2 = __ldg(z + R + i);
+    const float* ui = u + i * nt;
+    float* wi = w + i * nt;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nt; l += gridDim.x * blockDim.x) {
+      const double t = (double)(l + 1) * dt;
+      wi[l] = (float)(dt * (z1 + z2 * t / T) * (double)__ldg(ui + l));
+    }
   }
 }
 
 int launch_project(const float* a, const float* b, int64_t R, int nt, double dt, double* y,
                    cudaStream_t st) {
-  const int64_t blocks = (R + kProjWarps - 1) / kProjWarps;
-  k_project<<<(unsigned)blocks, 32 * kProjWarps, 0, st>>>(a, b, R, nt, dt, y);
+  k_project<<<(unsigned)R, kProjThreads, 0, st>>>(a, b, R, nt, dt, y);
   return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
 int launch_projected_weights(const float* u, const double* z, int64_t R, int nt, double dt,
                              float* w, cudaStream_t st) {
-  const int64_t total = R * (int64_t)nt;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_projected_weights<<<(unsigned)blocks, 256, 0, st>>>(u, z, R, nt, dt, w);
+  const int bx = (int)std::min<int64_t>((nt + 255) / 256, 64);
+  const unsigned by = (unsigned)std::min<int64_t>(R, 65535);
+  k_projected_weights<<<dim3(bx, by), 256, 0, st>>>(u, z, R, nt, dt, w);
   return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
 bool args_ok(int64_t R, int nt, double dt) {
-  return R >= 0 && nt >= 1 && dt > 0.0 && dt < 1e300 && R < ((int64_t)1 << 31) / 32 &&
+  return R >= 0 && nt >= 1 && dt > 0.0 && dt < 1e300 && R < ((int64_t)1 << 31) &&
          R * (int64_t)nt < ((int64_t)1 << 40);
 }
 
