@@ -26,6 +26,13 @@ nesting map, because the permittivity is a sum of coarse-cell indicators
 
 Boundary modes: "abc" (D as above), "neumann" (D = 0) and "dirichlet"
 (D = 0 and boundary nodes held at zero after every step).
+
+Conductivity (optional): the sigma du/dt term of Eq. (pde1), i.e. the mass
+matrix R of App. A weighted by sigma, lumped like the eps-mass
+(R_ii = sum_{e contains i} sigma_e |e|/(d+1)), joins the damping and is
+centred in time with it: D above becomes D + R.  sigma is a fixed nuisance
+parameter (Sec. III): the tangent and the adjoint differentiate with respect
+to eps only.
 """
 from __future__ import annotations
 
@@ -37,7 +44,7 @@ from . import fem
 class Problem:
     """Assembled FP64 system for one mesh, permittivity and boundary mode."""
 
-    def __init__(self, coords, cells, bnd, eps, bc="abc"):
+    def __init__(self, coords, cells, bnd, eps, bc="abc", sigma=None):
         self.coords = np.asarray(coords, dtype=np.float64)
         self.cells = np.asarray(cells, dtype=np.int64)
         self.bnd = np.asarray(bnd, dtype=np.int64)
@@ -56,6 +63,10 @@ class Problem:
             self.D = np.zeros(self.n, dtype=self.m.dtype)
         else:
             raise ValueError(bc)
+        # lumped conductivity mass R, added to the damping
+        self.R = (np.zeros(self.n) if sigma is None
+                  else fem.lumped_mass(self.coords, self.cells, np.asarray(sigma, np.float64)))
+        self.D = self.D + self.R
         self.fixed = (np.unique(self.bnd.ravel()) if bc == "dirichlet"
                       else np.zeros(0, dtype=np.int64))
 
