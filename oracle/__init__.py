@@ -15,6 +15,8 @@ Modules:
           projected data and the weights of its Jacobian transpose.
   inversion - the TV-regularised iteration, coarse-to-fine steps and
           compression of Sec. II, dense on tiny problems.
+  approx_jacobian - the paper's approximate Jacobian (auxiliary sources,
+          Green's functions by reciprocity, coarse-mass multigrid variant).
 
 Every function here is pinned by tests against facts that do not come from
 the oracle itself (tests/test_oracle_pins.py): exact discrete energy balance,
@@ -22,4 +24,4 @@ the closed-form leapfrog evolution of a Dirichlet eigenmode, the straight-ray
 travel time, complex-step and central finite differences, reciprocity, and
 the source's mass balance.
 """
-from . import fem, inversion, projected, wave  # noqa: F401
+from . import approx_jacobian, fem, inversion, projected, wave  # noqa: F401
