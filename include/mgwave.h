@@ -45,6 +45,7 @@
 #ifndef MGWAVE_H
 #define MGWAVE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -362,12 +363,60 @@ int mg_tv_reconstruct(mg_mesh* mesh, int level_c, int level_f, const double* eps
                       const mg_tv_params* params, double* x_out, double* history,
                       void* stream, int flags);
 
+/* The paper's approximate Jacobian (App. A.1-A.3: auxiliary system,
+ * Green's functions by reciprocity, multigrid approach, Eq. (approx_2)).
+ *
+ * For shot s (source a_s, one receiver r_s) and level cell j:
+ *   L'_j(s)[l] = (|T'_j| / (d+1)) sum_{i in corners(j)} phi_{s,i}[l],
+ *   phi_{s,i} = H_{i,r_s} * z_{s,i},  z_{s,i}[l] = -(p_{l+1} - 2 p_l + p_{l-1})_i / dt^2,
+ * where p is the forward field of shot s, H_{i,r} the impulse response at
+ * node i of a unit source (s_0 = 1) at r, equal by the symmetry of the
+ * scheme to the response at r of a source at i, and corners(j) the d+1
+ * corner nodes of cell j (the descendant vertices used by exactly one
+ * descendant; MG_ERR_NESTING if a cell has not exactly d+1, i.e. the
+ * refinement is not regular).  The auxiliary sources of a coarse cell sit
+ * on its corners with the lumped coarse mass; the boundary-damping term of
+ * the exact tangent is not included (the paper's auxiliary source carries
+ * dC/dc only).  The Green's functions come from an impulse run rather than
+ * the regularised deconvolution of App. A.2 (the impulse run is exact).
+ * Cost: two batched forward runs recording every corner node, and FP32 FFT
+ * convolutions.
+ *   shots      exactly one receiver per shot (MG_ERR_UNSUPPORTED otherwise).
+ *   u          [n_shots][nt] FP32 traces the columns are projected on
+ *              (required with Lp, else may be NULL).
+ *   Lp         optional out [2][n_shots][cells of level] FP64:
+ *              <u_s, L'_j(s)>_k of Sec. II (projected data), k = 1, 2.
+ *   phi        optional out [n_shots][n_nodes][nt] FP32 node responses.
+ *   nodes      optional out [n_nodes] caller ids of the corner nodes, in
+ *              the order of phi; n_nodes (required) receives their count.
+ *              With Lp and phi both NULL only the node list is returned.
+ *   mem_budget device bytes for the per-chunk work buffers (0: 8 GiB);
+ *              shots are processed in chunks that fit.
+ *   flags      MG_HOST_PTRS (eps, wavelet, u, Lp, phi host), MG_ALLOW_CFL.
+ *              Synchronous. */
+int mg_approx_jacobian(mg_mesh* mesh, int level, const double* eps, const mg_shots* shots,
+                       const double* wavelet, double dt, int nt, const float* u, double* Lp,
+                       float* phi, int32_t* nodes, int64_t* n_nodes, size_t mem_budget,
+                       void* stream, int flags);
+
 /* Nested prolongation of level-cell values to the finest cells (Sec. II-B:
  * eps_r = sum_j c_j chi'_j): out[e] = base[e] + v[anc_level(e)] for every
  * finest cell e (base may be NULL for 0).  v: [cells of level], base, out:
  * [n_cells]; data pointers (float64). */
 int mg_prolong(mg_mesh* mesh, int level, const double* v, const double* base, double* out,
                void* stream, int flags);
+
+/* Conductivity of the mesh (the sigma du/dt term of Eq. (pde1); the mass
+ * matrix R of App. A weighted by sigma), used by every later call on the
+ * handle.  Lumped like the eps-mass (R_ii = sum_{e contains i} sigma_e
+ * |e|/(d+1)) and centred in time with the boundary damping:
+ *   (M + dt/2 (D + R)) p_{l+1} = 2 M p_l - (M - dt/2 (D + R)) p_{l-1} - dt^2 (K p_l - s_l e).
+ * sigma is a fixed nuisance parameter (Sec. III): the Jacobians remain
+ * derivatives with respect to eps.  sigma: [n_cells] FP64 >= 0 (finest cells,
+ * caller order), device pointer or host pointer with MG_HOST_PTRS (checked
+ * there: MG_ERR_ARG for a negative or non-finite value); NULL removes it
+ * (the default: no conductivity).  Invalidates kept checkpoints. */
+int mg_mesh_set_conductivity(mg_mesh* mesh, const double* sigma, void* stream, int flags);
 
 /* Release the handle's scratch (states, checkpoints, graphs). */
 int mg_mesh_trim(mg_mesh* mesh);

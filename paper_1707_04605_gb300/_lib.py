@@ -85,10 +85,14 @@ SIGNATURES = {
                              C.c_void_p, C.c_int]),
     "mg_mesh_set_kernel_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_mesh_set_conductivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int]),
+    "mg_approx_jacobian": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int]),
     "mg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
                              C.c_void_p, C.c_void_p, C.c_int]),
     "mg_projected_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,

@@ -131,6 +131,18 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_shot_groups(self.handle, k, int(groups)),
                 "mg_mesh_set_shot_groups")
 
+    def set_conductivity(self, sigma, stream=None):
+        """Per-cell conductivity (mg_mesh_set_conductivity); None removes it."""
+        if sigma is None:
+            rc = self._lib.mg_mesh_set_conductivity(self.handle, None, None, 0)
+        elif _is_cuda(sigma):
+            sigma, ps = _dev(sigma, "float64")
+            rc = self._lib.mg_mesh_set_conductivity(self.handle, ps, _stream_ptr(stream), 0)
+        else:
+            sigma, ps = _host(sigma, np.float64)
+            rc = self._lib.mg_mesh_set_conductivity(self.handle, ps, None, L.MG_HOST_PTRS)
+        L.check(rc, "mg_mesh_set_conductivity")
+
     def tuning(self) -> dict:
         out = np.zeros(13, dtype=np.int32)
         L.check(self._lib.mg_mesh_get_tuning(self.handle, C.c_void_p(out.ctypes.data)),

@@ -125,6 +125,8 @@ struct mg_mesh {
   std::map<int, std::array<Tuning, 3>> tuned;
   cudaStream_t cap = nullptr;             // private capture stream
   std::map<std::string, cudaGraphExec_t> graphs;
+  Buf sigma;                              // conductivity per finest cell (FP64)
+  bool has_sigma = false;
   Buf tr;                                 // internal trace buffer [R][nt]
   Buf tune_scratch;                       // autotuner inputs/outputs
 };
@@ -151,6 +153,7 @@ mg::CoefArgs coef_args(mg_mesh* M, const double* eps, double dt) {
   c.bc = M->hm.bc;
   c.coef = P<float4>(M->coef);
   c.mass = nullptr;
+  c.sigma = M->has_sigma ? P<double>(M->sigma) : nullptr;
   return c;
 }
 
@@ -674,6 +677,30 @@ int mg_mesh_trim(mg_mesh* M) {
   }
   M->ev_valid = false;
   M->ck_valid = false;
+  return MG_OK;
+}
+
+int mg_mesh_set_conductivity(mg_mesh* M, const double* sigma, void* stream, int flags) {
+  if (!M) return MG_ERR_ARG;
+  if (flags & ~MG_HOST_PTRS) return MG_ERR_UNSUPPORTED;
+  DeviceGuard g(M->device);
+  if (!g.ok) return MG_ERR_CUDA;
+  M->ck_valid = false;  // checkpoints of an earlier forward no longer apply
+  if (!sigma) {
+    M->has_sigma = false;
+    return MG_OK;
+  }
+  const size_t bytes = (size_t)M->hm.m * sizeof(double);
+  if (flags & MG_HOST_PTRS)
+    for (int64_t e = 0; e < M->hm.m; ++e)
+      if (!(sigma[e] >= 0.0) || !std::isfinite(sigma[e])) return MG_ERR_ARG;
+  MG_TRY(ensure(M->sigma, bytes));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MG_CU(cudaMemcpyAsync(M->sigma.p, sigma, bytes,
+                        (flags & MG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                        st));
+  if (flags & MG_HOST_PTRS) MG_CU(cudaStreamSynchronize(st));
+  M->has_sigma = true;
   return MG_OK;
 }
 

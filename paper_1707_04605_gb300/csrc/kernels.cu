@@ -67,6 +67,15 @@ __global__ void __launch_bounds__(256) k_step_single(StepArgs a, int shot) {
   }
 }
 
+// Lumped conductivity mass R_rr = sum_{e contains r} sigma_e |e|/(d+1): the
+// sigma du/dt term of Eq. (pde1), centred in time with the boundary damping.
+__device__ __forceinline__ double sigma_mass(const CoefArgs& a, int r) {
+  double R = 0.0;
+  if (a.sigma)
+    for (int64_t q = a.nc_ptr[r]; q < a.nc_ptr[r + 1]; ++q) R += a.sigma[a.nc_cell[q]] * a.nc_w[q];
+  return R;
+}
+
 __global__ void k_coefs(CoefArgs a) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.n) return;
@@ -75,6 +84,7 @@ __global__ void k_coefs(CoefArgs a) {
   if (a.bc == MG_BC_ABC1)
     for (int64_t q = a.nf_ptr[r]; q < a.nf_ptr[r + 1]; ++q)
       D += sqrt(a.eps[a.nf_cell[q]]) * a.nf_w[q];
+  D += sigma_mass(a, r);
   const double w = m + 0.5 * a.dt * D;
   float4 c = make_float4((float)(2.0 * m / w), (float)((m - 0.5 * a.dt * D) / w),
                          (float)(a.dt * a.dt / w), (float)(1.0 / w));
@@ -99,6 +109,7 @@ __global__ void k_tangent_coefs(TangentCoefArgs a) {
       D += se * a.c.nf_w[q];
       dD += a.v[a.anc[e]] / (2.0 * se) * a.c.nf_w[q];
     }
+  D += sigma_mass(a.c, r);  // sigma is not a parameter: no dD term
   const double w = m + 0.5 * a.c.dt * D;
   float2 t = make_float2((float)(dm / w), (float)(a.c.dt * dD / (2.0 * w)));
   if (a.c.bc == MG_BC_DIRICHLET && a.c.is_bnd[r]) t = make_float2(0.f, 0.f);

@@ -125,6 +125,7 @@ struct CoefArgs {
   int32_t bc;
   float4* coef;             // out
   double* mass;             // out (may be null)
+  const double* sigma = nullptr;  // conductivity per finest cell, or null (none)
 };
 int launch_coefs(const CoefArgs& a, cudaStream_t st);
 
