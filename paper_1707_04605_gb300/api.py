@@ -398,6 +398,39 @@ def tv_reconstruct(mesh: Mesh, level_c, eps0, shots, wavelet, dt, dy, *, level_f
     return x, hist
 
 
+def approx_jacobian(mesh: Mesh, level, eps, shots, wavelet, dt, u=None, *, want_phi=False,
+                    mem_budget=0, nt=None, allow_cfl=False, stream=None):
+    """The paper's approximate Jacobian (mg_approx_jacobian).  Returns a dict:
+    nodes (caller ids of the level's corner nodes), Lp ([2, n_shots, cells]
+    projected columns <u_s, L'_j(s)>_k when u is given) and phi ([n_shots,
+    n_nodes, nt] node responses when want_phi)."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    extra = [(u, "float32")] if u is not None else []
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, extra, stream)
+    pu = ex[0][1] if u is not None else None
+    n_max = int(mesh.info()["n_nodes"])
+    nodes = np.zeros(n_max, dtype=np.int32)
+    count = C.c_int64(0)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_approx_jacobian(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt), nt,
+                                None, None, None, C.c_void_p(nodes.ctypes.data),
+                                C.byref(count), 0, st, f)
+    L.check(rc, "mg_approx_jacobian")
+    N = int(count.value)
+    nl = mesh.n_cells_per_level[level]
+    Lp = _alloc(dev, (2, sh.n_shots, nl), "float64", eps) if u is not None else None
+    phi = _alloc(dev, (sh.n_shots, N, nt), "float32", eps) if want_phi else None
+    if Lp is not None or phi is not None:
+        rc = lib.mg_approx_jacobian(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
+                                    nt, pu, _ptr(Lp) if Lp is not None else None,
+                                    _ptr(phi) if phi is not None else None, None,
+                                    C.byref(count), int(mem_budget), st, f)
+        L.check(rc, "mg_approx_jacobian")
+    return {"nodes": nodes[:N], "Lp": Lp, "phi": phi}
+
+
 def _ptr_array(xs):
     return (C.c_void_p * len(xs))(*[C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr")
                                                else x.ctypes.data) for x in xs])

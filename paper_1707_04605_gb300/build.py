@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmgwave.so")
 SOURCES = ["mesh_host.cpp", "kernels.cu", "kernels_rows.cu", "kernels_tiled.cu", "capi.cu",
            "static_scratch.cu", "batch.cu", "projected.cu",
-           "inversion.cu"]
+           "inversion.cu", "approx.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lgomp",
-                                                          "-Xlinker", "--no-undefined"]
+                                                          "-lcufft", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
