@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=-1, help="leapfrog steps per CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-inversion-leg", action="store_true",
-                    help="skip the TV-reconstruction timing")
+                    help="skip the TV-reconstruction and approximate-Jacobian timings")
     ap.add_argument("--lane-vec", type=int, default=-1,
                     help="row kernels: float4 vectors of shots per lane (1, 2, 4)")
     ap.add_argument("--hbm-only", action="store_true",
@@ -233,6 +233,43 @@ def inversion_leg(mg, torch, mesh, w, eps_d, wav_d, dt, y, nt=1000, n_cg=3):
             "forward_J_JT_seconds": [t_fwd, t_j, t_jt],
             "seconds_per_cg_iteration": total / max(1, it),
             "overhead_vs_its_wave_solves": total / parts - 1.0}
+
+
+def approx_jacobian_leg(mg, torch, mesh, w, eps_d, wav_d, dt, y, level=1, n_check=3):
+    """The paper's approximate projected Jacobian (all cells of `level`, every
+    shot) against exact J e_j columns: time and the relative error on a few
+    cells."""
+    stream = torch.cuda.current_stream()
+    u = torch.as_tensor(np.ascontiguousarray(y), dtype=torch.float32, device=eps_d.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    out = mg.approx_jacobian(mesh, level, eps_d, w.shots, wav_d, dt, u=u,
+                             mem_budget=16 << 30)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    Lp = out["Lp"]
+    nl = w.mesh.n_cells[level]
+    cells = np.linspace(0, nl - 1, n_check).astype(int)
+    errs = []
+    t_exact = 0.0
+    for j in cells:
+        v = torch.zeros(nl, dtype=torch.float64, device=eps_d.device)
+        v[int(j)] = 1.0
+        ev[2].record(stream)
+        jv = mg.jacobian_apply(mesh, level, eps_d, w.shots, wav_d, dt, v)
+        ev[3].record(stream)
+        ex = mg.project(u, jv, dt)
+        torch.cuda.synchronize()
+        t_exact += ev[2].elapsed_time(ev[3]) / 1e3
+        a = Lp[:, :, int(j)]
+        errs.append(float(torch.linalg.norm(a - ex) / torch.linalg.norm(ex)))
+    t_col = t_exact / len(cells)
+    t_approx = ev[0].elapsed_time(ev[1]) / 1e3
+    return {"workload": f"{w.name} level {level}: {nl} cells x {w.shots.n_shots} shots, "
+                        f"{len(wav_d)} steps, {len(out['nodes'])} corner nodes",
+            "seconds": t_approx, "exact_column_seconds": t_col,
+            "speedup_vs_exact_columns": nl * t_col / t_approx,
+            "relative_error_sampled_cells": errs}
 
 
 def cpu_baseline(w, dt, budget_s=20.0):
@@ -475,6 +512,8 @@ def main():
                       "bytes_per_launch": nbytes}
     inversion = None if args.no_inversion_leg else inversion_leg(
         mg, torch, mesh, w, eps_d, wav_d, dt, y)
+    approx = None if args.no_inversion_leg else approx_jacobian_leg(
+        mg, torch, mesh, w, eps_d, wav_d, dt, y)
     proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
                     "the projected Jacobian products cost one jacobian_apply / "
                     "jacobian_T_apply each (the forward and adjoint phases above)")
@@ -514,6 +553,7 @@ def main():
         "clocks": clocks,
         "projected_data": proj,
         "tv_reconstruction": inversion,
+        "approx_jacobian": approx,
     }
     if not args.no_hbm_leg:
         out["hbm_workload"] = hbm_leg(mg, torch, dev)

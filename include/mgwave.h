@@ -257,17 +257,25 @@ int mg_mesh_set_kernel_tuning(mg_mesh* mesh, int kind, int batch, int tile_rows,
  * graphs.  Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_shot_groups(mg_mesh* mesh, int kind, int groups);
 
-/* Current tuning into out[13]: chunk, then (batch, tile_rows, src_tile,
- * groups) for the forward, tangent and adjoint kinds. */
+/* Register cap of the forward row kernel: 0 (none, default) or 5 (at least
+ * five resident 256-thread CTAs per SM; more warps in flight for
+ * HBM-bound meshes, a few spilled registers).  Drops the cached graphs.
+ * Errors: MG_ERR_ARG for other values. */
+int mg_mesh_set_min_blocks(mg_mesh* mesh, int min_blocks);
+
+/* Current tuning into out[16]: chunk, then (batch, tile_rows, src_tile,
+ * groups, min_blocks) for the forward, tangent and adjoint kinds. */
 int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
 
 /* Autotuner: times every candidate launch shape of each kernel kind on the
  * caller's problem (steps leapfrog steps of mg_forward, mg_jacobian_apply
  * and mg_jacobian_T_apply on `level`, device pointers; wavelet must hold at
  * least `steps` samples), keeps the fastest per kind on the handle and
- * returns it in chosen[13] (may be NULL).  Candidates: row kernels with 1,
+ * returns it in chosen[16] (may be NULL).  Candidates: row kernels with 1,
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
- * per pass; then 2, 4 and 8 shot groups on the two fastest of those.  Each
+ * per pass; for the forward also the 2- and 4-vector row kernels with the
+ * register cap of mg_mesh_set_min_blocks; then 2, 4 and 8 shot groups on
+ * the two fastest of those.  Each
  * candidate is timed as the best of three runs after the GPU has been
  * warmed up; shapes within 1% of the fastest count as equal (the earliest
  * listed wins) and shot groups must win by more than 1%.  The choice is cached on

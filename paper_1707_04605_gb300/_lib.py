@@ -86,6 +86,7 @@ SIGNATURES = {
     "mg_mesh_set_kernel_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_set_conductivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mg_mesh_set_min_blocks": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -143,14 +143,20 @@ class Mesh:
             rc = self._lib.mg_mesh_set_conductivity(self.handle, ps, None, L.MG_HOST_PTRS)
         L.check(rc, "mg_mesh_set_conductivity")
 
+    def set_min_blocks(self, min_blocks: int):
+        """Register cap of the forward row kernel (mg_mesh_set_min_blocks): 0 or 5."""
+        L.check(self._lib.mg_mesh_set_min_blocks(self.handle, int(min_blocks)),
+                "mg_mesh_set_min_blocks")
+
     def tuning(self) -> dict:
-        out = np.zeros(13, dtype=np.int32)
+        out = np.zeros(16, dtype=np.int32)
         L.check(self._lib.mg_mesh_get_tuning(self.handle, C.c_void_p(out.ctypes.data)),
                 "mg_mesh_get_tuning")
         d = {"chunk": int(out[0])}
         for name, k in self.KINDS.items():
-            d[name] = {"batch": int(out[1 + 4 * k]), "tile_rows": int(out[2 + 4 * k]),
-                       "src_tile": int(out[3 + 4 * k]), "groups": int(out[4 + 4 * k])}
+            d[name] = {"batch": int(out[1 + 5 * k]), "tile_rows": int(out[2 + 5 * k]),
+                       "src_tile": int(out[3 + 5 * k]), "groups": int(out[4 + 5 * k]),
+                       "min_blocks": int(out[5 + 5 * k])}
         return d
 
     def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,
@@ -160,7 +166,7 @@ class Mesh:
         sh = Shots.of(shots)
         eps, pe = _dev(eps, "float64")
         wavelet, pw = _dev(wavelet, "float64")
-        out = np.zeros(13, dtype=np.int32)
+        out = np.zeros(16, dtype=np.int32)
         L.check(self._lib.mg_autotune(self.handle, pe, C.byref(sh.c), pw, float(dt), int(steps),
                                       int(level), _stream_ptr(stream),
                                       L.MG_ALLOW_CFL if allow_cfl else 0,

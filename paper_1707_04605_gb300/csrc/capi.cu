@@ -113,6 +113,7 @@ struct mg_mesh {
     int tile_rows = 0;
     int src_tile = 32;
     int groups = 1;
+    int min_blocks = 0;   // forward row kernel: 0, or 5 resident CTAs per SM
   } tune[3];
   struct TileTables {
     Buf ell_off, ell_idx, ell_val, sinfo, halo_off, halo_cnt, halo;
@@ -388,6 +389,7 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   if (T.n_tiles) return mg::launch_step_tiled(a, T, st);
   mg::StepArgs b = a;
   b.batch = M->tune[0].batch;
+  b.min_blocks = M->tune[0].min_blocks;
   return mg::launch_step(b, S_pad, st);
 }
 
@@ -775,14 +777,22 @@ int mg_mesh_set_shot_groups(mg_mesh* M, int kind, int groups) {
   return MG_OK;
 }
 
+int mg_mesh_set_min_blocks(mg_mesh* M, int min_blocks) {
+  if (!M || (min_blocks != 0 && min_blocks != 5)) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->tune[0].min_blocks = min_blocks;
+  return MG_OK;
+}
+
 int mg_mesh_get_tuning(const mg_mesh* M, int32_t* out) {
   if (!M || !out) return MG_ERR_ARG;
   out[0] = M->chunk;
   for (int k = 0; k < 3; ++k) {
-    out[1 + 4 * k] = M->tune[k].batch;
-    out[2 + 4 * k] = M->tune[k].tile_rows;
-    out[3 + 4 * k] = M->tune[k].src_tile;
-    out[4 + 4 * k] = M->tune[k].groups;
+    out[1 + 5 * k] = M->tune[k].batch;
+    out[2 + 5 * k] = M->tune[k].tile_rows;
+    out[3 + 5 * k] = M->tune[k].src_tile;
+    out[4 + 5 * k] = M->tune[k].groups;
+    out[5 + 5 * k] = M->tune[k].min_blocks;
   }
   return MG_OK;
 }
@@ -1181,9 +1191,10 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
                                           stream, flags);
     }
   };
-  const mg_mesh::Tuning shapes[] = {{1, 0, 32},  {2, 0, 32},   {4, 0, 32},   {1, 64, 32},
-                                    {1, 64, 16}, {1, 128, 32}, {1, 128, 16}, {1, 256, 32},
-                                    {1, 256, 16}};
+  // the last two (a register cap for 5 CTAs per SM) apply to the forward only
+  const mg_mesh::Tuning shapes[] = {{1, 0, 32},   {2, 0, 32},   {4, 0, 32},   {1, 64, 32},
+                                    {1, 64, 16},  {1, 128, 32}, {1, 128, 16}, {1, 256, 32},
+                                    {1, 256, 16}, {2, 0, 32, 1, 5}, {4, 0, 32, 1, 5}};
   const int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
   cudaEvent_t e0, e1;
   MG_CU(cudaEventCreate(&e0));
@@ -1215,7 +1226,11 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
     // launch shapes with one shot group, then 2, 4 and 8 groups on the two
     // fastest shapes (groups that do not give a valid width are skipped)
     float ms[n_shapes];
-    for (int i = 0; i < n_shapes && rc == MG_OK; ++i) rc = time_of(kind, shapes[i], &ms[i]);
+    for (int i = 0; i < n_shapes && rc == MG_OK; ++i) {
+      ms[i] = 1e30f;
+      if (shapes[i].min_blocks && kind != 0) continue;
+      rc = time_of(kind, shapes[i], &ms[i]);
+    }
     if (rc != MG_OK) break;
     int order[n_shapes];
     for (int i = 0; i < n_shapes; ++i) order[i] = i;

@@ -40,6 +40,7 @@ struct StepArgs {
   int32_t step;             // l = step + (step_base ? *step_base : 0)
   const int32_t* step_base;
   int32_t batch;            // row kernels: float4 vectors (4 shots each) per lane, 1/2/4
+  int32_t min_blocks = 0;   // row kernel: 0, or 5 resident CTAs per SM requested (register cap)
   int32_t col0 = 0;         // first shot column advanced (multiple of the launch's shot tile)
   int32_t cols = 0;         // shot columns advanced, [col0, col0 + cols); 0 = all ld
 };

@@ -150,8 +150,11 @@ __device__ __forceinline__ float get_from(const float4 (&v)[NV], int j, int d) {
   return out;
 }
 
-template <int LPR, int NV>
-__global__ void __launch_bounds__(kThreads) k_step_rows(StepArgs a) {
+// MINB > 1 asks the compiler for at least MINB resident CTAs per SM (a
+// register cap): more warps in flight for the HBM-bound case, at the price
+// of a few spilled registers in the rare source/receiver epilogue.
+template <int LPR, int NV, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
@@ -344,6 +347,29 @@ bool range_ok(const Shape& sh, int col0, int cols, int ld) {
     default: return MG_ERR_ARG;                                                            \
   }
 
+#define MG_ROWS_SWITCH_M(KERN, M, ARGS)                                                         \
+  switch (sh.lpr * 8 + sh.nv) {                                                            \
+    case 32 * 8 + 1: KERN<32, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
+    case 32 * 8 + 2: KERN<32, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
+    case 32 * 8 + 4: KERN<32, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
+    case 16 * 8 + 1: KERN<16, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
+    case 16 * 8 + 2: KERN<16, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
+    case 16 * 8 + 4: KERN<16, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
+    case 8 * 8 + 1: KERN<8, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 8 * 8 + 2: KERN<8, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 8 * 8 + 4: KERN<8, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 4 * 8 + 1: KERN<4, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 4 * 8 + 2: KERN<4, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 4 * 8 + 4: KERN<4, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 2 * 8 + 1: KERN<2, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 2 * 8 + 2: KERN<2, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 2 * 8 + 4: KERN<2, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 1 * 8 + 1: KERN<1, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 1 * 8 + 2: KERN<1, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 1 * 8 + 4: KERN<1, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    default: return MG_ERR_ARG;                                                            \
+  }
+
 }  // namespace
 
 int rows_tiles(int cols, int nv) { return (int)shape_of(1, cols, nv).grid.y; }
@@ -352,7 +378,13 @@ int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
   const int cols = a.cols ? a.cols : S_pad;
   const Shape sh = shape_of(a.K.n, cols, a.batch);
   if (!range_ok(sh, a.col0, cols, a.ld)) return MG_ERR_ARG;
-  MG_ROWS_SWITCH(k_step_rows, a)
+  if (a.min_blocks == 5) {
+    MG_ROWS_SWITCH_M(k_step_rows, 5, a)
+  } else if (a.min_blocks == 0) {
+    MG_ROWS_SWITCH_M(k_step_rows, 1, a)
+  } else {
+    return MG_ERR_ARG;
+  }
   return check_launch();
 }
 
@@ -372,5 +404,6 @@ int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st) {
   return check_launch();
 }
 #undef MG_ROWS_SWITCH
+#undef MG_ROWS_SWITCH_M
 
 }  // namespace mg

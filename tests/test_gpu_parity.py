@@ -301,6 +301,29 @@ def test_wide_batch_row_shapes_cover_every_shot(mg):
     assert rel_l2(out.cpu().numpy()[rows], y) < TRACE_TOL
 
 
+@pytest.mark.parametrize("batch", [1, 2, 4])
+def test_register_capped_forward_gives_identical_results(mg, batch):
+    """mg_mesh_set_min_blocks(5) only changes register allocation: same bits."""
+    w = configs.asteroid_2d(n_refine=1, S=100, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(-1, batch, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    W = _dev(np.random.default_rng(4).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    mesh.set_min_blocks(5)
+    assert mesh.tuning()["forward"]["min_blocks"] == 5
+    out = run()
+    assert torch.equal(ref[0], out[0])
+    assert torch.equal(ref[1], out[1])
+
+
 def test_autotune_picks_valid_shapes_and_keeps_results(mg):
     w = configs.asteroid_2d(n_refine=2, S=64, nt=256)
     eps = _dev(w.eps)
