@@ -17,6 +17,8 @@ Modules:
           compression of Sec. II, dense on tiny problems.
   approx_jacobian - the paper's approximate Jacobian (auxiliary sources,
           Green's functions by reciprocity, coarse-mass multigrid variant).
+  mixed - the first-order leapfrog with element fluxes and the split-field
+          perfectly matched layer of App. A.
 
 Every function here is pinned by tests against facts that do not come from
 the oracle itself (tests/test_oracle_pins.py): exact discrete energy balance,
@@ -24,4 +26,4 @@ the closed-form leapfrog evolution of a Dirichlet eigenmode, the straight-ray
 travel time, complex-step and central finite differences, reciprocity, and
 the source's mass balance.
 """
-from . import approx_jacobian, fem, inversion, projected, wave  # noqa: F401
+from . import approx_jacobian, fem, inversion, mixed, projected, wave  # noqa: F401
