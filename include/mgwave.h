@@ -407,6 +407,30 @@ int mg_approx_jacobian(mg_mesh* mesh, int level, const double* eps, const mg_sho
                        float* phi, int32_t* nodes, int64_t* n_nodes, size_t mem_budget,
                        void* stream, int flags);
 
+/* Forward traces of the paper's first-order leapfrog with element flux
+ * variables and the split-field perfectly matched layer (App. A, Eqs.
+ * (system1)-(system2), (leap-frog1)-(leap-frog2)):
+ *   q^(k)_{l+1/2} = q^(k)_{l-1/2} + dt A^-1 (B^(k) p_l - T^(k) q^(k)_{l-1/2})
+ *   p_{l+1}       = p_l + dt C^-1 (f_l - R p_l - S p_l - sum_k B^(k)T q^(k)_{l+1/2})
+ * with A_ii = |T_i|, B^(k)_ij = |T_i| dphi_j/dx_k, C, R (the handle's
+ * conductivity, evaluated explicitly as printed) and S = xi-mass lumped,
+ * T^(k) = zeta^(k) A, f_l = dt sum_{m <= l} s_m.  The outer boundary is
+ * natural (the handle's boundary mode is not used); the layer absorbs.
+ * Sample l of a trace is p_{l+1} at the receiver.  With no layer and no
+ * conductivity the traces equal mg_forward's with the Neumann boundary.
+ *   xi    [n_cells] FP64 >= 0 per finest cell (caller order), or NULL.
+ *   zeta  [n_cells][dim] FP64 >= 0 per finest cell and direction, or NULL.
+ *   traces, shots, wavelet, dt, nt, flags (MG_HOST_PTRS, MG_ALLOW_CFL) as
+ *   mg_forward; dt is checked against the CFL bound of mg_cfl_dt (the
+ *   explicit damping terms need dt zeta and dt (sigma + xi)/eps below 1 in
+ *   addition, which the caller chooses).  Synchronous; one launch per flux
+ *   and per node update.
+ * Errors: MG_ERR_ARG (null, negative zeta, degenerate cell), MG_ERR_CFL,
+ * MG_ERR_UNSUPPORTED (other flags), MG_ERR_OOM, MG_ERR_CUDA. */
+int mg_forward_pml(mg_mesh* mesh, const double* eps, const mg_shots* shots, const double* wavelet,
+                   double dt, int nt, const double* xi, const double* zeta, float* traces,
+                   void* stream, int flags);
+
 /* Nested prolongation of level-cell values to the finest cells (Sec. II-B:
  * eps_r = sum_j c_j chi'_j): out[e] = base[e] + v[anc_level(e)] for every
  * finest cell e (base may be NULL for 0).  v: [cells of level], base, out:

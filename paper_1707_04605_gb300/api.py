@@ -437,6 +437,26 @@ def approx_jacobian(mesh: Mesh, level, eps, shots, wavelet, dt, u=None, *, want_
     return {"nodes": nodes[:N], "Lp": Lp, "phi": phi}
 
 
+def forward_pml(mesh: Mesh, eps, shots, wavelet, dt, xi=None, zeta=None, nt=None, *,
+                allow_cfl=False, stream=None):
+    """Traces [n_traces, nt] float32 of the first-order flux leapfrog with the
+    split-field layer xi [cells], zeta [cells, dim] (mg_forward_pml)."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    extra = [(x, "float64") for x in (xi, zeta) if x is not None]
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, extra, stream)
+    it = iter(ex)
+    pxi = next(it)[1] if xi is not None else None
+    pzeta = next(it)[1] if zeta is not None else None
+    out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_forward_pml(mesh.handle, pe, C.byref(sh.c), pw, float(dt), nt, pxi, pzeta,
+                            _ptr(out), st, f)
+    L.check(rc, "mg_forward_pml")
+    return out
+
+
 def _ptr_array(xs):
     return (C.c_void_p * len(xs))(*[C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr")
                                                else x.ctypes.data) for x in xs])
