@@ -263,15 +263,29 @@ int mg_mesh_set_shot_groups(mg_mesh* mesh, int kind, int groups);
  * Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_min_blocks(mg_mesh* mesh, int min_blocks);
 
-/* Current tuning into out[16]: chunk, then (batch, tile_rows, src_tile,
- * groups, min_blocks) for the forward, tangent and adjoint kinds. */
+/* Forward step with the neighbour rows of each warp staged in shared
+ * memory by bulk asynchronous copies (cp.async.bulk on an mbarrier) instead
+ * of per-lane loads: same arithmetic and bits, more bytes in flight per
+ * warp.  on: 0 (default) or 1.  Its waits are bounded; a wait that runs out
+ * is reported by mg_mesh_device_status.  Drops the cached graphs. */
+int mg_mesh_set_bulk_copies(mg_mesh* mesh, int on);
+
+/* Status of the handle's bounded device waits since the last call:
+ * MG_OK, MG_ERR_TIMEOUT (a wait ran out; the step it belongs to is
+ * incomplete), MG_ERR_ARG (a copy address failed its alignment check).
+ * Synchronises with the device and clears the status. */
+int mg_mesh_device_status(mg_mesh* mesh);
+
+/* Current tuning into out[17]: chunk, then (batch, tile_rows, src_tile,
+ * groups, min_blocks) for the forward, tangent and adjoint kinds, then the
+ * forward's bulk-copy switch. */
 int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
 
 /* Autotuner: times every candidate launch shape of each kernel kind on the
  * caller's problem (steps leapfrog steps of mg_forward, mg_jacobian_apply
  * and mg_jacobian_T_apply on `level`, device pointers; wavelet must hold at
  * least `steps` samples), keeps the fastest per kind on the handle and
- * returns it in chosen[16] (may be NULL).  Candidates: row kernels with 1,
+ * returns it in chosen[17] (may be NULL).  Candidates: row kernels with 1,
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
  * per pass; for the forward also the 2- and 4-vector row kernels with the
  * register cap of mg_mesh_set_min_blocks; then 2, 4 and 8 shot groups on

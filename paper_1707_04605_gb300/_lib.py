@@ -87,6 +87,8 @@ SIGNATURES = {
     "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_set_conductivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_mesh_set_min_blocks": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_bulk_copies": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_device_status": (C.c_int, [C.c_void_p]),
     "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -148,8 +148,17 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_min_blocks(self.handle, int(min_blocks)),
                 "mg_mesh_set_min_blocks")
 
+    def set_bulk_copies(self, on: bool):
+        """Forward step with bulk-copied neighbour rows (mg_mesh_set_bulk_copies)."""
+        L.check(self._lib.mg_mesh_set_bulk_copies(self.handle, int(bool(on))),
+                "mg_mesh_set_bulk_copies")
+
+    def device_status(self) -> int:
+        """mg_mesh_device_status: 0, or the MG_ERR_* code of a failed bounded wait."""
+        return int(self._lib.mg_mesh_device_status(self.handle))
+
     def tuning(self) -> dict:
-        out = np.zeros(16, dtype=np.int32)
+        out = np.zeros(17, dtype=np.int32)
         L.check(self._lib.mg_mesh_get_tuning(self.handle, C.c_void_p(out.ctypes.data)),
                 "mg_mesh_get_tuning")
         d = {"chunk": int(out[0])}
@@ -157,6 +166,7 @@ class Mesh:
             d[name] = {"batch": int(out[1 + 5 * k]), "tile_rows": int(out[2 + 5 * k]),
                        "src_tile": int(out[3 + 5 * k]), "groups": int(out[4 + 5 * k]),
                        "min_blocks": int(out[5 + 5 * k])}
+        d["forward"]["bulk"] = int(out[16])
         return d
 
     def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,
@@ -166,7 +176,7 @@ class Mesh:
         sh = Shots.of(shots)
         eps, pe = _dev(eps, "float64")
         wavelet, pw = _dev(wavelet, "float64")
-        out = np.zeros(16, dtype=np.int32)
+        out = np.zeros(17, dtype=np.int32)
         L.check(self._lib.mg_autotune(self.handle, pe, C.byref(sh.c), pw, float(dt), int(steps),
                                       int(level), _stream_ptr(stream),
                                       L.MG_ALLOW_CFL if allow_cfl else 0,

@@ -111,6 +111,10 @@ int launch_adjoint_tiled(const AdjointArgs& a, const DevTiles& T, cudaStream_t s
 int rows_tiles(int cols, int nv);
 
 int launch_step(const StepArgs& a, int S_pad, cudaStream_t st);
+// Forward step with neighbour rows staged by bulk asynchronous copies
+// (kernels_bulk.cu); err: device int set to 1 when a bounded wait ran out,
+// 2 when a copy address was misaligned.
+int launch_step_bulk(const StepArgs& a, int S_pad, int* err, cudaStream_t st);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);
 int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st);
 int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st);

@@ -324,6 +324,32 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     assert torch.equal(ref[1], out[1])
 
 
+@pytest.mark.parametrize("S,batch", [(100, 1), (100, 2), (6, 1), (300, 2), (64, 2)])
+def test_bulk_copied_forward_gives_identical_results(mg, S, batch):
+    """Neighbour rows staged by bulk asynchronous copies: same arithmetic in
+    the same order as the row kernel, so the same bits, with graphs and
+    checkpoints (the adjoint's recompute uses the forward kernel too)."""
+    w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(-1, batch, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    W = _dev(np.random.default_rng(4).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    mesh.set_bulk_copies(True)
+    assert mesh.tuning()["forward"]["bulk"] == 1
+    out = run()
+    assert mesh.device_status() == 0
+    assert torch.equal(ref[0], out[0])
+    assert torch.equal(ref[1], out[1])
+
+
 def test_autotune_picks_valid_shapes_and_keeps_results(mg):
     w = configs.asteroid_2d(n_refine=2, S=64, nt=256)
     eps = _dev(w.eps)
