@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-inversion-leg", action="store_true",
                     help="skip the TV-reconstruction and approximate-Jacobian timings")
+    ap.add_argument("--no-batch-leg", action="store_true",
+                    help="skip the uneven multi-instance batch timing")
+    ap.add_argument("--min-blocks", type=int, default=-1,
+                    help="register cap of the forward row kernel (0 or 5)")
     ap.add_argument("--lane-vec", type=int, default=-1,
                     help="row kernels: float4 vectors of shots per lane (1, 2, 4)")
     ap.add_argument("--hbm-only", action="store_true",
@@ -133,6 +137,40 @@ def clocks_stop(proc, gpu_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch of the forward step kernel, from one
+# ncu capture of the same workload and launch shape (summaries in profiles/),
+# with the SHA-1 of the kernel sources at capture time: a figure is reported
+# only while those sources are unchanged, else the roofline's traffic is null.
+KERNEL_SOURCES = ["kernels_rows.cu", "device_util.cuh", "kernels.cuh"]
+TRAFFIC = {
+    # (workload, batch, tile_rows, groups, min_blocks, bulk): (bytes, sha1)
+    # k_step_rows<16,2,1>, --cache-control none, mean of launches 2-5 (the
+    # states stay in L2; DRAM sees write-backs)
+    ("asteroid_2d", 2, 0, 1, 0, 0): (11.2e6, "cbdedf17368d2819d576b09129ba7b10fd3ce055"),
+    # k_step_rows<8,2,5>, one launch
+    ("ellipsoid_3d", 2, 0, 1, 5, 0): (1.668e9, "cbdedf17368d2819d576b09129ba7b10fd3ce055"),
+}
+
+
+def sources_sha1():
+    import hashlib
+
+    h = hashlib.sha1()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1707_04605_gb300",
+                        "csrc")
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(workload, fwd):
+    key = (workload, fwd["batch"], fwd["tile_rows"], fwd.get("groups", 1),
+           fwd.get("min_blocks", 0), fwd.get("bulk", 0))
+    hit = TRAFFIC.get(key)
+    return hit[0] if hit and hit[1] == sources_sha1() else None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -156,6 +194,8 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
     wav = torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
     if args is not None and (args.tile_rows != -1 or args.src_tile != -1 or args.lane_vec != -1):
         mesh.set_kernel_tuning("forward", args.lane_vec, args.tile_rows, args.src_tile)
+        if args.min_blocks != -1:
+            mesh.set_min_blocks(args.min_blocks)
     else:
         mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
     tuning = mesh.tuning()
@@ -186,7 +226,8 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
             "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind_note(kind),
-                         "algorithmic_bytes_per_launch": bytes_step, "traffic": None}}
+                         "algorithmic_bytes_per_launch": bytes_step,
+                         "traffic": traffic_for("ellipsoid_3d", tuning["forward"])}}
 
 
 def peak_kind_note(kind):
@@ -270,6 +311,52 @@ def approx_jacobian_leg(mg, torch, mesh, w, eps_d, wav_d, dt, y, level=1, n_chec
             "seconds": t_approx, "exact_column_seconds": t_col,
             "speedup_vs_exact_columns": nl * t_col / t_approx,
             "relative_error_sampled_cells": errs}
+
+
+def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
+    """The uneven batch: 24 asteroid instances (levels 1-4, 8-256 shots, own
+    eps, shots, f and dt) advanced by one launch per step for all of them
+    (forward, and J^T with its recompute and reverse steps), against the
+    same instances run one after another through the single-instance calls."""
+    ws = configs.uneven_batch_2d(nt=nt)
+    meshes = [mg.mesh_from_workload(w) for w in ws]
+    eps = [torch.as_tensor(w.eps, dtype=torch.float64, device=dev) for w in ws]
+    dts = [w.cfl_fraction * mg.cfl_dt(m, e) for m, e in zip(meshes, eps)]
+    wavs = [torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
+            for w, dt in zip(ws, dts)]
+    shots = [w.shots for w in ws]
+    levels = [1] * len(ws)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    t_fb, ys = timed(lambda: mg.forward_batch(meshes, eps, shots, wavs, dts))
+    t_fs, _ = timed(lambda: [mg.forward(m, e, sh, wv, dt)
+                             for m, e, sh, wv, dt in zip(meshes, eps, shots, wavs, dts)])
+    t_ab, _ = timed(lambda: mg.jacobian_T_apply_batch(meshes, levels, eps, shots, wavs, dts, ys,
+                                                      ckpt_every=ckpt))
+    t_as, _ = timed(lambda: [mg.jacobian_T_apply(m, 1, e, sh, wv, dt, y, ckpt_every=ckpt)
+                             for m, e, sh, wv, dt, y in zip(meshes, eps, shots, wavs, dts, ys)])
+    units = sum(w.n_nodes * w.shots.n_shots for w in ws) * nt
+    for m in meshes:
+        m.close()
+    return {"workload": f"uneven_batch_2d: {len(ws)} instances, "
+                        f"{min(w.n_nodes for w in ws)}-{max(w.n_nodes for w in ws)} nodes, "
+                        f"{min(w.shots.n_shots for w in ws)}-{max(w.shots.n_shots for w in ws)} "
+                        f"shots, {nt} steps, checkpoints every {ckpt}",
+            "forward_updates_per_s": {"batched": units / t_fb, "one_by_one": units / t_fs},
+            "adjoint_updates_per_s": {"batched": units / t_ab, "one_by_one": units / t_as},
+            "seconds": {"forward_batched": t_fb, "forward_one_by_one": t_fs,
+                        "adjoint_batched": t_ab, "adjoint_one_by_one": t_as},
+            "note": "adjoint seconds include the checkpointed forward and the recompute"}
 
 
 def cpu_baseline(w, dt, budget_s=20.0):
@@ -374,6 +461,8 @@ def main():
     w = workload_for_rank(rank, args.nt)
     mesh = mg.mesh_from_workload(w)
     mesh.set_tuning(args.chunk, args.lane_vec, args.tile_rows, args.src_tile)
+    if args.min_blocks != -1:
+        mesh.set_min_blocks(args.min_blocks)
     n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
     eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)
@@ -514,6 +603,7 @@ def main():
         mg, torch, mesh, w, eps_d, wav_d, dt, y)
     approx = None if args.no_inversion_leg else approx_jacobian_leg(
         mg, torch, mesh, w, eps_d, wav_d, dt, y)
+    batch = None if args.no_batch_leg or ws > 1 else batch_leg(mg, torch, dev)
     proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
                     "the projected Jacobian products cost one jacobian_apply / "
                     "jacobian_T_apply each (the forward and adjoint phases above)")
@@ -543,7 +633,8 @@ def main():
         "batched_vs_single_source": fwd_rate / single_rate,
         "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": traffic_for("asteroid_2d", tuning["forward"]),
                      "algorithmic_bytes_per_launch": bytes_fwd,
                      "note": "per-launch time = forward phase / nt (includes launch gaps); "
                              "state (2 x 32 MB) is L2-resident"},
@@ -554,6 +645,7 @@ def main():
         "projected_data": proj,
         "tv_reconstruction": inversion,
         "approx_jacobian": approx,
+        "uneven_batch": batch,
     }
     if not args.no_hbm_leg:
         out["hbm_workload"] = hbm_leg(mg, torch, dev)
