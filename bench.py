@@ -321,10 +321,10 @@ def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
     ws = configs.uneven_batch_2d(nt=nt)
     meshes = [mg.mesh_from_workload(w) for w in ws]
     eps = [torch.as_tensor(w.eps, dtype=torch.float64, device=dev) for w in ws]
-    dts = [w.cfl_fraction * mg.cfl_dt(m, e) for m, e in zip(meshes, eps)]
-    wavs = [torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
-            for w, dt in zip(ws, dts)]
-    shots = [w.shots for w in ws]
+    dts = [wi.cfl_fraction * mg.cfl_dt(m, e) for wi, m, e in zip(ws, meshes, eps)]
+    wavs = [torch.as_tensor(wi.wavelet(dt), dtype=torch.float64, device=dev)
+            for wi, dt in zip(ws, dts)]
+    shots = [wi.shots for wi in ws]
     levels = [1] * len(ws)
     stream = torch.cuda.current_stream(dev)
 
@@ -345,18 +345,28 @@ def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
                                                       ckpt_every=ckpt))
     t_as, _ = timed(lambda: [mg.jacobian_T_apply(m, 1, e, sh, wv, dt, y, ckpt_every=ckpt)
                              for m, e, sh, wv, dt, y in zip(meshes, eps, shots, wavs, dts, ys)])
-    units = sum(w.n_nodes * w.shots.n_shots for w in ws) * nt
+    units = sum(wi.n_nodes * wi.shots.n_shots for wi in ws) * nt
     for m in meshes:
         m.close()
-    return {"workload": f"uneven_batch_2d: {len(ws)} instances, "
-                        f"{min(w.n_nodes for w in ws)}-{max(w.n_nodes for w in ws)} nodes, "
-                        f"{min(w.shots.n_shots for w in ws)}-{max(w.shots.n_shots for w in ws)} "
-                        f"shots, {nt} steps, checkpoints every {ckpt}",
+    nodes = [wi.n_nodes for wi in ws]
+    nshots = [wi.shots.n_shots for wi in ws]
+    return {"workload": f"uneven_batch_2d: {len(ws)} instances, {min(nodes)}-{max(nodes)} "
+                        f"nodes, {min(nshots)}-{max(nshots)} shots, {nt} steps, "
+                        f"checkpoints every {ckpt}",
             "forward_updates_per_s": {"batched": units / t_fb, "one_by_one": units / t_fs},
             "adjoint_updates_per_s": {"batched": units / t_ab, "one_by_one": units / t_as},
             "seconds": {"forward_batched": t_fb, "forward_one_by_one": t_fs,
                         "adjoint_batched": t_ab, "adjoint_one_by_one": t_as},
             "note": "adjoint seconds include the checkpointed forward and the recompute"}
+
+
+def guarded(fn, *a, **k):
+    """Run one of the auxiliary legs; a failure is reported inside the JSON
+    line instead of ending the run."""
+    try:
+        return fn(*a, **k)
+    except Exception as e:                      # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def cpu_baseline(w, dt, budget_s=20.0):
@@ -599,11 +609,11 @@ def main():
         us = a0.elapsed_time(a1) * 1e3 / 20
         proj[name] = {"us": us, "GB_per_s": nbytes / (us * 1e-6) / 1e9,
                       "bytes_per_launch": nbytes}
-    inversion = None if args.no_inversion_leg else inversion_leg(
-        mg, torch, mesh, w, eps_d, wav_d, dt, y)
-    approx = None if args.no_inversion_leg else approx_jacobian_leg(
-        mg, torch, mesh, w, eps_d, wav_d, dt, y)
-    batch = None if args.no_batch_leg or ws > 1 else batch_leg(mg, torch, dev)
+    inversion = None if args.no_inversion_leg else guarded(
+        inversion_leg, mg, torch, mesh, w, eps_d, wav_d, dt, y)
+    approx = None if args.no_inversion_leg else guarded(
+        approx_jacobian_leg, mg, torch, mesh, w, eps_d, wav_d, dt, y)
+    batch = None if args.no_batch_leg or ws > 1 else guarded(batch_leg, mg, torch, dev)
     proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
                     "the projected Jacobian products cost one jacobian_apply / "
                     "jacobian_T_apply each (the forward and adjoint phases above)")
@@ -648,7 +658,7 @@ def main():
         "uneven_batch": batch,
     }
     if not args.no_hbm_leg:
-        out["hbm_workload"] = hbm_leg(mg, torch, dev)
+        out["hbm_workload"] = guarded(hbm_leg, mg, torch, dev)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, dt)
     print(json.dumps(out))
