@@ -216,10 +216,14 @@ int mg_jacobian_T_apply(mg_mesh* mesh, int level, const double* eps,
 
 /* Uneven batches: n_inst independent problems, each with its own handle
  * (distinct handles, one device), permittivity, shot batch, wavelet and dt,
- * all with the same step count nt, advanced by ONE kernel launch per
- * leapfrog step over a work list of (instance, row block, source tile)
- * items.  Instance i computes exactly what mg_forward /
- * mg_jacobian_T_apply would compute for it alone.
+ * all with the same step count nt.  The instances are cut, in the given
+ * order, into groups whose states fit half of L2 (two states per instance
+ * for the forward, three for J^T); a group of several instances is
+ * advanced by ONE kernel launch per leapfrog step over a work list of
+ * (instance, row block, source tile) items, an instance alone (one too
+ * large to share L2) by its own tuned single-instance path.  Instance i
+ * computes what mg_forward / mg_jacobian_T_apply would compute for it
+ * alone (to FP32 rounding: the kernels differ).
  *  meshes, eps, wavelets, traces, w, g: arrays of n_inst pointers (host
  *  arrays; the pointed-to data are device pointers, or host pointers with
  *  MG_HOST_PTRS); shots, dts, levels: host arrays of n_inst entries.

@@ -1,8 +1,11 @@
 // Uneven batches: several independent problems (own mesh handle, eps, shot
-// batch, wavelet and dt; common step count) advanced by one kernel launch
-// per leapfrog step.  A work list of (instance, row block, source tile)
-// items covers all instances, so small instances no longer leave the GPU
-// idle and a batch of 24 costs one launch per step instead of 24.
+// batch, wavelet and dt; common step count).  The instances are cut into
+// groups whose states fit half of L2; each group of several instances is
+// advanced by one kernel launch per leapfrog step over a work list of
+// (instance, row block, source tile) items, so small instances share the
+// GPU instead of leaving it idle, while every step still finds its states
+// in L2; an instance too large to share L2 runs the tuned single-instance
+// path.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -235,6 +238,38 @@ int check_batch(int n_inst, mg_mesh* const* meshes) {
   return MG_OK;
 }
 
+// L2-aware grouping.  Advancing every instance at every step touches the
+// states of all of them; when those exceed L2 every step streams from HBM,
+// while an instance run on its own may stay L2-resident.  So the batch is
+// cut, in the caller's order, into groups whose working set (`states`
+// padded states per instance) fits half of L2: a group of several
+// instances runs the batched kernels, an instance alone runs the tuned
+// single-instance path (its autotuned kernels and CUDA graphs).
+std::vector<std::vector<int>> l2_groups(int n_inst, mg_mesh* const* meshes, const mg_shots* shots,
+                                        int states) {
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0)
+    l2 = 64 << 20;
+  const size_t budget = (size_t)l2 / 2;
+  std::vector<std::vector<int>> groups;
+  size_t used = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    MeshView v;
+    mesh_view(meshes[i], &v);
+    const size_t ws = (size_t)states * v.n * padded_shots(shots[i].n_shots) * sizeof(float);
+    if (groups.empty() || used + ws > budget || ws > budget) {
+      groups.push_back({i});
+      used = ws;
+    } else {
+      groups.back().push_back(i);
+      used += ws;
+    }
+    if (ws > budget) used = budget + 1;   // an instance beyond the budget stays alone
+  }
+  return groups;
+}
+
 // Forward of every instance over [0, nt); checkpoints (p_l, p_{l-1}) of
 // instance i every ckpt_every steps when `views[i].ckpt` is set.
 int run_batch_forward(std::vector<InstanceView>& views, std::vector<Inst>& insts, int nt,
@@ -280,23 +315,41 @@ extern "C" int mg_forward_batch(int n_inst, mg_mesh* const* meshes, const double
   if (!eps || !shots || !wavelets || !dts || !traces || nt < 1) return MG_ERR_ARG;
   if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::vector<InstanceView> views(n_inst);
-  std::vector<Inst> insts(n_inst);
-  for (int i = 0; i < n_inst; ++i) {
-    if (!traces[i]) return MG_ERR_ARG;
-    B_TRY(prepare_instance(meshes[i], eps[i], &shots[i], wavelets[i], dts[i], nt, flags, stream, 0,
-                           nullptr, &views[i]));
-    insts[i] = make_inst(views[i], nt);
-    insts[i].traces = views[i].tr;
-  }
-  B_TRY(run_batch_forward(views, insts, nt, 0, st, views[0].launches));
   for (int i = 0; i < n_inst; ++i)
-    B_CU(cudaMemcpyAsync(traces[i], views[i].tr, (size_t)views[i].R * nt * sizeof(float),
-                         (flags & MG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                         st));
+    if (!traces[i]) return MG_ERR_ARG;
+  for (const auto& grp : l2_groups(n_inst, meshes, shots, 2)) {
+    if (grp.size() == 1) {
+      const int i = grp[0];
+      B_TRY(mg_forward(meshes[i], eps[i], &shots[i], wavelets[i], dts[i], nt, traces[i], 0, stream,
+                       flags));
+      continue;
+    }
+    const int n = (int)grp.size();
+    std::vector<InstanceView> views(n);
+    std::vector<Inst> insts(n);
+    for (int j = 0; j < n; ++j) {
+      const int i = grp[j];
+      B_TRY(prepare_instance(meshes[i], eps[i], &shots[i], wavelets[i], dts[i], nt, flags, stream,
+                             0, nullptr, &views[j]));
+      insts[j] = make_inst(views[j], nt);
+      insts[j].traces = views[j].tr;
+    }
+    B_TRY(run_batch_forward(views, insts, nt, 0, st, views[0].launches));
+    for (int j = 0; j < n; ++j)
+      B_CU(cudaMemcpyAsync(traces[grp[j]], views[j].tr, (size_t)views[j].R * nt * sizeof(float),
+                           (flags & MG_HOST_PTRS) ? cudaMemcpyDeviceToHost
+                                                  : cudaMemcpyDeviceToDevice,
+                           st));
+  }
   if (flags & MG_HOST_PTRS) B_CU(cudaStreamSynchronize(st));
   return MG_OK;
 }
+
+static int adjoint_group(int n_inst, mg_mesh* const* meshes, const int* levels,
+                         const double* const* eps, const mg_shots* shots,
+                         const double* const* wavelets, const double* dts, int nt,
+                         const float* const* w, double* const* g, int ckpt_every, void* stream,
+                         int flags);
 
 extern "C" int mg_jacobian_T_apply_batch(int n_inst, mg_mesh* const* meshes, const int* levels,
                                          const double* const* eps, const mg_shots* shots,
@@ -308,12 +361,43 @@ extern "C" int mg_jacobian_T_apply_batch(int n_inst, mg_mesh* const* meshes, con
     return MG_ERR_ARG;
   if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n_inst; ++i)
+    if (!w[i] || !g[i]) return MG_ERR_ARG;
+  for (const auto& grp : l2_groups(n_inst, meshes, shots, 3)) {
+    if (grp.size() == 1) {
+      const int i = grp[0];
+      B_TRY(mg_jacobian_T_apply(meshes[i], levels[i], eps[i], &shots[i], wavelets[i], dts[i], nt,
+                                w[i], g[i], ckpt_every, stream, flags));
+      continue;
+    }
+    std::vector<mg_mesh*> gm;
+    std::vector<const double*> ge, gwv;
+    std::vector<mg_shots> gs;
+    std::vector<double> gdt;
+    std::vector<int> gl;
+    std::vector<const float*> gw;
+    std::vector<double*> gg;
+    for (int i : grp) {
+      gm.push_back(meshes[i]); ge.push_back(eps[i]); gs.push_back(shots[i]);
+      gwv.push_back(wavelets[i]); gdt.push_back(dts[i]); gl.push_back(levels[i]);
+      gw.push_back(w[i]); gg.push_back(g[i]);
+    }
+    B_TRY(adjoint_group((int)grp.size(), gm.data(), gl.data(), ge.data(), gs.data(), gwv.data(),
+                        gdt.data(), nt, gw.data(), gg.data(), ckpt_every, stream, flags));
+  }
+  return MG_OK;
+}
+
+// J^T w of one group of instances with the batched kernels.
+static int adjoint_group(int n_inst, mg_mesh* const* meshes, const int* levels,
+                  const double* const* eps, const mg_shots* shots,
+                  const double* const* wavelets, const double* dts, int nt,
+                  const float* const* w, double* const* g, int ckpt_every, void* stream,
+                  int flags) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<InstanceView> views(n_inst);
   std::vector<Inst> insts(n_inst);
   for (int i = 0; i < n_inst; ++i) {
-    if (!w[i] || !g[i]) return MG_ERR_ARG;
-    MeshView mv;
-    B_TRY(mesh_view(meshes[i], &mv));
     B_TRY(prepare_instance(meshes[i], eps[i], &shots[i], wavelets[i], dts[i], nt, flags, stream,
                            ckpt_every, w[i], &views[i]));
     insts[i] = make_inst(views[i], nt);

@@ -1314,6 +1314,7 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
 
 namespace mg {
 
+int padded_shots(int S) { return round_pad(S); }
 const HostMesh* host_mesh(const mg_mesh* M) { return M ? &M->hm : nullptr; }
 int mesh_device(const mg_mesh* M) { return M->device; }
 void add_launches(mg_mesh* M, int64_t n) { M->launches += n; }

@@ -24,6 +24,9 @@ struct MeshView {
 
 int mesh_view(mg_mesh* mesh, MeshView* out);
 
+// Padded shot count (row stride of the states) of a batch of S shots.
+int padded_shots(int S);
+
 struct HostMesh;
 // Host image of a handle's mesh (read-only), its device, and a way to count
 // launches made on its behalf by entry points outside capi.cu.
