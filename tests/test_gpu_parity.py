@@ -376,6 +376,26 @@ def test_autotune_picks_valid_shapes_and_keeps_results(mg):
     assert rel_l2(out[2].cpu().numpy(), ref[2].cpu().numpy()) < 1e-5
 
 
+def test_twenty_jacobian_columns_square_disc_2d(mg):
+    """20 seeded level-1 cells of square_disc_2d (4225 nodes, 2000 steps):
+    every GPU column J e_j within the Jacobian tolerance of the oracle's."""
+    w = configs.square_disc_2d()
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = w.wavelet(dt)
+    level = 1
+    nl = w.mesh.n_cells[level]
+    cells = np.random.default_rng(20).choice(nl, size=20, replace=False)
+    worst = 0.0
+    for c in cells:
+        v = np.zeros(nl)
+        v[c] = 1.0
+        jv = mg.jacobian_apply(mesh, level, _dev(w.eps), w.shots, _dev(s), dt,
+                               _dev(v)).cpu().numpy()
+        worst = max(worst, rel_l2(jv, oracle_tangent(w, dt, s, w.shots, v, level)))
+    assert worst < JAC_TOL
+
+
 def test_jacobian_square_disc_2d(mg):
     """4225 nodes, 2000 steps: a level-1 column J e_j and J^T w vs oracle."""
     w = configs.square_disc_2d()

@@ -246,6 +246,26 @@ def test_tangent_matches_central_differences():
     assert np.linalg.norm(dy - fd) <= 1e-5 * np.linalg.norm(fd)
 
 
+def test_level_column_matches_central_differences_on_square_disc():
+    """square_disc_2d (4225 nodes, 2000 steps), two level-1 columns: the
+    oracle's J e_j within 1e-5 of its own central difference with h = 1e-3
+    (the finite-difference step of the level parameters)."""
+    w = configs.square_disc_2d()
+    m, sh = w.mesh, w.shots
+    pb = _problem(w)
+    dt = 0.5 * pb.cfl_dt()
+    s = w.wavelet(dt)
+    anc = m.ancestor(1)
+    h = 1e-3
+    for c in (17, 201):
+        de = wave.prolong(np.eye(m.n_cells[1])[c], anc)
+        jv = wave.tangent(pb, dt, s, sh.src, sh.rec_ptr, sh.rec, de)
+        yp = wave.forward(_problem(w, eps=w.eps + h * de), dt, s, sh.src, sh.rec_ptr, sh.rec)
+        ym = wave.forward(_problem(w, eps=w.eps - h * de), dt, s, sh.src, sh.rec_ptr, sh.rec)
+        fd = (yp - ym) / (2 * h)
+        assert np.linalg.norm(jv - fd) <= 1e-5 * np.linalg.norm(fd)
+
+
 @pytest.mark.parametrize("bc", ["abc", "neumann", "dirichlet"])
 def test_adjoint_matches_complex_step_per_cell(bc):
     """Every entry of the gradient of <w, y> against a complex-step derivative."""
