@@ -48,6 +48,17 @@ design notes):
   ceil(keep_frac n_c) coarse cells with the largest |x^(c)_{l+1} - x^(c)_0|
   (ties: lower index), keep_frac = 1/3 in the paper; x^(f) is zero outside
   the kept set, and G for the fine step is formed from the full x^(f)_l.
+* More than two nested levels l_0 < l_1 < ... < l_nf (tv_iteration_3): L is
+  the Jacobian on the cells of the last level; f_i is the fluctuation space
+  of level l_i inside the cells of level l_{i-1} (the basis above), with
+  L_fi = L P_i R_fi (P_i prolongs level l_i to the last level) and
+  D_fi = D_level_li R_fi.  The printed residual sums L_{f_i} x^(f_i) over
+  k = 1..i-1, which refers to the unknown itself; it is read as
+  sum_k L_{f_k} [x^(f_k)_{l+1} - x^(f_k)_0], the corrections of the coarser
+  fine levels found in the same outer step.  Compression at level i ranks
+  the cells of level l_{i-1} by |x| of the reconstruction assembled so far
+  (coarse plus the corrections of levels 1..i-1), which for i = 1 is
+  |x^(c)|.  With two levels this is steps (1)-(5).
 """
 from __future__ import annotations
 
@@ -182,4 +193,74 @@ def coarse_to_fine(L_f, D_level_f, D_c, Rc, Rf, basis, dy, alpha: float, n_outer
         xb = np.zeros(Rf.shape[1])
         xb[K] = xK
         out.append((xc.copy(), xb.copy(), Rc @ xc + Rf @ xb, K))
+    return out
+
+
+def hierarchy(coords, cells, cell_parent, n_cells, levels, beta: float):
+    """Per listed level l_i (increasing): D of the level, P_i [n_top][n_li]
+    (each last-level cell takes its level-l_i ancestor's value) and, for
+    i >= 1, the fine_basis of level l_i inside level l_{i-1} with its
+    R_fi [n_li][nb_i].  Entry 0 of the basis lists is None."""
+    coords = np.asarray(coords, dtype=np.float64)
+    cells = np.asarray(cells)
+    finest = len(n_cells) - 1
+    top = levels[-1]
+    Ds, Ps, bases, Rs = [], [], [None], [None]
+    for i, lev in enumerate(levels):
+        anc = parent_map(cell_parent, n_cells, lev, finest)
+        s = shared_measure(coords, cells, anc, n_cells[lev])
+        Ds.append(regularisation_matrix(s, beta))
+        up = parent_map(cell_parent, n_cells, lev, top)
+        P = np.zeros((n_cells[top], n_cells[lev]))
+        P[np.arange(n_cells[top]), up] = 1.0
+        Ps.append(P)
+        if i > 0:
+            parent = parent_map(cell_parent, n_cells, levels[i - 1], lev)
+            basis, _, Rf = fine_basis(s, parent, n_cells[levels[i - 1]])
+            bases.append(basis)
+            Rs.append(Rf)
+    return Ds, Ps, bases, Rs
+
+
+def coarse_to_fine_levels(L, Ds, Ps, bases, Rs, dy, alpha: float, n_outer: int,
+                          keep_frac: float = 1.0 / 3.0):
+    """Steps (1)-(5) with the recursion (tv_iteration_3) over the levels of
+    ``hierarchy``; L: data x last-level cells.  Per outer step the coarse
+    update (tv_iteration_0), then for i = 1..nf the compressed correction in
+    f_i against the data left by the coarse step and by the corrections of
+    f_1..f_{i-1} of the same step.  Returns per step
+    (x_c, [x_f1, ..], x_last_level, [K_1, ..])."""
+    nf = len(Ds) - 1
+    Lc = L @ Ps[0]
+    Lf = [None] + [L @ Ps[i] @ Rs[i] for i in range(1, nf + 1)]
+    Df = [None] + [Ds[i] @ Rs[i] for i in range(1, nf + 1)]
+    xc = np.zeros(Ps[0].shape[1])
+    xf = [None] + [np.zeros(Rs[i].shape[1]) for i in range(1, nf + 1)]
+    out = []
+    for l in range(n_outer):
+        gc = weights(Ds[0] @ xc, l == 0)
+        xc = np.linalg.solve(Lc.T @ Lc + alpha * Ds[0].T @ (gc[:, None] * Ds[0]), Lc.T @ dy)
+        new = [None] * (nf + 1)
+        kept = []
+        for i in range(1, nf + 1):
+            # reconstruction so far, on the last level, then on level l_{i-1}
+            x_top = Ps[0] @ xc
+            for k in range(1, i):
+                x_top = x_top + Ps[k] @ (Rs[k] @ new[k])
+            prev = (Ps[i - 1].T @ x_top) / Ps[i - 1].sum(axis=0)
+            K = kept_basis(prev, bases[i], keep_frac)
+            r = dy - Lc @ xc
+            for k in range(1, i):
+                r = r - Lf[k] @ new[k]
+            g = weights(Df[i] @ xf[i], l == 0)
+            LK, DK = Lf[i][:, K], Df[i][:, K]
+            xK = np.linalg.solve(LK.T @ LK + alpha * DK.T @ (g[:, None] * DK), LK.T @ r)
+            new[i] = np.zeros(Rs[i].shape[1])
+            new[i][K] = xK
+            kept.append(K)
+        xf = new
+        x = Ps[0] @ xc
+        for i in range(1, nf + 1):
+            x = x + Ps[i] @ (Rs[i] @ xf[i])
+        out.append((xc.copy(), [v.copy() for v in xf[1:]], x, kept))
     return out

@@ -17,7 +17,19 @@ Facts that do not come from the oracle:
   one is not improved by random perturbations;
 * data that a coarse vector explains exactly is recovered by the coarse step
   with a vanishing fine correction; the compression keeps the basis
-  functions of the top third of the coarse cells.
+  functions of the top third of the coarse cells;
+* with more than two levels and L = I on a uniformly refined mesh (every
+  cell of a level has the same number of last-level descendants, so the
+  coarse space and the fluctuation spaces are mutually orthogonal), the
+  recursion is the multiresolution split of the data: the coarse step gives
+  the level-0 means, the first correction the level-1 means minus the
+  level-0 means, the last the data minus the level-1 means, each only under
+  the cells the compression keeps;
+* with a general L and vanishing alpha every step is the least-squares fit
+  of the data left by the coarser steps: the data residual of the
+  reconstruction assembled up to level i is orthogonal to the kept columns
+  of L_fi (for i = 0, to the columns of L_c);
+* with two levels the recursion is the two-level procedure.
 """
 import math
 
@@ -157,3 +169,82 @@ def test_coarse_to_fine_recovers_coarse_explained_data(lin):
     top = set(np.argsort(-np.abs(xc), kind="stable")[:k])
     assert sorted(K) == [i for i, (_, _, c) in enumerate(basis) if c in top]
     assert len(K) == 3 * k
+
+
+def _means(v_top, P):
+    """Mean of last-level values over the descendants of each level cell."""
+    return (P.T @ v_top) / P.sum(axis=0)
+
+
+def _top(values, k):
+    """Indices of the k largest |values| (ties: lower index first)."""
+    return np.argsort(-np.abs(values), kind="stable")[:k]
+
+
+@pytest.mark.parametrize("make", [lambda: meshes.square_mesh(2, 2),
+                                  lambda: meshes.ellipsoid_mesh(2, (2, 2, 2))],
+                         ids=["square_2d", "ellipsoid_3d"])
+@pytest.mark.parametrize("keep", [1.0, 1.0 / 3.0])
+def test_levels_recursion_with_identity_data_is_the_multiresolution_split(make, keep):
+    m = make()
+    Ds, Ps, bases, Rs = inv.hierarchy(m.coords, m.cells, m.cell_parent, m.n_cells, [0, 1, 2],
+                                      0.5)
+    n = m.n_cells[2]
+    assert Ps[0].shape[1] + sum(R.shape[1] for R in Rs[1:]) == n
+    dy = np.random.default_rng(3).standard_normal(n)
+    xc, xfs, x, Ks = inv.coarse_to_fine_levels(np.eye(n), Ds, Ps, bases, Rs, dy, alpha=1e-12,
+                                               n_outer=1, keep_frac=keep)[0]
+    m0, m1 = _means(dy, Ps[0]), _means(dy, Ps[1])
+    assert np.allclose(xc, m0, rtol=0, atol=1e-9)
+    k1 = _top(m0, math.ceil(keep * m.n_cells[0] - 1e-12))
+    on1 = np.isin(inv.parent_map(m.cell_parent, m.n_cells, 0, 2), k1)
+    x1 = Ps[0] @ m0 + on1 * (Ps[1] @ m1 - Ps[0] @ m0)
+    k2 = _top(_means(x1, Ps[1]), math.ceil(keep * m.n_cells[1] - 1e-12))
+    on2 = np.isin(inv.parent_map(m.cell_parent, m.n_cells, 1, 2), k2)
+    expect = x1 + on2 * (dy - Ps[1] @ m1)
+    assert np.linalg.norm(x - expect) <= 1e-8 * np.linalg.norm(dy)
+    if keep == 1.0:
+        assert np.linalg.norm(x - dy) <= 1e-8 * np.linalg.norm(dy)
+    else:
+        assert 0 < len(Ks[1]) < Rs[2].shape[1]
+
+
+def test_levels_recursion_with_two_levels_is_coarse_to_fine(lin):
+    w, L1, s1 = lin
+    m = w.mesh
+    _, s0 = _level_data(m, 0)
+    parent = inv.parent_map(m.cell_parent, m.n_cells, 0, 1)
+    basis, Rc, Rf = inv.fine_basis(s1, parent, m.n_cells[0])
+    rng = np.random.default_rng(4)
+    dy = L1 @ rng.standard_normal(m.n_cells[1])
+    alpha = 1e-3 * np.linalg.norm(L1 @ Rc, 2) ** 2
+    a = inv.coarse_to_fine(L1, inv.regularisation_matrix(s1, 0.2),
+                           inv.regularisation_matrix(s0, 0.2), Rc, Rf, basis, dy, alpha, 3)
+    Ds, Ps, bases, Rs = inv.hierarchy(m.coords, m.cells, m.cell_parent, m.n_cells, [0, 1], 0.2)
+    b = inv.coarse_to_fine_levels(L1, Ds, Ps, bases, Rs, dy, alpha, 3)
+    for (xc, xb, x, K), (yc, yfs, y, Ks) in zip(a, b):
+        assert K == Ks[0]
+        assert np.linalg.norm(xc - yc) <= 1e-10 * np.linalg.norm(xc)
+        assert np.linalg.norm(xb - yfs[0]) <= 1e-10 * np.linalg.norm(xb)
+        assert np.linalg.norm(x - y) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_levels_recursion_fits_what_the_coarser_levels_left():
+    m = meshes.square_mesh(2, 2)
+    Ds, Ps, bases, Rs = inv.hierarchy(m.coords, m.cells, m.cell_parent, m.n_cells, [0, 1, 2],
+                                      0.5)
+    rng = np.random.default_rng(6)
+    L = rng.standard_normal((300, m.n_cells[2]))
+    dy = rng.standard_normal(300)
+    xc, xfs, x, Ks = inv.coarse_to_fine_levels(L, Ds, Ps, bases, Rs, dy,
+                                               alpha=1e-12 * np.linalg.norm(L, 2) ** 2,
+                                               n_outer=1)[0]
+    scale = np.linalg.norm(L, 2) * np.linalg.norm(dy)
+    x_top = Ps[0] @ xc
+    assert np.linalg.norm((L @ Ps[0]).T @ (dy - L @ x_top)) <= 1e-8 * scale
+    for i in (1, 2):
+        x_top = x_top + Ps[i] @ (Rs[i] @ xfs[i - 1])
+        cols = (L @ Ps[i] @ Rs[i])[:, Ks[i - 1]]
+        assert len(Ks[i - 1]) > 0
+        assert np.linalg.norm(cols.T @ (dy - L @ x_top)) <= 1e-8 * scale
+    assert np.allclose(x_top, x, rtol=0, atol=1e-12 * np.abs(x).max())
