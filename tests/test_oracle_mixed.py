@@ -77,3 +77,74 @@ def test_layer_absorbs_boundary_echo():
         echo = np.abs(y[(t > t0 + 1.3) & (t < t0 + 2.6)]).max()
         ratio[vs] = echo / direct
     assert ratio[5.0] < 0.2 * ratio[0.0]
+
+
+# ------------------------------------------------------------------ Jacobians
+def _layer_case(dim):
+    if dim == 2:
+        m = meshes.square_mesh(3, 1)
+        c = m.coords[m.cells].mean(1)
+        xi, zeta = mixed.square_layer(m.coords, m.cells, 0.6, 1.0, 4.0)
+    else:
+        m = meshes.ellipsoid_mesh(1, (2, 2, 2))
+        c = m.coords[m.cells].mean(1)
+        zeta = np.where(np.abs(c) > 0.4, 3.0, 0.0)
+        xi = np.where(np.abs(c).max(1) > 0.4, 3.0, 0.0)
+    rng = np.random.default_rng(dim)
+    eps = rng.uniform(1.0, 3.0, len(m.cells))
+    sigma = 0.3 * rng.uniform(0.0, 1.0, len(m.cells))
+    pb = wave.Problem(m.coords, m.cells, m.bnd, eps, "neumann")
+    dt = 0.5 * pb.cfl_dt()
+    f = shots_mod.ricker_frequency(m.mean_edge_length(), 8.0, 1.0)
+    s = shots_mod.ricker(f, dt, 60)
+    n = len(m.coords)
+    src = rng.choice(n, 2, replace=False)
+    rec = rng.choice(n, 5, replace=False)
+    return m, eps, sigma, xi, zeta, dt, s, src, np.array([0, 3, 5]), rec
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pml_tangent_matches_complex_step(dim):
+    m, eps, sigma, xi, zeta, dt, s, src, rp, rec = _layer_case(dim)
+    de = np.random.default_rng(10 + dim).standard_normal(len(eps))
+    h = 1e-30
+    yc = mixed.forward(m.coords, m.cells, eps + 1j * h * de, dt, s, src, rp, rec, sigma=sigma,
+                       xi=xi, zeta=zeta)
+    cs = yc.imag / h
+    jv = mixed.tangent(m.coords, m.cells, eps, dt, s, src, rp, rec, de, sigma=sigma, xi=xi,
+                       zeta=zeta)
+    assert np.abs(cs).max() > 0
+    assert np.linalg.norm(jv - cs) <= 1e-12 * np.linalg.norm(cs)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pml_adjoint_dot_test(dim):
+    m, eps, sigma, xi, zeta, dt, s, src, rp, rec = _layer_case(dim)
+    rng = np.random.default_rng(20 + dim)
+    de = rng.standard_normal(len(eps))
+    W = rng.standard_normal((len(rec), len(s)))
+    jv = mixed.tangent(m.coords, m.cells, eps, dt, s, src, rp, rec, de, sigma=sigma, xi=xi,
+                       zeta=zeta)
+    g = mixed.adjoint_eps(m.coords, m.cells, eps, dt, s, src, rp, rec, W, sigma=sigma, xi=xi,
+                          zeta=zeta)
+    lhs, rhs = np.sum(jv * W), np.sum(de * g)
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), np.linalg.norm(jv) * np.linalg.norm(W))
+
+
+def test_pml_jacobians_without_layer_equal_second_order_jacobians():
+    """T = S = R = 0: the flux scheme is the second-order scheme with the
+    Neumann boundary, so its derivatives are too."""
+    w = configs.tiny_2d(n_coarse=2, n_refine=2, nt=120)
+    m, sh = w.mesh, w.shots
+    pb = wave.Problem(m.coords, m.cells, m.bnd, w.eps, "neumann")
+    dt = 0.5 * pb.cfl_dt()
+    s = w.wavelet(dt)
+    rng = np.random.default_rng(30)
+    de = rng.standard_normal(len(w.eps))
+    W = rng.standard_normal((sh.n_traces, len(s)))
+    t2 = wave.tangent(pb, dt, s, sh.src, sh.rec_ptr, sh.rec, de)
+    t1 = mixed.tangent(m.coords, m.cells, w.eps, dt, s, sh.src, sh.rec_ptr, sh.rec, de)
+    assert np.linalg.norm(t1 - t2) <= 1e-10 * np.linalg.norm(t2)
+    g2 = wave.adjoint_eps(pb, dt, s, sh.src, sh.rec_ptr, sh.rec, W)
+    g1 = mixed.adjoint_eps(m.coords, m.cells, w.eps, dt, s, sh.src, sh.rec_ptr, sh.rec, W)
+    assert np.linalg.norm(g1 - g2) <= 1e-10 * np.linalg.norm(g2)
