@@ -389,6 +389,29 @@ int mg_tv_reconstruct(mg_mesh* mesh, int level_c, int level_f, const double* eps
                       const mg_tv_params* params, double* x_out, double* history,
                       void* stream, int flags);
 
+/* The coarse-to-fine reconstruction over more than two nested levels
+ * (Sec. II, coarse-to-fine approach, the recursion (tv_iteration_3)).
+ *  levels    host array of n_levels >= 1 strictly increasing mesh levels
+ *            l_0 < l_1 < ... ; l_0 carries the coarse update, each further
+ *            level l_i a correction in the fluctuations of l_i inside the
+ *            cells of l_{i-1} (same basis, regulariser and compression as
+ *            mg_tv_reconstruct's fine step).  The correction of l_i fits the
+ *            data left by the coarse update and by the corrections of
+ *            l_1..l_{i-1} of the same outer step (the printed sum of the
+ *            recursion, its index read as running over the coarser levels);
+ *            compression ranks the cells of l_{i-1} by |x| of the
+ *            reconstruction assembled so far.  With {level_c} or
+ *            {level_c, level_f} this is mg_tv_reconstruct.
+ *  x_out     [cells of the last listed level] FP64.
+ *  history   optional host array [n_outer][2 n_levels]: CG iterations and
+ *            final relative residual of each level's solve, coarse first.
+ * Other arguments, flags and errors as mg_tv_reconstruct. */
+int mg_tv_reconstruct_levels(mg_mesh* mesh, const int* levels, int n_levels,
+                             const double* eps0, const mg_shots* shots, const double* wavelet,
+                             double dt, int nt, int data_mode, const void* dy, const float* u,
+                             const mg_tv_params* params, double* x_out, double* history,
+                             void* stream, int flags);
+
 /* The paper's approximate Jacobian (App. A.1-A.3: auxiliary system,
  * Green's functions by reciprocity, multigrid approach, Eq. (approx_2)).
  *

@@ -414,6 +414,42 @@ def tv_reconstruct(mesh: Mesh, level_c, eps0, shots, wavelet, dt, dy, *, level_f
     return x, hist
 
 
+def tv_reconstruct_levels(mesh: Mesh, levels, eps0, shots, wavelet, dt, dy, *, u=None, alpha,
+                          beta=0.0, n_outer=3, n_cg=50, cg_rtol=1e-8, keep_frac=1.0 / 3.0,
+                          ckpt_every=256, nt=None, allow_cfl=False, stream=None):
+    """Coarse-to-fine reconstruction over the nested ``levels`` (increasing;
+    mg_tv_reconstruct_levels): the perturbation x on the cells of the last
+    level and the history [n_outer, 2 len(levels)] (CG iterations and
+    relative residual of each level's solve, coarse first).  dy, u as in
+    tv_reconstruct."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32).ravel())
+    projected = u is not None
+    extra = [(dy, "float64" if projected else "float32")]
+    if projected:
+        extra.append((u, "float32"))
+    dev, (eps0, pe), (wav, pw), ex, st, f0 = _prep(eps0, wavelet, extra, stream)
+    pdy = ex[0][1]
+    pu = ex[1][1] if projected else None
+    last = int(lv[-1]) if len(lv) else 0
+    if not 0 <= last < len(mesh.n_cells_per_level):
+        raise ValueError(f"level {last} out of range")
+    x = _alloc(dev, (mesh.n_cells_per_level[last],), "float64", eps0)
+    hist = np.zeros((int(n_outer), 2 * len(lv)), dtype=np.float64)
+    prm = L.mg_tv_params(float(alpha), float(beta), int(n_outer), int(n_cg), float(cg_rtol),
+                         float(keep_frac), int(ckpt_every))
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_tv_reconstruct_levels(mesh.handle, C.c_void_p(lv.ctypes.data), len(lv), pe,
+                                      C.byref(sh.c), pw, float(dt), nt,
+                                      L.MG_DATA_PROJECTED if projected else L.MG_DATA_TRACES,
+                                      pdy, pu, C.byref(prm), _ptr(x),
+                                      C.c_void_p(hist.ctypes.data), st, f)
+    L.check(rc, "mg_tv_reconstruct_levels")
+    return x, hist
+
+
 def approx_jacobian(mesh: Mesh, level, eps, shots, wavelet, dt, u=None, *, want_phi=False,
                     mem_budget=0, nt=None, allow_cfl=False, stream=None):
     """The paper's approximate Jacobian (mg_approx_jacobian).  Returns a dict:

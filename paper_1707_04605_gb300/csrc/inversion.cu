@@ -23,6 +23,15 @@
 // D_f = D_level_f R_f.  Compression keeps the basis functions of the
 // ceil(keep_frac n_c) coarse cells with the largest |x_c| (ties: lower
 // index); the fine system is solved on that subspace (a 0/1 mask).
+//
+// More nested levels l_0 < l_1 < ... < l_nf (tv_iteration_3): after the
+// coarse update, each f_i (the fluctuations of level l_i inside the cells
+// of l_{i-1}) gets a compressed correction against the data that the
+// coarse update and the corrections of f_1..f_{i-1} of the same outer step
+// leave.  Those are assembled on the cells of l_{i-1} (comp: each cell
+// takes its parent's value plus its own fluctuation), so the residual is
+// dy - J_{l_{i-1}} comp, one Jacobian product; compression ranks the cells
+// of l_{i-1} by |comp|.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -371,7 +380,6 @@ struct Arena {  // stream-ordered device scratch, released with the solver
 
 struct Solver {
   mg_mesh* M;
-  int level_c, level_f;
   const double* eps;
   const mg_shots* shots;
   const double* wav;
@@ -479,13 +487,15 @@ struct Solver {
 }  // namespace
 }  // namespace mg
 
-extern "C" int mg_tv_reconstruct(mg_mesh* M, int level_c, int level_f, const double* eps0,
-                                 const mg_shots* shots, const double* wavelet, double dt, int nt,
-                                 int data_mode, const void* dy, const float* u,
-                                 const mg_tv_params* params, double* x_out, double* history,
-                                 void* stream, int flags) {
+extern "C" int mg_tv_reconstruct_levels(mg_mesh* M, const int* levels, int n_levels,
+                                        const double* eps0, const mg_shots* shots,
+                                        const double* wavelet, double dt, int nt, int data_mode,
+                                        const void* dy, const float* u,
+                                        const mg_tv_params* params, double* x_out,
+                                        double* history, void* stream, int flags) {
   using namespace mg;
-  if (!M || !eps0 || !shots || !wavelet || !dy || !params || !x_out || nt < 1 || !(dt > 0.0))
+  if (!M || !levels || n_levels < 1 || !eps0 || !shots || !wavelet || !dy || !params ||
+      !x_out || nt < 1 || !(dt > 0.0))
     return MG_ERR_ARG;
   if (data_mode != MG_DATA_TRACES && data_mode != MG_DATA_PROJECTED) return MG_ERR_ARG;
   if (data_mode == MG_DATA_PROJECTED && !u) return MG_ERR_ARG;
@@ -496,10 +506,11 @@ extern "C" int mg_tv_reconstruct(mg_mesh* M, int level_c, int level_f, const dou
     return MG_ERR_ARG;
   const HostMesh* hm = host_mesh(M);
   if (!hm) return MG_ERR_ARG;
-  const bool two = level_f >= 0;
-  if (level_c < 0 || level_c >= hm->n_levels || (two && (level_f <= level_c ||
-                                                          level_f >= hm->n_levels)))
-    return MG_ERR_ARG;
+  for (int i = 0; i < n_levels; ++i)
+    if (levels[i] < 0 || levels[i] >= hm->n_levels || (i > 0 && levels[i] <= levels[i - 1]))
+      return MG_ERR_ARG;
+  const int level_c = levels[0];
+  const int nf = n_levels - 1;  // fine levels f_1 .. f_nf
   int dev_prev = 0;
   if (cudaGetDevice(&dev_prev) != cudaSuccess) return MG_ERR_CUDA;
   if (cudaSetDevice(mesh_device(M)) != cudaSuccess) return MG_ERR_CUDA;
@@ -512,32 +523,45 @@ extern "C" int mg_tv_reconstruct(mg_mesh* M, int level_c, int level_f, const dou
   const int64_t R = shots->n_shots >= 0 && shots->rec_ptr ? shots->rec_ptr[shots->n_shots] : -1;
   if (R < 0) return MG_ERR_ARG;
 
-  // host-side structure: level graphs, D matrices, basis
+  // host-side structure: level graphs, D matrices, one basis per fine level
   Facets F;
   MG_RC(interior_facets(*hm, F));
   const Csr gc = level_graph(*hm, F, level_c);
   const Csr Dc = reg_matrix(gc, Pm.beta);
   const int64_t n_c = hm->n_cells_level[level_c];
-  Csr Dl;
-  Basis B;
-  std::vector<int32_t> parent;
-  int64_t n_f = 0, n_b = 0;
-  if (two) {
-    const Csr gf = level_graph(*hm, F, level_f);
-    Dl = reg_matrix(gf, Pm.beta);
-    n_f = hm->n_cells_level[level_f];
-    parent.assign(n_f, -1);
+  struct Fine {
+    int level = 0;
+    int64_t n = 0, n_b = 0;
+    Csr D;
+    Basis B;
+    std::vector<int32_t> parent;  // cell of this level -> cell of the previous listed level
+    DevCsr dD;
+    double *x = nullptr, *g = nullptr, *mask = nullptr, *cells = nullptr, *comp = nullptr;
+    int32_t *plus = nullptr, *minus = nullptr, *cfun = nullptr, *parent_d = nullptr;
+    int64_t* cptr = nullptr;
+    double* csign = nullptr;
+  };
+  std::vector<Fine> FL(nf);
+  int64_t nmax = n_c, nb_max = 0;
+  for (int i = 0; i < nf; ++i) {
+    Fine& f = FL[i];
+    f.level = levels[i + 1];
+    const int prev = levels[i];
+    const Csr gf = level_graph(*hm, F, f.level);
+    f.D = reg_matrix(gf, Pm.beta);
+    f.n = hm->n_cells_level[f.level];
+    f.parent.assign(f.n, -1);
     for (int64_t e = 0; e < hm->m; ++e)
-      parent[hm->ancestors[level_f][e]] = hm->ancestors[level_c][e];
-    MG_RC(fine_basis(gf, parent, n_c, B));
-    n_b = (int64_t)B.plus.size();
+      f.parent[hm->ancestors[f.level][e]] = hm->ancestors[prev][e];
+    MG_RC(fine_basis(gf, f.parent, hm->n_cells_level[prev], f.B));
+    f.n_b = (int64_t)f.B.plus.size();
+    nmax = std::max(nmax, std::max(f.n, f.n_b));
+    nb_max = std::max(nb_max, f.n_b);
   }
 
   Arena A(st);
   Solver S;
   S.M = M;
-  S.level_c = level_c;
-  S.level_f = level_f;
   S.shots = shots;
   S.dt = dt;
   S.nt = nt;
@@ -580,44 +604,39 @@ extern "C" int mg_tv_reconstruct(mg_mesh* M, int level_c, int level_f, const dou
   MG_RC(A.get(&S.pd, 2 * (size_t)R));
   MG_RC(A.get(&S.pd2, 2 * (size_t)R));
   MG_RC(A.get(&S.red, 4));
-  DevCsr dDc, dDl;
+  DevCsr dDc;
   MG_RC(A.put_csr(dDc, Dc));
-  // coarse vectors
-  double *xc, *bc, *r, *p, *q, *t, *g, *gcw, *v1, *v2;
-  const int64_t nmax = std::max<int64_t>(std::max(n_c, n_f), n_b);
+  // coarse vectors and shared CG scratch
+  double *xc, *bc, *r, *p, *q, *t, *gcw, *v1, *v2, *bb = nullptr, *all = nullptr;
   MG_RC(A.get(&xc, n_c));
   MG_RC(A.get(&bc, n_c));
   MG_RC(A.get(&r, nmax));
   MG_RC(A.get(&p, nmax));
   MG_RC(A.get(&q, nmax));
   MG_RC(A.get(&t, nmax));
-  MG_RC(A.get(&g, nmax));
   MG_RC(A.get(&gcw, n_c));
   MG_RC(A.get(&v1, nmax));
   MG_RC(A.get(&v2, nmax));
-  // fine structures
-  double *xb = nullptr, *bb = nullptr, *gfw = nullptr, *mask = nullptr, *cells = nullptr,
-         *all = nullptr;  // all: a mask of ones
-  int32_t *d_plus = nullptr, *d_minus = nullptr, *d_cfun = nullptr, *d_parent = nullptr;
-  int64_t* d_cptr = nullptr;
-  double* d_csign = nullptr;
-  if (two) {
-    MG_RC(A.put_csr(dDl, Dl));
-    MG_RC(A.get(&xb, n_b));
-    MG_RC(A.get(&bb, n_b));
-    MG_RC(A.get(&gfw, n_f));
-    MG_RC(A.get(&mask, n_b));
-    MG_RC(A.get(&cells, n_f));
-    MG_RC(A.put(&d_plus, B.plus));
-    MG_RC(A.put(&d_minus, B.minus));
-    MG_RC(A.put(&d_cptr, B.cptr));
-    MG_RC(A.put(&d_cfun, B.cfun));
-    MG_RC(A.put(&d_csign, B.csign));
-    MG_RC(A.put(&d_parent, parent));
-    MG_RC(A.put(&all, std::vector<double>(n_b, 1.0)));
+  if (nf > 0) {
+    MG_RC(A.get(&bb, nb_max));
+    MG_RC(A.put(&all, std::vector<double>(nb_max, 1.0)));  // a mask of ones
+  }
+  for (Fine& f : FL) {
+    MG_RC(A.put_csr(f.dD, f.D));
+    MG_RC(A.get(&f.x, f.n_b));
+    MG_RC(A.get(&f.g, f.n));
+    MG_RC(A.get(&f.mask, f.n_b));
+    MG_RC(A.get(&f.cells, f.n));
+    MG_RC(A.get(&f.comp, f.n));
+    MG_RC(A.put(&f.plus, f.B.plus));
+    MG_RC(A.put(&f.minus, f.B.minus));
+    MG_RC(A.put(&f.cptr, f.B.cptr));
+    MG_RC(A.put(&f.cfun, f.B.cfun));
+    MG_RC(A.put(&f.csign, f.B.csign));
+    MG_RC(A.put(&f.parent_d, f.parent));
+    MG_CK(cudaMemsetAsync(f.x, 0, f.n_b * sizeof(double), st));
   }
   MG_CK(cudaMemsetAsync(xc, 0, n_c * sizeof(double), st));
-  if (two) MG_CK(cudaMemsetAsync(xb, 0, n_b * sizeof(double), st));
 
   // one forward with checkpoints; every J^T reuses them
   MG_RC(mg_forward(M, S.eps, shots, S.wav, dt, nt, S.tr, Pm.ckpt_every, st,
@@ -636,94 +655,132 @@ extern "C" int mg_tv_reconstruct(mg_mesh* M, int level_c, int level_f, const dou
     MG_RC(S.csr(dDc, v1, v2));
     return S.lincomb(n_c, 1.0, out, alpha, v2, out);
   };
-  // A_f p = mask R_f^T (L^T L + alpha D_l G_f D_l) R_f mask p   (level-f cells)
+  // A_fi p = mask R_fi^T (L^T L + alpha D_li G_fi D_li) R_fi mask p   (level l_i cells)
+  const Fine* cur = nullptr;
   auto op_f = [&](const double* pin, double* out) -> int {
-    k_rf<<<grid_of(n_f), 256, 0, st>>>(n_f, d_cptr, d_cfun, d_csign, mask, pin, cells);
+    const Fine& f = *cur;
+    k_rf<<<grid_of(f.n), 256, 0, st>>>(f.n, f.cptr, f.cfun, f.csign, f.mask, pin, f.cells);
     MG_CK(cudaGetLastError());
-    MG_RC(S.apply_L(level_f, cells, S.data_buf()));
-    MG_RC(S.apply_LT(level_f, S.data_buf(), v1));
-    MG_RC(S.csr(dDl, cells, v2));
-    k_mul<<<grid_of(n_f), 256, 0, st>>>(n_f, gfw, v2);
+    MG_RC(S.apply_L(f.level, f.cells, S.data_buf()));
+    MG_RC(S.apply_LT(f.level, S.data_buf(), v1));
+    MG_RC(S.csr(f.dD, f.cells, v2));
+    k_mul<<<grid_of(f.n), 256, 0, st>>>(f.n, f.g, v2);
     MG_CK(cudaGetLastError());
-    MG_RC(S.csr(dDl, v2, t));
-    MG_RC(S.lincomb(n_f, 1.0, v1, alpha, t, v1));
-    k_rft<<<grid_of(n_b), 256, 0, st>>>(n_b, d_plus, d_minus, mask, v1, out);
+    MG_RC(S.csr(f.dD, v2, t));
+    MG_RC(S.lincomb(f.n, 1.0, v1, alpha, t, v1));
+    k_rft<<<grid_of(f.n_b), 256, 0, st>>>(f.n_b, f.plus, f.minus, f.mask, v1, out);
     S.launches += 2;
     return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
   };
 
-  std::vector<double> hist(4 * (size_t)Pm.n_outer, 0.0);
-  std::vector<double> xc_h(n_c), mask_h(n_b);
+  const int hw = 2 * n_levels;  // history entries per outer step
+  std::vector<double> hist((size_t)hw * Pm.n_outer, 0.0);
+  std::vector<double> prev_h, mask_h;
   for (int l = 0; l < Pm.n_outer; ++l) {
     // (2) coarse update
     MG_RC(S.weights(dDc, xc, l == 0, t, gcw));
     int it = 0;
     double rel = 0.0;
     MG_RC(S.cg(n_c, op_c, bc, xc, r, p, q, &it, &rel));
-    hist[4 * l + 0] = it;
-    hist[4 * l + 1] = rel;
-    if (!two) continue;
-    // compression: basis functions of the top keep_frac of the coarse cells
-    MG_CK(cudaMemcpyAsync(xc_h.data(), xc, n_c * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MG_CK(cudaStreamSynchronize(st));
-    std::vector<int64_t> order(n_c);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-      return std::fabs(xc_h[a]) > std::fabs(xc_h[b]);
-    });
-    const int64_t keep = std::min<int64_t>(
-        n_c, (int64_t)std::ceil(Pm.keep_frac * (double)n_c - 1e-12));
-    std::vector<char> kept(n_c, 0);
-    for (int64_t i = 0; i < keep; ++i) kept[order[i]] = 1;
-    for (int64_t k = 0; k < n_b; ++k) mask_h[k] = kept[B.coarse[k]] ? 1.0 : 0.0;
-    MG_CK(cudaMemcpyAsync(mask, mask_h.data(), n_b * sizeof(double), cudaMemcpyHostToDevice,
-                          st));
-    // (3) fine correction; G_f from the previous fine coordinates
-    // cells = R_f xb of the previous step (zero outside its kept set)
-    k_rf<<<grid_of(n_f), 256, 0, st>>>(n_f, d_cptr, d_cfun, d_csign, all, xb, cells);
-    MG_CK(cudaGetLastError());
-    MG_RC(S.weights(dDl, cells, l == 0, t, gfw));
-    // residual data r = dy - L_c xc, then b_f = mask R_f^T L_f^T r
-    MG_RC(S.apply_L(level_c, xc, S.data_buf()));
-    void* rd;
-    if (data_mode == MG_DATA_PROJECTED) {
-      k_sub_d<<<grid_of(2 * R), 256, 0, st>>>(2 * R, static_cast<const double*>(S.dy), S.pd,
-                                               S.pd2);
-      rd = S.pd2;
-    } else {
-      k_sub_f<<<grid_of(R * nt), 256, 0, st>>>(R * nt, static_cast<const float*>(S.dy), S.tr,
-                                                S.tr2);
-      rd = S.tr2;
+    hist[(size_t)hw * l + 0] = it;
+    hist[(size_t)hw * l + 1] = rel;
+    // (3) and the recursion over f_1 .. f_nf: comp is the reconstruction
+    // assembled so far, on the cells of the previous listed level
+    const double* comp = xc;
+    int64_t n_prev = n_c;
+    int level_prev = level_c;
+    for (int i = 0; i < nf; ++i) {
+      Fine& f = FL[i];
+      cur = &f;
+      // compression: basis functions under the top keep_frac of the
+      // previous level's cells by |comp|
+      prev_h.resize(n_prev);
+      MG_CK(cudaMemcpyAsync(prev_h.data(), comp, n_prev * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+      MG_CK(cudaStreamSynchronize(st));
+      std::vector<int64_t> order(n_prev);
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return std::fabs(prev_h[a]) > std::fabs(prev_h[b]);
+      });
+      const int64_t keep = std::min<int64_t>(
+          n_prev, (int64_t)std::ceil(Pm.keep_frac * (double)n_prev - 1e-12));
+      std::vector<char> kept(n_prev, 0);
+      for (int64_t k = 0; k < keep; ++k) kept[order[k]] = 1;
+      mask_h.resize(f.n_b);
+      for (int64_t k = 0; k < f.n_b; ++k) mask_h[k] = kept[f.B.coarse[k]] ? 1.0 : 0.0;
+      MG_CK(cudaMemcpyAsync(f.mask, mask_h.data(), f.n_b * sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+      // G_fi from the previous outer step's coordinates (zero outside its
+      // kept set): cells = R_fi x_fi
+      k_rf<<<grid_of(f.n), 256, 0, st>>>(f.n, f.cptr, f.cfun, f.csign, all, f.x, f.cells);
+      MG_CK(cudaGetLastError());
+      MG_RC(S.weights(f.dD, f.cells, l == 0, t, f.g));
+      // residual data r = dy - L comp (= dy - L_c x_c - sum_k<i L_fk x_fk),
+      // then b = mask R_fi^T L_fi^T r
+      MG_RC(S.apply_L(level_prev, comp, S.data_buf()));
+      void* rd;
+      if (data_mode == MG_DATA_PROJECTED) {
+        k_sub_d<<<grid_of(2 * R), 256, 0, st>>>(2 * R, static_cast<const double*>(S.dy), S.pd,
+                                                 S.pd2);
+        rd = S.pd2;
+      } else {
+        k_sub_f<<<grid_of(R * nt), 256, 0, st>>>(R * nt, static_cast<const float*>(S.dy), S.tr,
+                                                  S.tr2);
+        rd = S.tr2;
+      }
+      MG_CK(cudaGetLastError());
+      if (data_mode == MG_DATA_PROJECTED) {
+        MG_RC(S.apply_LT(f.level, rd, v1));
+      } else {
+        // apply_LT reads its traces directly (tr2 holds r)
+        MG_RC(mg_jacobian_T_apply(M, f.level, S.eps, shots, S.wav, dt, nt, S.tr2, v1,
+                                  Pm.ckpt_every, st, S.fl | MG_REUSE_CHECKPOINTS));
+      }
+      k_rft<<<grid_of(f.n_b), 256, 0, st>>>(f.n_b, f.plus, f.minus, f.mask, v1, bb);
+      MG_CK(cudaGetLastError());
+      MG_RC(S.cg(f.n_b, op_f, bb, f.x, r, p, q, &it, &rel));
+      hist[(size_t)hw * l + 2 * (i + 1)] = it;
+      hist[(size_t)hw * l + 2 * (i + 1) + 1] = rel;
+      // comp on this level: the previous level's value plus R_fi x_fi
+      k_rf<<<grid_of(f.n), 256, 0, st>>>(f.n, f.cptr, f.cfun, f.csign, all, f.x, f.cells);
+      k_level_sum<<<grid_of(f.n), 256, 0, st>>>(f.n, f.parent_d, comp, f.cells, f.comp);
+      MG_CK(cudaGetLastError());
+      S.launches += 2;
+      comp = f.comp;
+      n_prev = f.n;
+      level_prev = f.level;
     }
-    MG_CK(cudaGetLastError());
-    if (data_mode == MG_DATA_PROJECTED) {
-      MG_RC(S.apply_LT(level_f, rd, v1));
-    } else {
-      // apply_LT reads its traces directly (tr2 holds r)
-      MG_RC(mg_jacobian_T_apply(M, level_f, S.eps, shots, S.wav, dt, nt, S.tr2, v1,
-                                Pm.ckpt_every, st, S.fl | MG_REUSE_CHECKPOINTS));
-    }
-    k_rft<<<grid_of(n_b), 256, 0, st>>>(n_b, d_plus, d_minus, mask, v1, bb);
-    MG_CK(cudaGetLastError());
-    MG_RC(S.cg(n_b, op_f, bb, xb, r, p, q, &it, &rel));
-    hist[4 * l + 2] = it;
-    hist[4 * l + 3] = rel;
   }
-  // (4) x = R_c x_c + R_f x_b on level f, or x_c
-  double* xo = nullptr;
-  const int64_t n_out = two ? n_f : n_c;
-  if (host) MG_RC(A.get(&xo, n_out));
-  else xo = x_out;
-  if (two) {
-    k_rf<<<grid_of(n_f), 256, 0, st>>>(n_f, d_cptr, d_cfun, d_csign, all, xb, cells);
-    k_level_sum<<<grid_of(n_f), 256, 0, st>>>(n_f, d_parent, xc, cells, xo);
+  // (4) x = R_c x_c + sum_i R_fi x_fi on the last level
+  const int64_t n_out = nf ? FL[nf - 1].n : n_c;
+  const double* xl = nf ? FL[nf - 1].comp : xc;
+  if (host) {
+    MG_CK(cudaMemcpyAsync(x_out, xl, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
   } else {
-    MG_RC(S.lincomb(n_c, 1.0, xc, 0.0, nullptr, xo));
+    MG_CK(cudaMemcpyAsync(x_out, xl, n_out * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
-  MG_CK(cudaGetLastError());
-  if (host) MG_CK(cudaMemcpyAsync(x_out, xo, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (history) std::memcpy(history, hist.data(), hist.size() * sizeof(double));
   add_launches(M, S.launches);
   MG_CK(cudaStreamSynchronize(st));
   return MG_OK;
+}
+
+extern "C" int mg_tv_reconstruct(mg_mesh* M, int level_c, int level_f, const double* eps0,
+                                 const mg_shots* shots, const double* wavelet, double dt, int nt,
+                                 int data_mode, const void* dy, const float* u,
+                                 const mg_tv_params* params, double* x_out, double* history,
+                                 void* stream, int flags) {
+  const int levels[2] = {level_c, level_f};
+  const int n = level_f >= 0 ? 2 : 1;
+  if (!params || params->n_outer < 1) return MG_ERR_ARG;
+  std::vector<double> h((size_t)2 * n * params->n_outer, 0.0);
+  const int rc = mg_tv_reconstruct_levels(M, levels, n, eps0, shots, wavelet, dt, nt, data_mode,
+                                          dy, u, params, x_out, history ? h.data() : nullptr,
+                                          stream, flags);
+  if (rc == MG_OK && history) {
+    for (int l = 0; l < params->n_outer; ++l)
+      for (int k = 0; k < 4; ++k) history[4 * l + k] = k < 2 * n ? h[(size_t)2 * n * l + k] : 0.0;
+  }
+  return rc;
 }

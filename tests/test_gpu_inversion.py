@@ -144,3 +144,90 @@ def test_projected_data_inversion_matches_dense_oracle(mg, prob):
                              n_outer=1,
                              n_cg=100, cg_rtol=1e-12, ckpt_every=30)
     assert rel_l2(x.cpu().numpy(), ref[0]) < 1e-3
+
+
+def _level2_jacobian(w, dt, s):
+    m, sh = w.mesh, w.shots
+    pb = wave.Problem(m.coords, m.cells, m.bnd, w.eps, w.bc)
+    anc2 = m.ancestor(2)
+    return np.stack([wave.tangent(pb, dt, s, sh.src, sh.rec_ptr, sh.rec,
+                                  wave.prolong(np.eye(m.n_cells[2])[c], anc2)).ravel()
+                     for c in range(m.n_cells[2])], 1)
+
+
+def _levels_tol(L, Ds, Ps, Rs, ref, step, alpha):
+    """max(1e-3, 1e-4 kappa) over the coarse and every fine system of the
+    oracle's outer step `step` (weights from the step before)."""
+    first = step == 0
+    xc_prev = ref[step - 1][0] if step else np.zeros(Ps[0].shape[1])
+    Lc = L @ Ps[0]
+    g = inv.weights(Ds[0] @ xc_prev, first)
+    kappas = [np.linalg.cond(Lc.T @ Lc + alpha * Ds[0].T @ (g[:, None] * Ds[0]))]
+    for i in range(1, len(Ds)):
+        Lf, Df = L @ Ps[i] @ Rs[i], Ds[i] @ Rs[i]
+        K = ref[step][3][i - 1]
+        xf_prev = ref[step - 1][1][i - 1] if step else np.zeros(Rs[i].shape[1])
+        g = inv.weights(Df @ xf_prev, first)
+        kappas.append(np.linalg.cond(Lf[:, K].T @ Lf[:, K] +
+                                     alpha * Df[:, K].T @ (g[:, None] * Df[:, K])))
+    return max(1e-3, 1e-4 * max(kappas))
+
+
+@pytest.mark.parametrize("levels,keep", [([0, 1, 2], 1.0 / 3.0), ([0, 1, 2], 1.0),
+                                         ([0, 2], 1.0 / 3.0)])
+def test_level_recursion_matches_dense_oracle(mg, prob, levels, keep):
+    """The recursion over nested levels (tv_iteration_3) against the dense
+    oracle with L on the level-2 cells.  One outer step is compared element
+    by element (its systems have kappa < 1e3).  From the second step on, the
+    weights 1/|D x| of cells where D x nearly vanishes make kappa 1e5-1e10,
+    so the solutions themselves are not determined to any useful tolerance;
+    there the data misfit ||L x - dy||, which the well-determined directions
+    fix, is compared instead."""
+    import torch
+
+    w, dt, s = prob["w"], prob["dt"], prob["s"]
+    m = w.mesh
+    L2 = _level2_jacobian(w, dt, s)
+    Ds, Ps, bases, Rs = inv.hierarchy(m.coords, m.cells, m.cell_parent, m.n_cells, levels, 1.0)
+    alpha = 1e-2 * np.linalg.norm(L2 @ Ps[0], 2) ** 2
+    dy = prob["dy32"]
+    ref = inv.coarse_to_fine_levels(L2, Ds, Ps, bases, Rs, dy.ravel().astype(np.float64),
+                                    alpha, 2, keep)
+    mesh = mg.mesh_from_workload(w)
+    dyd = torch.as_tensor(dy, device="cuda:0")
+    dy64 = dy.ravel().astype(np.float64)
+    for n_outer in (1, 2):
+        x, hist = mg.tv_reconstruct_levels(mesh, levels, _dev(w.eps), w.shots, _dev(s), dt, dyd,
+                                           alpha=alpha, beta=1.0, n_outer=n_outer, n_cg=300,
+                                           cg_rtol=1e-12, keep_frac=keep, ckpt_every=30)
+        x = x.cpu().numpy()
+        assert x.shape == (m.n_cells[levels[-1]],) and np.all(np.isfinite(x))
+        assert hist.shape == (n_outer, 2 * len(levels))
+        assert np.all(hist[:, 0::2] >= 1) and np.all(hist[0, 1::2] < 1e-6)
+        if n_outer == 1:
+            tol = _levels_tol(L2, Ds, Ps, Rs, ref, 0, alpha)
+            assert tol < 0.1
+            assert rel_l2(x, ref[0][2]) < tol
+        else:
+            mis, mis_ref = (np.linalg.norm(L2 @ v - dy64) for v in (x, ref[1][2]))
+            assert abs(mis - mis_ref) <= 0.05 * mis_ref
+
+
+def test_level_recursion_with_two_levels_is_tv_reconstruct(mg, prob):
+    """mg_tv_reconstruct_levels with {0, 1} gives mg_tv_reconstruct's bits,
+    and with {1} the single-level iteration on level 1."""
+    import torch
+
+    w, dt, s = prob["w"], prob["dt"], prob["s"]
+    alpha = 1e-2 * np.linalg.norm(prob["L1"] @ prob["Rc"], 2) ** 2
+    dyd = torch.as_tensor(prob["dy32"], device="cuda:0")
+    mesh = mg.mesh_from_workload(w)
+    kw = dict(alpha=alpha, beta=1.0, n_outer=2, n_cg=100, cg_rtol=1e-12, ckpt_every=30)
+    a, ha = mg.tv_reconstruct(mesh, 0, _dev(w.eps), w.shots, _dev(s), dt, dyd, level_f=1, **kw)
+    b, hb = mg.tv_reconstruct_levels(mesh, [0, 1], _dev(w.eps), w.shots, _dev(s), dt, dyd, **kw)
+    assert torch.equal(a, b) and np.array_equal(ha, hb)
+    c, _ = mg.tv_reconstruct(mesh, 1, _dev(w.eps), w.shots, _dev(s), dt, dyd, **kw)
+    d, hd = mg.tv_reconstruct_levels(mesh, [1], _dev(w.eps), w.shots, _dev(s), dt, dyd, **kw)
+    assert torch.equal(c, d) and hd.shape == (2, 2)
+    with pytest.raises(mg._lib.MgError):
+        mg.tv_reconstruct_levels(mesh, [1, 1], _dev(w.eps), w.shots, _dev(s), dt, dyd, **kw)
