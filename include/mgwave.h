@@ -472,6 +472,41 @@ int mg_forward_pml(mg_mesh* mesh, const double* eps, const mg_shots* shots, cons
                    double dt, int nt, const double* xi, const double* zeta, float* traces,
                    void* stream, int flags);
 
+/* Jacobian of mg_forward_pml's traces with respect to the cell permittivity
+ * (App. A; only the eps-mass C depends on it), restricted to a level like
+ * mg_jacobian_apply: jv = J v with eps_fine = eps + t v[anc_level(e)].
+ * In lockstep with the forward, the fluxes of dp follow the flux update and
+ *   dp_{l+1} = dp_l + dt C^-1 (-(R+S) dp_l - sum_k B^(k)T dq^(k)_{l+1/2})
+ *              - (dC / C)(p_{l+1} - p_l),
+ * dC the lumped mass of the direction (exact for the discrete scheme).
+ *   level, v, jv  as mg_jacobian_apply ([cells of level] FP64 in,
+ *                 [rec_ptr[n_shots]][nt] FP32 out);
+ *   xi, zeta, the other arguments and flags as mg_forward_pml.
+ * Synchronous.  Errors as mg_forward_pml, and MG_ERR_ARG for the level. */
+int mg_jacobian_apply_pml(mg_mesh* mesh, int level, const double* eps, const mg_shots* shots,
+                          const double* wavelet, double dt, int nt, const double* xi,
+                          const double* zeta, const double* v, float* jv, void* stream,
+                          int flags);
+
+/* Gradient g = J^T w of mg_forward_pml's traces (the adjoint of the flux
+ * leapfrog, App. A), g_c = sum over the level cell's descendants e of
+ * d/deps_e sum_{r,l} w[r,l] y[r,l].  The forward keeps (p, q) every
+ * ckpt_every steps; each segment's p states are recomputed, then the
+ * adjoint steps run backwards: with a the adjoint of p_{l+1} and
+ * r = a dt / C, the flux adjoint Qt^(k) = Q^(k)/|e| becomes
+ * (1 - dt zeta_k) Qt^(k) - sum_a dphi_a/dx_k r[v_a], p_l receives
+ * a - (R+S) r + dt sum_k B^(k)T Qt^(k), and the C-sensitivity gathers
+ * -a (p_{l+1} - p_l) / C (FP64), turned into cells by |e|/(d+1).
+ *   w        [rec_ptr[n_shots]][nt] FP32 trace weights;
+ *   g        [cells of level] FP64 out;
+ *   ckpt_every  checkpoint spacing >= 1 (memory: ceil(nt / ckpt_every)
+ *            copies of p and q, and ckpt_every + 1 copies of p).
+ * Other arguments and flags as mg_jacobian_apply_pml.  Synchronous. */
+int mg_jacobian_T_apply_pml(mg_mesh* mesh, int level, const double* eps,
+                            const mg_shots* shots, const double* wavelet, double dt, int nt,
+                            const double* xi, const double* zeta, const float* w, double* g,
+                            int ckpt_every, void* stream, int flags);
+
 /* Nested prolongation of level-cell values to the finest cells (Sec. II-B:
  * eps_r = sum_j c_j chi'_j): out[e] = base[e] + v[anc_level(e)] for every
  * finest cell e (base may be NULL for 0).  v: [cells of level], base, out:

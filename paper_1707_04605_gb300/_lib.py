@@ -103,6 +103,14 @@ SIGNATURES = {
     "mg_forward_pml": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                  C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_int]),
+    "mg_jacobian_apply_pml": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int]),
+    "mg_jacobian_T_apply_pml": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                          C.c_void_p, C.c_int]),
     "mg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
                              C.c_void_p, C.c_void_p, C.c_int]),
     "mg_projected_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int,

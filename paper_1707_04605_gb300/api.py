@@ -503,6 +503,48 @@ def forward_pml(mesh: Mesh, eps, shots, wavelet, dt, xi=None, zeta=None, nt=None
     return out
 
 
+def jacobian_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, v, xi=None, zeta=None,
+                       nt=None, *, allow_cfl=False, stream=None):
+    """J v [n_traces, nt] float32 of forward_pml's traces for v on the cells of
+    ``level`` (mg_jacobian_apply_pml)."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    extra = [(v, "float64")] + [(x, "float64") for x in (xi, zeta) if x is not None]
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, extra, stream)
+    it = iter(ex)
+    pv = next(it)[1]
+    pxi = next(it)[1] if xi is not None else None
+    pzeta = next(it)[1] if zeta is not None else None
+    out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_jacobian_apply_pml(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
+                                   nt, pxi, pzeta, pv, _ptr(out), st, f)
+    L.check(rc, "mg_jacobian_apply_pml")
+    return out
+
+
+def jacobian_T_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, w, xi=None, zeta=None,
+                         nt=None, *, ckpt_every=64, allow_cfl=False, stream=None):
+    """J^T w (float64 [cells of level]) of forward_pml's traces for the trace
+    weights w [n_traces, nt] float32 (mg_jacobian_T_apply_pml)."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    extra = [(w, "float32")] + [(x, "float64") for x in (xi, zeta) if x is not None]
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, extra, stream)
+    it = iter(ex)
+    pw_ = next(it)[1]
+    pxi = next(it)[1] if xi is not None else None
+    pzeta = next(it)[1] if zeta is not None else None
+    g = _alloc(dev, (mesh.n_cells_per_level[level],), "float64", eps)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    rc = lib.mg_jacobian_T_apply_pml(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
+                                     nt, pxi, pzeta, pw_, _ptr(g), int(ckpt_every), st, f)
+    L.check(rc, "mg_jacobian_T_apply_pml")
+    return g
+
+
 def _ptr_array(xs):
     return (C.c_void_p * len(xs))(*[C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr")
                                                else x.ctypes.data) for x in xs])

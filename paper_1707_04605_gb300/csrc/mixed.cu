@@ -11,6 +11,19 @@
 // wavelet).  Natural outer boundary: the layer absorbs.  State: p [n][ld],
 // q [d][m][ld] FP32 (ld = padded shot count); a thread advances one float4
 // of shots of one node or one cell.  Sample l of a trace is p_{l+1}.
+//
+// Jacobians with respect to the cell permittivity (only C depends on it):
+//  * tangent, in lockstep with the forward: the fluxes of dp follow the
+//    same update; dp_{l+1} = dp_l + dt/C (-(R+S) dp_l - sum_k B^(k)T dq^(k))
+//    - (dC/C)(p_{l+1} - p_l), dC the lumped mass of the direction;
+//  * adjoint, backwards over checkpointed segments (p and q stored every
+//    ckpt_every steps, each segment's p states recomputed into a buffer):
+//    with a the adjoint of p_{l+1} (traces' weights at the receivers plus
+//    what step l+1 sends back) and r = a dt / C, the scaled flux adjoint
+//    Qt^(k) = Q^(k)/|e| becomes (1 - dt zeta_k) Qt^(k) - sum_a dphi_a/dx_k r[v_a],
+//    p_l receives a - (R+S) r + dt sum_k B^(k)T Qt^(k), and the C-sensitivity
+//    gathers -sum_l a (p_{l+1} - p_l) / C; the cell gradient is
+//    |e|/(d+1) times its sum over the cell's vertices, restricted to a level.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -130,6 +143,209 @@ __global__ void k_flux_p(int64_t n, int64_t m, int ld4, const int64_t* __restric
   }
 }
 
+// C_i = sum_{e ni i} x[e] |e| / (d+1) in FP64 (x = eps, or a direction)
+__global__ void k_flux_mass(CoefArgs c, const double* __restrict__ x, double* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= c.n) return;
+  double s = 0.0;
+  for (int64_t q = c.nc_ptr[r]; q < c.nc_ptr[r + 1]; ++q) s += x[c.nc_cell[q]] * c.nc_w[q];
+  out[r] = s;
+}
+
+__global__ void k_flux_ratio(int64_t n, const double* __restrict__ dC, const double* __restrict__ C,
+                             float* __restrict__ ratio) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) ratio[r] = (float)(dC[r] / C[r]);
+}
+
+// Tangent node update: p as in k_flux_p, and
+// dp <- dp + dt/C (-(R+S) dp - sum B^T dq) - ratio (p_new - p_old); traces of dp.
+template <int D>
+__global__ void k_flux_p_tan(int64_t n, int64_t m, int ld4, const int64_t* __restrict__ nc_ptr,
+                             const int32_t* __restrict__ nc_cell, const float* __restrict__ w,
+                             const float2* __restrict__ coef, const float* __restrict__ ratio,
+                             const float4* __restrict__ q, const float4* __restrict__ dq,
+                             float4* __restrict__ p, float4* __restrict__ dp,
+                             const int32_t* __restrict__ src_ptr,
+                             const int32_t* __restrict__ src_shot,
+                             const int32_t* __restrict__ rec_ptr,
+                             const int32_t* __restrict__ rec_shot,
+                             const int32_t* __restrict__ rec_trace, float f,
+                             float* __restrict__ traces, int nt, int l) {
+  const int64_t total = n * ld4;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ld4;
+    const int c4 = (int)(t - i * ld4);
+    float4 bt = make_float4(0.f, 0.f, 0.f, 0.f), dbt = bt;
+    for (int64_t s = __ldg(nc_ptr + i); s < __ldg(nc_ptr + i + 1); ++s) {
+      const int64_t e = __ldg(nc_cell + s);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float wk = __ldg(w + s * D + k);
+        const int64_t at = ((int64_t)k * m + e) * ld4 + c4;
+        const float4 qv = __ldg(q + at), dv = __ldg(dq + at);
+        bt.x = fmaf(wk, qv.x, bt.x);
+        bt.y = fmaf(wk, qv.y, bt.y);
+        bt.z = fmaf(wk, qv.z, bt.z);
+        bt.w = fmaf(wk, qv.w, bt.w);
+        dbt.x = fmaf(wk, dv.x, dbt.x);
+        dbt.y = fmaf(wk, dv.y, dbt.y);
+        dbt.z = fmaf(wk, dv.z, dbt.z);
+        dbt.w = fmaf(wk, dv.w, dbt.w);
+      }
+    }
+    const float2 c = __ldg(coef + i);
+    const float rt = __ldg(ratio + i);
+    float4 rhs = make_float4(-bt.x, -bt.y, -bt.z, -bt.w);
+    const int s0 = __ldg(src_ptr + i), s1 = __ldg(src_ptr + i + 1);
+    for (int s = s0; s < s1; ++s) {
+      const int d = __ldg(src_shot + s) - 4 * c4;
+      if (d == 0) rhs.x += f;
+      if (d == 1) rhs.y += f;
+      if (d == 2) rhs.z += f;
+      if (d == 3) rhs.w += f;
+    }
+    float4 pv = p[t], dv = dp[t];
+    const float4 inc = make_float4(fmaf(-c.y, pv.x, rhs.x), fmaf(-c.y, pv.y, rhs.y),
+                                   fmaf(-c.y, pv.z, rhs.z), fmaf(-c.y, pv.w, rhs.w));
+    dv.x = fmaf(-rt, c.x * inc.x, fmaf(c.x, fmaf(-c.y, dv.x, -dbt.x), dv.x));
+    dv.y = fmaf(-rt, c.x * inc.y, fmaf(c.x, fmaf(-c.y, dv.y, -dbt.y), dv.y));
+    dv.z = fmaf(-rt, c.x * inc.z, fmaf(c.x, fmaf(-c.y, dv.z, -dbt.z), dv.z));
+    dv.w = fmaf(-rt, c.x * inc.w, fmaf(c.x, fmaf(-c.y, dv.w, -dbt.w), dv.w));
+    pv.x = fmaf(c.x, inc.x, pv.x);
+    pv.y = fmaf(c.x, inc.y, pv.y);
+    pv.z = fmaf(c.x, inc.z, pv.z);
+    pv.w = fmaf(c.x, inc.w, pv.w);
+    p[t] = pv;
+    dp[t] = dv;
+    const int r0 = __ldg(rec_ptr + i), r1 = __ldg(rec_ptr + i + 1);
+    for (int r = r0; r < r1; ++r) {
+      const int d = __ldg(rec_shot + r) - 4 * c4;
+      if (d < 0 || d > 3) continue;
+      const float v = d == 0 ? dv.x : d == 1 ? dv.y : d == 2 ? dv.z : dv.w;
+      traces[(int64_t)__ldg(rec_trace + r) * nt + l] = v;
+    }
+  }
+}
+
+// Adjoint node kernel of reverse step l.  a = adjoint of p_{l+1}: what step
+// l+1 sent back (tp + dt sum_k B^(k)T Qt^(k); zero when l = nt-1) plus the
+// weights of the row's receivers at sample l.  Accumulates a (p_{l+1} - p_l)
+// in FP64, then stores r = a dt/C and tp = a - (R+S) r.
+template <int D>
+__global__ void k_flux_adj_p(int64_t n, int64_t m, int ld4, const int64_t* __restrict__ nc_ptr,
+                             const int32_t* __restrict__ nc_cell, const float* __restrict__ w,
+                             const float2* __restrict__ coef, const float4* __restrict__ Qt,
+                             float4* __restrict__ tp, float4* __restrict__ rr,
+                             const float4* __restrict__ p1, const float4* __restrict__ p0,
+                             double* __restrict__ hacc, const int32_t* __restrict__ rec_ptr,
+                             const int32_t* __restrict__ rec_shot,
+                             const int32_t* __restrict__ rec_trace,
+                             const float* __restrict__ W, int nt, int l, int first, float dt) {
+  const int64_t total = n * ld4;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ld4;
+    const int c4 = (int)(t - i * ld4);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!first) {
+      float4 bt = a;
+      for (int64_t s = __ldg(nc_ptr + i); s < __ldg(nc_ptr + i + 1); ++s) {
+        const int64_t e = __ldg(nc_cell + s);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float wk = __ldg(w + s * D + k);
+          const float4 qv = __ldg(Qt + ((int64_t)k * m + e) * ld4 + c4);
+          bt.x = fmaf(wk, qv.x, bt.x);
+          bt.y = fmaf(wk, qv.y, bt.y);
+          bt.z = fmaf(wk, qv.z, bt.z);
+          bt.w = fmaf(wk, qv.w, bt.w);
+        }
+      }
+      const float4 tv = tp[t];
+      a = make_float4(fmaf(dt, bt.x, tv.x), fmaf(dt, bt.y, tv.y), fmaf(dt, bt.z, tv.z),
+                      fmaf(dt, bt.w, tv.w));
+    }
+    const int r0 = __ldg(rec_ptr + i), r1 = __ldg(rec_ptr + i + 1);
+    for (int r = r0; r < r1; ++r) {
+      const int d = __ldg(rec_shot + r) - 4 * c4;
+      if (d < 0 || d > 3) continue;
+      const float v = __ldg(W + (int64_t)__ldg(rec_trace + r) * nt + l);
+      if (d == 0) a.x += v;
+      if (d == 1) a.y += v;
+      if (d == 2) a.z += v;
+      if (d == 3) a.w += v;
+    }
+    const float4 x1 = __ldg(p1 + t), x0 = __ldg(p0 + t);
+    double* h = hacc + 4 * t;
+    h[0] += (double)a.x * ((double)x1.x - (double)x0.x);
+    h[1] += (double)a.y * ((double)x1.y - (double)x0.y);
+    h[2] += (double)a.z * ((double)x1.z - (double)x0.z);
+    h[3] += (double)a.w * ((double)x1.w - (double)x0.w);
+    const float2 c = __ldg(coef + i);
+    const float4 r = make_float4(a.x * c.x, a.y * c.x, a.z * c.x, a.w * c.x);
+    rr[t] = r;
+    tp[t] = make_float4(fmaf(-c.y, r.x, a.x), fmaf(-c.y, r.y, a.y), fmaf(-c.y, r.z, a.z),
+                        fmaf(-c.y, r.w, a.w));
+  }
+}
+
+// Adjoint cell kernel: Qt^(k) <- (1 - dt zeta_k) Qt^(k) - sum_a dphi_a/dx_k r[v_a]
+template <int D>
+__global__ void k_flux_adj_q(int64_t m, int ld4, const int32_t* __restrict__ cells,
+                             const float* __restrict__ grad, const float* __restrict__ damp,
+                             const float4* __restrict__ rr, float4* __restrict__ Qt, float dt) {
+  const int64_t total = m * ld4;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / ld4;
+    const int c4 = (int)(t - e * ld4);
+    float4 rv[D + 1];
+#pragma unroll
+    for (int a = 0; a <= D; ++a)
+      rv[a] = __ldg(rr + (int64_t)__ldg(cells + e * (D + 1) + a) * ld4 + c4);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a <= D; ++a) {
+        const float g = __ldg(grad + (e * (D + 1) + a) * D + k);
+        acc.x = fmaf(g, rv[a].x, acc.x);
+        acc.y = fmaf(g, rv[a].y, acc.y);
+        acc.z = fmaf(g, rv[a].z, acc.z);
+        acc.w = fmaf(g, rv[a].w, acc.w);
+      }
+      const float keep = 1.0f - dt * __ldg(damp + e * D + k);
+      float4* qp = Qt + ((int64_t)k * m + e) * ld4 + c4;
+      const float4 o = *qp;
+      *qp = make_float4(fmaf(keep, o.x, -acc.x), fmaf(keep, o.y, -acc.y),
+                        fmaf(keep, o.z, -acc.z), fmaf(keep, o.w, -acc.w));
+    }
+  }
+}
+
+// gC_i = -sum_s hacc[i][s] / C_i (fixed order over the shots)
+__global__ void k_flux_hsum(int64_t n, int ld, const double* __restrict__ hacc,
+                            const double* __restrict__ C, double* __restrict__ gC) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < ld; ++j) s += hacc[i * ld + j];
+  gC[i] = -s / C[i];
+}
+
+// g_e = |e| / (d+1) sum_a gC[v_a]
+__global__ void k_flux_cell_grad(int64_t m, int k1, const int32_t* __restrict__ cells,
+                                 const double* __restrict__ vol, const double* __restrict__ gC,
+                                 double* __restrict__ g) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  double s = 0.0;
+  for (int a = 0; a < k1; ++a) s += gC[cells[e * k1 + a]];
+  g[e] = vol[e] / k1 * s;
+}
+
 struct Scratch {
   cudaStream_t st;
   std::vector<void*> p;
@@ -150,6 +366,10 @@ struct Scratch {
     return static_cast<T*>(x);
   }
   template <class T>
+  T* put(const T* src, size_t count) {  // host array
+    return put(std::vector<T>(src, src + count));
+  }
+  template <class T>
   T* get(size_t count) {
     void* x = nullptr;
     if (cudaMallocAsync(&x, std::max<size_t>(count, 1) * sizeof(T), st) != cudaSuccess)
@@ -163,15 +383,53 @@ int grid_for(int64_t total) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
 }
 
-}  // namespace
-}  // namespace mg
+// Everything the three entry points share: geometry, layer damping, event
+// lists, source amplitudes, per-node coefficients, device inputs.
+struct Flux {
+  int d = 0, k1 = 0, S = 0, ld = 0, ld4 = 0, nt = 0;
+  int64_t n = 0, m = 0, R = 0;
+  double dt = 0.0;
+  bool host = false;
+  cudaStream_t st = nullptr;
+  MeshView V;
+  CoefArgs c;
+  const double* eps_d = nullptr;
+  int32_t* cells = nullptr;
+  float *grad = nullptr, *w = nullptr, *damp = nullptr;
+  int32_t *sp = nullptr, *ss = nullptr, *rp = nullptr, *rs = nullptr, *rt = nullptr;
+  std::vector<float> fl;
+  float2* coef = nullptr;
 
-extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* shots,
-                              const double* wavelet, double dt, int nt, const double* xi,
-                              const double* zeta, float* traces, void* stream, int flags) {
-  using namespace mg;
-  if (!M || !eps || !shots || !wavelet || !traces || nt < 1 || !(dt > 0.0)) return MG_ERR_ARG;
-  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  void step_q(float* p, float* q) const {
+    const int g = grid_for(m * ld4);
+    if (d == 2)
+      k_flux_q<2><<<g, 256, 0, st>>>(m, ld4, cells, grad, damp,
+                                      reinterpret_cast<const float4*>(p),
+                                      reinterpret_cast<float4*>(q), (float)dt);
+    else
+      k_flux_q<3><<<g, 256, 0, st>>>(m, ld4, cells, grad, damp,
+                                      reinterpret_cast<const float4*>(p),
+                                      reinterpret_cast<float4*>(q), (float)dt);
+  }
+  void step_p(const float* q, float* p, float* traces, int l) const {
+    const int g = grid_for(n * ld4);
+    if (d == 2)
+      k_flux_p<2><<<g, 256, 0, st>>>(n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
+                                      reinterpret_cast<const float4*>(q),
+                                      reinterpret_cast<float4*>(p), sp, ss, rp, rs, rt, fl[l],
+                                      traces, nt, l);
+    else
+      k_flux_p<3><<<g, 256, 0, st>>>(n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
+                                      reinterpret_cast<const float4*>(q),
+                                      reinterpret_cast<float4*>(p), sp, ss, rp, rs, rt, fl[l],
+                                      traces, nt, l);
+  }
+};
+
+int flux_setup(mg_mesh* M, const double* eps, const mg_shots* shots, const double* wavelet,
+               double dt, int nt, const double* xi, const double* zeta, int flags,
+               cudaStream_t st, Scratch& X, Flux& F) {
+  if (!M || !eps || !shots || !wavelet || nt < 1 || !(dt > 0.0)) return MG_ERR_ARG;
   const HostMesh* hm = host_mesh(M);
   const int d = hm->dim, k1 = d + 1;
   if (d < 2 || d > kMaxDim) return MG_ERR_UNSUPPORTED;
@@ -186,16 +444,17 @@ extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* sho
   }
   for (int64_t r = 0; r < R; ++r)
     if (shots->rec[r] < 0 || shots->rec[r] >= n) return MG_ERR_ARG;
-  int dev_prev = 0;
-  if (cudaGetDevice(&dev_prev) != cudaSuccess) return MG_ERR_CUDA;
-  if (cudaSetDevice(mesh_device(M)) != cudaSuccess) return MG_ERR_CUDA;
-  struct Restore {
-    int dv;
-    ~Restore() { cudaSetDevice(dv); }
-  } restore{dev_prev};
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool host = flags & MG_HOST_PTRS;
-  Scratch X(st);
+  F.d = d;
+  F.k1 = k1;
+  F.S = S;
+  F.n = n;
+  F.m = m;
+  F.R = R;
+  F.nt = nt;
+  F.dt = dt;
+  F.host = host;
+  F.st = st;
 
   // per cell: gradients of the barycentric functions (FP64 -> FP32) and
   // per node-cell incidence: |e| dphi_i/dx_k
@@ -245,9 +504,8 @@ extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* sho
     }
   // damping zeta per cell and direction (FP32), sources / receivers per row
   std::vector<float> damp((size_t)m * d, 0.0f);
-  std::vector<double> zeta_h, xi_h;
   if (zeta) {
-    zeta_h.resize((size_t)m * d);
+    std::vector<double> zeta_h((size_t)m * d);
     if (host) std::copy(zeta, zeta + (size_t)m * d, zeta_h.begin());
     else if (cudaMemcpy(zeta_h.data(), zeta, zeta_h.size() * sizeof(double),
                         cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -257,8 +515,8 @@ extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* sho
       damp[q] = (float)zeta_h[q];
     }
   }
-  const int ld = S <= 4 ? 4 : ((S + 3) / 4) * 4;
-  const int ld4 = ld / 4;
+  F.ld = S <= 4 ? 4 : ((S + 3) / 4) * 4;
+  F.ld4 = F.ld / 4;
   std::vector<int32_t> sp(n + 1, 0), ss(S), rp(n + 1, 0), rs(R), rt(R);
   const std::vector<int32_t>& perm = hm->perm;
   for (int s = 0; s < S; ++s) sp[perm[shots->src[s]] + 1]++;
@@ -283,73 +541,278 @@ extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* sho
   else if (cudaMemcpy(wav_h.data(), wavelet, nt * sizeof(double), cudaMemcpyDeviceToHost) !=
            cudaSuccess)
     return MG_ERR_CUDA;
-  std::vector<float> fl(nt);
+  F.fl.resize(nt);
   double acc = 0.0;
   for (int l = 0; l < nt; ++l) {
     acc += dt * wav_h[l];
-    fl[l] = (float)acc;
+    F.fl[l] = (float)acc;
   }
 
-  MeshView V;
-  if (mesh_view(M, &V) != MG_OK) return MG_ERR_ARG;
-  const double* eps_d = eps;
+  if (mesh_view(M, &F.V) != MG_OK) return MG_ERR_ARG;
+  F.eps_d = eps;
   const double* xi_d = xi;
   if (host) {
-    eps_d = X.put(std::vector<double>(eps, eps + m));
-    if (xi) xi_d = X.put(std::vector<double>(xi, xi + m));
-    if (!eps_d || (xi && !xi_d)) return MG_ERR_OOM;
+    F.eps_d = X.put(eps, (size_t)m);
+    if (xi) xi_d = X.put(xi, (size_t)m);
+    if (!F.eps_d || (xi && !xi_d)) return MG_ERR_OOM;
   }
   if (!(flags & MG_ALLOW_CFL)) {
     double dtc = 0.0;
-    const int rc = mg_cfl_dt(M, eps_d, 0, stream, &dtc);
+    const int rc = mg_cfl_dt(M, F.eps_d, 0, st, &dtc);
     if (rc) return rc;
     if (dt > dtc * (1.0 + 1e-12)) return MG_ERR_CFL;
   }
-  int32_t* d_cells = X.put(hm->cells);
-  float* d_grad = X.put(grad);
-  float* d_w = X.put(wnc);
-  float* d_damp = X.put(damp);
-  int32_t *d_sp = X.put(sp), *d_ss = X.put(ss), *d_rp = X.put(rp), *d_rs = X.put(rs),
-          *d_rt = X.put(rt);
-  float2* coef = X.get<float2>(n);
-  float* p = X.get<float>((size_t)n * ld);
-  float* q = X.get<float>((size_t)d * m * ld);
-  float* tr = host ? X.get<float>((size_t)R * nt) : traces;
-  if (!d_cells || !d_grad || !d_w || !d_damp || !d_sp || !d_ss || !d_rp || !d_rs || !d_rt ||
-      !coef || !p || !q || !tr)
+  F.cells = X.put(hm->cells);
+  F.grad = X.put(grad);
+  F.w = X.put(wnc);
+  F.damp = X.put(damp);
+  F.sp = X.put(sp);
+  F.ss = X.put(ss);
+  F.rp = X.put(rp);
+  F.rs = X.put(rs);
+  F.rt = X.put(rt);
+  F.coef = X.get<float2>(n);
+  if (!F.cells || !F.grad || !F.w || !F.damp || !F.sp || !F.ss || !F.rp || !F.rs || !F.rt ||
+      !F.coef)
     return MG_ERR_OOM;
-  if (cudaMemsetAsync(p, 0, (size_t)n * ld * sizeof(float), st) ||
-      cudaMemsetAsync(q, 0, (size_t)d * m * ld * sizeof(float), st))
+  F.c = F.V.coef_base;
+  F.c.eps = F.eps_d;
+  k_flux_coefs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F.c, xi_d, dt, F.coef);
+  return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+struct DeviceScope {
+  int prev = 0;
+  bool ok = false;
+  explicit DeviceScope(int dev) {
+    ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() { cudaSetDevice(prev); }
+};
+
+#define MG_FX(x)                  \
+  do {                            \
+    const int rc_ = (x);          \
+    if (rc_ != MG_OK) return rc_; \
+  } while (0)
+
+}  // namespace
+}  // namespace mg
+
+extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* shots,
+                              const double* wavelet, double dt, int nt, const double* xi,
+                              const double* zeta, float* traces, void* stream, int flags) {
+  using namespace mg;
+  if (!M || !eps || !shots || !wavelet || !traces || nt < 1 || !(dt > 0.0)) return MG_ERR_ARG;
+  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  DeviceScope scope(mesh_device(M));
+  if (!scope.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch X(st);
+  Flux F;
+  MG_FX(flux_setup(M, eps, shots, wavelet, dt, nt, xi, zeta, flags, st, X, F));
+  const int64_t n = F.n, m = F.m, R = F.R;
+  float* p = X.get<float>((size_t)n * F.ld);
+  float* q = X.get<float>((size_t)F.d * m * F.ld);
+  float* tr = F.host ? X.get<float>((size_t)R * nt) : traces;
+  if (!p || !q || !tr) return MG_ERR_OOM;
+  if (cudaMemsetAsync(p, 0, (size_t)n * F.ld * sizeof(float), st) ||
+      cudaMemsetAsync(q, 0, (size_t)F.d * m * F.ld * sizeof(float), st))
     return MG_ERR_CUDA;
-  CoefArgs c = V.coef_base;
-  c.eps = eps_d;
-  k_flux_coefs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, xi_d, dt, coef);
-  if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
-  const int gq = grid_for(m * ld4), gp = grid_for(n * ld4);
-  const float fdt = (float)dt;
   for (int l = 0; l < nt; ++l) {
-    if (d == 2) {
-      k_flux_q<2><<<gq, 256, 0, st>>>(m, ld4, d_cells, d_grad, d_damp,
-                                       reinterpret_cast<const float4*>(p),
-                                       reinterpret_cast<float4*>(q), fdt);
-      k_flux_p<2><<<gp, 256, 0, st>>>(n, m, ld4, V.coef_base.nc_ptr, V.coef_base.nc_cell, d_w,
-                                       coef, reinterpret_cast<const float4*>(q),
-                                       reinterpret_cast<float4*>(p), d_sp, d_ss, d_rp, d_rs,
-                                       d_rt, fl[l], tr, nt, l);
-    } else {
-      k_flux_q<3><<<gq, 256, 0, st>>>(m, ld4, d_cells, d_grad, d_damp,
-                                       reinterpret_cast<const float4*>(p),
-                                       reinterpret_cast<float4*>(q), fdt);
-      k_flux_p<3><<<gp, 256, 0, st>>>(n, m, ld4, V.coef_base.nc_ptr, V.coef_base.nc_cell, d_w,
-                                       coef, reinterpret_cast<const float4*>(q),
-                                       reinterpret_cast<float4*>(p), d_sp, d_ss, d_rp, d_rs,
-                                       d_rt, fl[l], tr, nt, l);
-    }
+    F.step_q(p, q);
+    F.step_p(q, p, tr, l);
   }
   if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
   add_launches(M, 1 + 2 * (int64_t)nt);
-  if (host && cudaMemcpyAsync(traces, tr, (size_t)R * nt * sizeof(float), cudaMemcpyDeviceToHost,
-                              st) != cudaSuccess)
+  if (F.host && cudaMemcpyAsync(traces, tr, (size_t)R * nt * sizeof(float),
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MG_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+extern "C" int mg_jacobian_apply_pml(mg_mesh* M, int level, const double* eps,
+                                     const mg_shots* shots, const double* wavelet, double dt,
+                                     int nt, const double* xi, const double* zeta,
+                                     const double* v, float* jv, void* stream, int flags) {
+  using namespace mg;
+  if (!M || !eps || !shots || !wavelet || !v || !jv || nt < 1 || !(dt > 0.0)) return MG_ERR_ARG;
+  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  const HostMesh* hm = host_mesh(M);
+  if (level < 0 || level >= hm->n_levels) return MG_ERR_ARG;
+  DeviceScope scope(mesh_device(M));
+  if (!scope.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch X(st);
+  Flux F;
+  MG_FX(flux_setup(M, eps, shots, wavelet, dt, nt, xi, zeta, flags, st, X, F));
+  const int64_t n = F.n, m = F.m, R = F.R, nc = hm->n_cells_level[level];
+  const double* v_d = F.host ? X.put(v, (size_t)nc) : v;
+  const int32_t* anc = X.put(hm->ancestors[level]);
+  double* dv = X.get<double>(m);
+  double* C = X.get<double>(n);
+  double* dC = X.get<double>(n);
+  float* ratio = X.get<float>(n);
+  const size_t ns = (size_t)n * F.ld, qs = (size_t)F.d * m * F.ld;
+  float* p = X.get<float>(ns);
+  float* dp = X.get<float>(ns);
+  float* q = X.get<float>(qs);
+  float* dq = X.get<float>(qs);
+  float* tr = F.host ? X.get<float>((size_t)R * nt) : jv;
+  if (!v_d || !anc || !dv || !C || !dC || !ratio || !p || !dp || !q || !dq || !tr)
+    return MG_ERR_OOM;
+  MG_FX(launch_prolong(m, anc, v_d, nullptr, dv, st));
+  const unsigned gn = (unsigned)((n + 255) / 256);
+  k_flux_mass<<<gn, 256, 0, st>>>(F.c, F.eps_d, C);
+  k_flux_mass<<<gn, 256, 0, st>>>(F.c, dv, dC);
+  k_flux_ratio<<<gn, 256, 0, st>>>(n, dC, C, ratio);
+  if (cudaMemsetAsync(p, 0, ns * sizeof(float), st) ||
+      cudaMemsetAsync(dp, 0, ns * sizeof(float), st) ||
+      cudaMemsetAsync(q, 0, qs * sizeof(float), st) ||
+      cudaMemsetAsync(dq, 0, qs * sizeof(float), st))
+    return MG_ERR_CUDA;
+  const int gp = grid_for(n * F.ld4);
+  for (int l = 0; l < nt; ++l) {
+    F.step_q(p, q);
+    F.step_q(dp, dq);
+    if (F.d == 2)
+      k_flux_p_tan<2><<<gp, 256, 0, st>>>(
+          n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef, ratio,
+          reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
+          reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp, F.rs,
+          F.rt, F.fl[l], tr, nt, l);
+    else
+      k_flux_p_tan<3><<<gp, 256, 0, st>>>(
+          n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef, ratio,
+          reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
+          reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp, F.rs,
+          F.rt, F.fl[l], tr, nt, l);
+  }
+  if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
+  add_launches(M, 5 + 3 * (int64_t)nt);
+  if (F.host && cudaMemcpyAsync(jv, tr, (size_t)R * nt * sizeof(float), cudaMemcpyDeviceToHost,
+                                st) != cudaSuccess)
+    return MG_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
+                                       const mg_shots* shots, const double* wavelet, double dt,
+                                       int nt, const double* xi, const double* zeta,
+                                       const float* w, double* g, int ckpt_every, void* stream,
+                                       int flags) {
+  using namespace mg;
+  if (!M || !eps || !shots || !wavelet || !w || !g || nt < 1 || !(dt > 0.0) || ckpt_every < 1)
+    return MG_ERR_ARG;
+  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  const HostMesh* hm = host_mesh(M);
+  if (level < 0 || level >= hm->n_levels) return MG_ERR_ARG;
+  DeviceScope scope(mesh_device(M));
+  if (!scope.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch X(st);
+  Flux F;
+  MG_FX(flux_setup(M, eps, shots, wavelet, dt, nt, xi, zeta, flags, st, X, F));
+  const int64_t n = F.n, m = F.m, R = F.R, nc = hm->n_cells_level[level];
+  const int K = std::min(ckpt_every, nt);
+  const int nck = (nt + K - 1) / K;
+  const size_t ns = (size_t)n * F.ld, qs = (size_t)F.d * m * F.ld;
+  const float* W = F.host ? X.put(w, (size_t)R * nt) : w;
+  float* ck_p = X.get<float>(ns * nck);
+  float* ck_q = X.get<float>(qs * nck);
+  float* p = X.get<float>(ns);
+  float* q = X.get<float>(qs);
+  float* seg = X.get<float>(ns * (K + 1));
+  float* trd = X.get<float>((size_t)R * nt);
+  float* tp = X.get<float>(ns);
+  float* rr = X.get<float>(ns);
+  float* Qt = X.get<float>(qs);
+  double* hacc = X.get<double>(ns);
+  double* C = X.get<double>(n);
+  double* gC = X.get<double>(n);
+  double* vol = X.put(hm->cell_vol);
+  double* gf = X.get<double>(m);
+  std::vector<int64_t> lp;
+  std::vector<int32_t> li;
+  level_children(*hm, level, lp, li);
+  int64_t* lp_d = X.put(lp);
+  int32_t* li_d = X.put(li);
+  double* go = F.host ? X.get<double>(nc) : g;
+  if (!W || !ck_p || !ck_q || !p || !q || !seg || !trd || !tp || !rr || !Qt || !hacc || !C ||
+      !gC || !vol || !gf || !lp_d || !li_d || !go)
+    return MG_ERR_OOM;
+  if (cudaMemsetAsync(p, 0, ns * sizeof(float), st) ||
+      cudaMemsetAsync(q, 0, qs * sizeof(float), st) ||
+      cudaMemsetAsync(Qt, 0, qs * sizeof(float), st) ||
+      cudaMemsetAsync(hacc, 0, ns * sizeof(double), st))
+    return MG_ERR_CUDA;
+  int64_t launches = 0;
+  // forward, keeping (p_l, q_{l-1/2}) at l = 0, K, 2K, ...
+  for (int l = 0; l < nt; ++l) {
+    if (l % K == 0) {
+      if (cudaMemcpyAsync(ck_p + ns * (l / K), p, ns * sizeof(float), cudaMemcpyDeviceToDevice,
+                          st) ||
+          cudaMemcpyAsync(ck_q + qs * (l / K), q, qs * sizeof(float), cudaMemcpyDeviceToDevice,
+                          st))
+        return MG_ERR_CUDA;
+    }
+    F.step_q(p, q);
+    F.step_p(q, p, trd, l);
+    launches += 2;
+  }
+  // reverse, segment by segment
+  const int gp = grid_for(n * F.ld4), gq = grid_for(m * F.ld4);
+  const float fdt = (float)dt;
+  for (int c = nck - 1; c >= 0; --c) {
+    const int l0 = c * K, l1 = std::min(nt, l0 + K);
+    if (cudaMemcpyAsync(p, ck_p + ns * c, ns * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
+        cudaMemcpyAsync(q, ck_q + qs * c, qs * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
+        cudaMemcpyAsync(seg, p, ns * sizeof(float), cudaMemcpyDeviceToDevice, st))
+      return MG_ERR_CUDA;
+    for (int l = l0; l < l1; ++l) {
+      F.step_q(p, q);
+      F.step_p(q, p, trd, l);
+      if (cudaMemcpyAsync(seg + ns * (l + 1 - l0), p, ns * sizeof(float),
+                          cudaMemcpyDeviceToDevice, st))
+        return MG_ERR_CUDA;
+      launches += 2;
+    }
+    for (int l = l1 - 1; l >= l0; --l) {
+      const float4* p1 = reinterpret_cast<const float4*>(seg + ns * (l + 1 - l0));
+      const float4* p0 = reinterpret_cast<const float4*>(seg + ns * (l - l0));
+      const int first = l == nt - 1;
+      if (F.d == 2) {
+        k_flux_adj_p<2><<<gp, 256, 0, st>>>(n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+                                             reinterpret_cast<const float4*>(Qt),
+                                             reinterpret_cast<float4*>(tp),
+                                             reinterpret_cast<float4*>(rr), p1, p0, hacc, F.rp,
+                                             F.rs, F.rt, W, nt, l, first, fdt);
+        k_flux_adj_q<2><<<gq, 256, 0, st>>>(m, F.ld4, F.cells, F.grad, F.damp,
+                                             reinterpret_cast<const float4*>(rr),
+                                             reinterpret_cast<float4*>(Qt), fdt);
+      } else {
+        k_flux_adj_p<3><<<gp, 256, 0, st>>>(n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+                                             reinterpret_cast<const float4*>(Qt),
+                                             reinterpret_cast<float4*>(tp),
+                                             reinterpret_cast<float4*>(rr), p1, p0, hacc, F.rp,
+                                             F.rs, F.rt, W, nt, l, first, fdt);
+        k_flux_adj_q<3><<<gq, 256, 0, st>>>(m, F.ld4, F.cells, F.grad, F.damp,
+                                             reinterpret_cast<const float4*>(rr),
+                                             reinterpret_cast<float4*>(Qt), fdt);
+      }
+      launches += 2;
+    }
+  }
+  // gradient: C-sensitivity per node, per finest cell, restricted to the level
+  const unsigned gn = (unsigned)((n + 255) / 256), gm = (unsigned)((m + 255) / 256);
+  k_flux_mass<<<gn, 256, 0, st>>>(F.c, F.eps_d, C);
+  k_flux_hsum<<<gn, 256, 0, st>>>(n, F.ld, hacc, C, gC);
+  k_flux_cell_grad<<<gm, 256, 0, st>>>(m, F.k1, F.cells, vol, gC, gf);
+  if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
+  MG_FX(launch_restrict(nc, lp_d, li_d, gf, go, st));
+  add_launches(M, launches + 5);
+  if (F.host && cudaMemcpyAsync(g, go, nc * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess)
     return MG_ERR_CUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
