@@ -59,10 +59,20 @@ def parse():
                     help="skip the TV-reconstruction and approximate-Jacobian timings")
     ap.add_argument("--no-batch-leg", action="store_true",
                     help="skip the uneven multi-instance batch timing")
+    ap.add_argument("--no-pml-leg", action="store_true",
+                    help="skip the split-field PML path timing")
     ap.add_argument("--min-blocks", type=int, default=-1,
                     help="register cap of the forward row kernel (0 or 5)")
     ap.add_argument("--lane-vec", type=int, default=-1,
                     help="row kernels: float4 vectors of shots per lane (1, 2, 4)")
+    ap.add_argument("--dep-launch", type=int, default=-1,
+                    help="row kernels as programmatic dependent launches (0 or 1)")
+    ap.add_argument("--checkpoints", action="store_true",
+                    help="adjoint from checkpoints every 256 steps even when HBM could "
+                         "hold every forward state")
+    ap.add_argument("--kept-groups", default="",
+                    help="shot groups forward,adjoint,tangent of the kept-history path "
+                         "(instead of timing 1, 2, 4)")
     ap.add_argument("--hbm-only", action="store_true",
                     help="only the 3D ellipsoid forward measurement")
     return ap.parse_args()
@@ -143,12 +153,13 @@ def clocks_stop(proc, gpu_index):
 # only while those sources are unchanged, else the roofline's traffic is null.
 KERNEL_SOURCES = ["kernels_rows.cu", "device_util.cuh", "kernels.cuh"]
 TRAFFIC = {
-    # (workload, batch, tile_rows, groups, min_blocks, bulk): (bytes, sha1)
-    # k_step_rows<16,2,1>, --cache-control none, mean of launches 2-5 (the
-    # states stay in L2; DRAM sees write-backs)
-    ("asteroid_2d", 2, 0, 1, 0, 0): (11.2e6, "cbdedf17368d2819d576b09129ba7b10fd3ce055"),
-    # k_step_rows<8,2,5>, one launch
-    ("ellipsoid_3d", 2, 0, 1, 5, 0): (1.668e9, "cbdedf17368d2819d576b09129ba7b10fd3ce055"),
+    # (workload, kept history, batch, tile_rows, groups, min_blocks, bulk): (bytes, sha1)
+    # k_step_rows<16,2,1> writing every state into the kept history,
+    # --cache-control none, mean of launches 3-5: 31.6 MB read + 31.1 MB
+    # written (the new state goes to HBM; part of p_l / p_{l-1} is re-read)
+    ("asteroid_2d", True, 2, 0, 1, 0, 0): (62.7e6, "deeea868f36dd3a57cc2713e08ffc4f98ffaa5a0"),
+    # k_step_rows<8,2,5>, two launches: 1228.2 MB read + 437.8 MB written
+    ("ellipsoid_3d", False, 2, 0, 1, 5, 0): (1.666e9, "deeea868f36dd3a57cc2713e08ffc4f98ffaa5a0"),
 }
 
 
@@ -164,8 +175,8 @@ def sources_sha1():
     return h.hexdigest()
 
 
-def traffic_for(workload, fwd):
-    key = (workload, fwd["batch"], fwd["tile_rows"], fwd.get("groups", 1),
+def traffic_for(workload, fwd, kept=False):
+    key = (workload, bool(kept), fwd["batch"], fwd["tile_rows"], fwd.get("groups", 1),
            fwd.get("min_blocks", 0), fwd.get("bulk", 0))
     hit = TRAFFIC.get(key)
     return hit[0] if hit and hit[1] == sources_sha1() else None
@@ -198,6 +209,8 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
             mesh.set_min_blocks(args.min_blocks)
     else:
         mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
+    if args is not None and args.dep_launch != -1:
+        mesh.set_dependent_launch(args.dep_launch)
     tuning = mesh.tuning()
     mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
     torch.cuda.synchronize()
@@ -313,6 +326,69 @@ def approx_jacobian_leg(mg, torch, mesh, w, eps_d, wav_d, dt, y, level=1, n_chec
             "relative_error_sampled_cells": errs}
 
 
+def pml_leg(mg, torch, mesh, w, eps_d, wav_d, dt, nt=1000, ckpt=100):
+    """The split-field PML path (first-order flux leapfrog with element
+    fluxes): forward, J v and J^T w on the bench mesh with the square layer
+    of thickness 15% of the half-width (varsigma dt = 1/4), over `nt` steps;
+    algorithmic bytes per forward step: p read by the flux update, q read
+    and written, q read by the node update, p read and written."""
+    stream = torch.cuda.current_stream()
+    m = w.mesh
+    half = float(np.abs(m.coords).max())
+    c = m.coords[m.cells].mean(axis=1)
+    a = np.abs(c)
+    vs = 0.25 / dt
+    xi = np.where(a.max(axis=1) >= 0.85 * half, vs, 0.0)
+    zeta = np.where(a >= 0.85 * half, vs, 0.0)
+    dev = eps_d.device
+    xi_d = torch.as_tensor(xi, dtype=torch.float64, device=dev)
+    zeta_d = torch.as_tensor(np.ascontiguousarray(zeta), dtype=torch.float64, device=dev)
+    wav = wav_d[:nt].contiguous()
+    v = torch.as_tensor(np.random.default_rng(0).standard_normal(m.n_cells[1]),
+                        dtype=torch.float64, device=dev)
+    calls = {
+        "forward": lambda: mg.forward_pml(mesh, eps_d, w.shots, wav, dt, xi_d, zeta_d),
+        "tangent": lambda: mg.jacobian_apply_pml(mesh, 1, eps_d, w.shots, wav, dt, v, xi_d,
+                                                 zeta_d),
+    }
+    secs = {}
+    y = None
+    for name, fn in calls.items():
+        out = fn()                                              # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs[name] = e0.elapsed_time(e1) / 1e3
+        if name == "forward":
+            y = out
+    fn = lambda: mg.jacobian_T_apply_pml(mesh, 1, eps_d, w.shots, wav, dt, y, xi_d, zeta_d,
+                                         ckpt_every=ckpt)
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs["adjoint"] = e0.elapsed_time(e1) / 1e3
+    n, mc, d = w.n_nodes, len(m.cells), m.coords.shape[1]
+    S = w.shots.n_shots
+    ld = 4 if S <= 4 else (S + 3) // 4 * 4
+    bytes_fwd = 4.0 * ld * (3 * n + 3 * d * mc)
+    us = {k: 1e6 * s / nt for k, s in secs.items()}
+    return {"workload": f"{w.name} with a square layer (xi, zeta = {vs:.3g} beyond 0.85 of the "
+                        f"half-width): {n} nodes, {mc} cells, {S} shots, {nt} steps",
+            "seconds": secs, "us_per_step": us,
+            "forward_updates_per_s": n * S * nt / secs["forward"],
+            "algorithmic_bytes_per_forward_step": bytes_fwd,
+            "forward_GB_per_s": bytes_fwd / (us["forward"] * 1e-6) / 1e9,
+            "note": "two launches per step (flux and node updates), no CUDA graphs; the "
+                    "adjoint includes its checkpointed forward and the recompute"}
+
+
 def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
     """The uneven batch: 24 asteroid instances (levels 1-4, 8-256 shots, own
     eps, shots, f and dt) advanced by one launch per step for all of them
@@ -358,6 +434,45 @@ def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
             "seconds": {"forward_batched": t_fb, "forward_one_by_one": t_fs,
                         "adjoint_batched": t_ab, "adjoint_one_by_one": t_as},
             "note": "adjoint seconds include the checkpointed forward and the recompute"}
+
+
+def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
+    """Shot groups per kind for the kept-history path (the states it streams
+    are larger than L2, unlike the checkpointed path the autotuner times):
+    each of forward (keeping states), J^T w and J v on kept states is timed
+    over the first nt_probe steps with 1, 2 and 4 groups; the fastest stays."""
+    stream = torch.cuda.current_stream()
+    nt_probe = min(nt_probe, len(wav_d))
+    wav = wav_d[:nt_probe].contiguous()
+    W = torch.zeros((w.shots.n_traces, nt_probe), dtype=torch.float32, device=eps_d.device)
+    calls = {
+        "forward": lambda: mg.forward(mesh, eps_d, w.shots, wav, dt, keep_states=True),
+        "adjoint": lambda: mg.jacobian_T_apply(mesh, level, eps_d, w.shots, wav, dt, W,
+                                               ckpt_every=nt_probe, reuse_checkpoints=True),
+        "tangent": lambda: mg.jacobian_apply(mesh, level, eps_d, w.shots, wav, dt, v_d,
+                                             reuse_states=True),
+    }
+    chosen = {}
+    for kind, fn in calls.items():
+        best = None
+        for g in (1, 2, 4):
+            mesh.set_shot_groups(g, kind)
+            fn()                                   # records the graph
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            if best is None or t < best[1] * 0.99:
+                best = (g, t)
+        mesh.set_shot_groups(best[0], kind)
+        chosen[kind] = best[0]
+        if kind == "forward":
+            calls["forward"]()                     # kept states for the next kinds
+    mesh.trim()
+    return chosen
 
 
 def guarded(fn, *a, **k):
@@ -473,6 +588,8 @@ def main():
     mesh.set_tuning(args.chunk, args.lane_vec, args.tile_rows, args.src_tile)
     if args.min_blocks != -1:
         mesh.set_min_blocks(args.min_blocks)
+    if args.dep_launch != -1:
+        mesh.set_dependent_launch(args.dep_launch)
     n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
     eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)
@@ -496,17 +613,38 @@ def main():
         return g
 
     phase_ev = {}
+    # Adjoint strategy: every forward state kept in HBM when it fits (one
+    # segment, no recompute), else checkpoints every CKPT steps and a
+    # recompute per segment.
+    S_pad = max(4, 1 << (S - 1).bit_length()) if S <= 128 else (S + 127) // 128 * 128
+    states_bytes = 4 * n * S_pad * (nt + 2)
+    free_bytes = torch.cuda.mem_get_info(dev)[0]
+    keep_states = not args.checkpoints and free_bytes > states_bytes + (16 << 30)
+    fwd_kw = dict(keep_states=True) if keep_states else dict(ckpt_every=CKPT,
+                                                             keep_checkpoints=True)
+    adj_ckpt = nt if keep_states else CKPT
+    kept_groups = None
+    if keep_states and args.kept_groups:
+        kept_groups = dict(zip(("forward", "adjoint", "tangent"),
+                               (int(x) for x in args.kept_groups.split(","))))
+        for kind, g in kept_groups.items():
+            mesh.set_shot_groups(g, kind)
+    elif keep_states and not args.no_autotune:
+        kept_groups = tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, LEVEL)
+    adjoint_mode = (f"every forward state kept in HBM ({states_bytes / 1e9:.1f} GB): J^T w "
+                    "without recompute, J v reads the forward field" if keep_states else
+                    f"checkpoints every {CKPT} steps, recompute per segment")
 
     def step(record=False):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         evs[0].record(stream)
-        y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, ckpt_every=CKPT, keep_checkpoints=True)
+        y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, **fwd_kw)
         evs[1].record(stream)
-        g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=CKPT,
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=adj_ckpt,
                                 reuse_checkpoints=True)
         allreduce(g)
         evs[2].record(stream)
-        mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d)
+        mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d, reuse_states=keep_states)
         evs[3].record(stream)
         if record:
             phase_ev.setdefault("ev", []).append(evs)
@@ -555,14 +693,15 @@ def main():
     eps_h, wav_h, v_h = pin(w.eps, torch.float64), pin(wav, torch.float64), pin(v, torch.float64)
 
     def step_host():
-        y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, ckpt_every=CKPT, keep_checkpoints=True)
-        g = mg.jacobian_T_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, y, ckpt_every=CKPT,
+        y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, **fwd_kw)
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, y, ckpt_every=adj_ckpt,
                                 reuse_checkpoints=True)
         if ws > 1:
             gt = torch.as_tensor(g, device=dev)
             allreduce(gt)
             g = gt.cpu().numpy()
-        jv = mg.jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h)
+        jv = mg.jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h,
+                               reuse_states=keep_states)
         return y, g, jv
 
     y, g, jv = step_host()
@@ -588,6 +727,9 @@ def main():
     torch.cuda.synchronize()
     single_rate = n * 4 * nt / (e0.elapsed_time(e1) / 1e3)
     fwd_rate = n * S * nt / (statistics.mean(fwd_ms) / 1e3)
+    # the kept forward history (up to ~257 GB) is not needed by the legs below
+    mesh.trim()
+    torch.cuda.empty_cache()
 
     # projected data (Sec. II): the two time inner products of every trace
     # pair and the adjoint weights of the projected Jacobian, on this step's
@@ -614,6 +756,7 @@ def main():
     approx = None if args.no_inversion_leg else guarded(
         approx_jacobian_leg, mg, torch, mesh, w, eps_d, wav_d, dt, y)
     batch = None if args.no_batch_leg or ws > 1 else guarded(batch_leg, mg, torch, dev)
+    pml = None if args.no_pml_leg else guarded(pml_leg, mg, torch, mesh, w, eps_d, wav_d, dt)
     proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
                     "the projected Jacobian products cost one jacobian_apply / "
                     "jacobian_T_apply each (the forward and adjoint phases above)")
@@ -634,7 +777,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": describe(w), "nodes": n, "shots": S, "nt": nt,
                    "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
-                   "tuning": tuning,
+                   "tuning": tuning, "adjoint": adjoint_mode, "kept_groups": kept_groups,
                    "l2": "flushed between timed steps (256 MB write)"},
         "phases_ms": {"forward": statistics.mean(fwd_ms), "adjoint": statistics.mean(adj_ms),
                       "tangent": statistics.mean(tan_ms)},
@@ -644,10 +787,14 @@ def main():
         "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": traffic_for("asteroid_2d", tuning["forward"]),
+                     "traffic": traffic_for("asteroid_2d", dict(
+                         tuning["forward"], groups=(kept_groups or {}).get(
+                             "forward", tuning["forward"].get("groups", 1))), keep_states),
                      "algorithmic_bytes_per_launch": bytes_fwd,
-                     "note": "per-launch time = forward phase / nt (includes launch gaps); "
-                             "state (2 x 32 MB) is L2-resident"},
+                     "note": "per-launch time = forward phase / nt (includes launch gaps); " + (
+                         "each step writes its new 32 MB state into the kept history in HBM, "
+                         "p_l and p_{l-1} are mostly L2-resident" if keep_states else
+                         "state (2 x 32 MB) is L2-resident")},
         "e2e": {"value": units_per_step * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -656,6 +803,7 @@ def main():
         "tv_reconstruction": inversion,
         "approx_jacobian": approx,
         "uneven_batch": batch,
+        "pml": pml,
     }
     if not args.no_hbm_leg:
         out["hbm_workload"] = guarded(hbm_leg, mg, torch, dev)

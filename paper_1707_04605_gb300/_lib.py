@@ -30,6 +30,7 @@ MG_PERSISTENT = 0x08
 MG_ALLOW_CFL = 0x10
 MG_KEEP_CHECKPOINTS = 0x20
 MG_REUSE_CHECKPOINTS = 0x40
+MG_KEEP_STATES = 0x80
 
 
 class mg_shots(C.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "mg_mesh_set_conductivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_mesh_set_min_blocks": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_bulk_copies": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_dependent_launch": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_device_status": (C.c_int, [C.c_void_p]),
     "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,

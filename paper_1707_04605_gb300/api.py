@@ -153,6 +153,12 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_bulk_copies(self.handle, int(bool(on))),
                 "mg_mesh_set_bulk_copies")
 
+    def set_dependent_launch(self, on: bool):
+        """Row kernels launched as programmatic dependents of the previous
+        kernel (mg_mesh_set_dependent_launch); bit-identical results."""
+        L.check(self._lib.mg_mesh_set_dependent_launch(self.handle, int(bool(on))),
+                "mg_mesh_set_dependent_launch")
+
     def device_status(self) -> int:
         """mg_mesh_device_status: 0, or the MG_ERR_* code of a failed bounded wait."""
         return int(self._lib.mg_mesh_device_status(self.handle))
@@ -255,9 +261,12 @@ def _ptr(x):
 
 
 def forward(mesh: Mesh, eps, shots, wavelet, dt, nt=None, *, ckpt_every=0,
-            keep_checkpoints=False, single_source=False, allow_cfl=False,
+            keep_checkpoints=False, keep_states=False, single_source=False, allow_cfl=False,
             stream=None, flags=0):
-    """Traces [n_traces, nt] float32 of mg_forward."""
+    """Traces [n_traces, nt] float32 of mg_forward.  keep_states keeps every
+    state in the handle (MG_KEEP_STATES; (nt + 2) n S_pad floats), so that
+    jacobian_T_apply(..., ckpt_every=nt, reuse_checkpoints=True) runs no
+    recompute."""
     lib = L.load()
     sh = Shots.of(shots)
     nt = int(len(wavelet) if nt is None else nt)
@@ -266,6 +275,8 @@ def forward(mesh: Mesh, eps, shots, wavelet, dt, nt=None, *, ckpt_every=0,
     f = f0 | flags
     if keep_checkpoints:
         f |= L.MG_KEEP_CHECKPOINTS
+    if keep_states:
+        f |= L.MG_KEEP_STATES
     if single_source:
         f |= L.MG_SINGLE_SOURCE
     if allow_cfl:
@@ -277,8 +288,10 @@ def forward(mesh: Mesh, eps, shots, wavelet, dt, nt=None, *, ckpt_every=0,
 
 
 def jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
-                   allow_cfl=False, stream=None, flags=0):
-    """J v: tangent traces [n_traces, nt] float32 for a level-cell direction v."""
+                   reuse_states=False, allow_cfl=False, stream=None, flags=0):
+    """J v: tangent traces [n_traces, nt] float32 for a level-cell direction v.
+    reuse_states reads the forward field kept by forward(..., keep_states=True)
+    (same inputs) instead of recomputing it."""
     lib = L.load()
     sh = Shots.of(shots)
     nt = int(len(wavelet) if nt is None else nt)
@@ -286,6 +299,8 @@ def jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
     (v, pv), = ex
     out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
     f = f0 | flags | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    if reuse_states:
+        f |= L.MG_REUSE_CHECKPOINTS
     rc = lib.mg_jacobian_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt), nt,
                                pv, _ptr(out), st, f)
     L.check(rc, "mg_jacobian_apply")

@@ -98,6 +98,7 @@ struct mg_mesh {
   int64_t ev_gen = 0;                     // bumped whenever the event lists change
   // checkpoints of the last mg_forward with MG_KEEP_CHECKPOINTS
   bool ck_valid = false;
+  bool seg_full = false;                  // seg holds p_{-1}..p_nt of that forward (MG_KEEP_STATES)
   int ck_every = 0, ck_nt = 0, ck_S_pad = 0, ck_nshots = 0;
   double ck_dt = 0.0;
   int64_t ck_ev_gen = -1;
@@ -116,6 +117,7 @@ struct mg_mesh {
     int min_blocks = 0;   // forward row kernel: 0, or 5 resident CTAs per SM
     int bulk = 0;         // forward: neighbour rows staged by bulk async copies
   } tune[3];
+  int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf errbuf;                             // device status word of bounded waits
   struct TileTables {
     Buf ell_off, ell_idx, ell_val, sinfo, halo_off, halo_cnt, halo;
@@ -404,6 +406,7 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   mg::StepArgs b = a;
   b.batch = M->tune[0].batch;
   b.min_blocks = M->tune[0].min_blocks;
+  b.pdl = M->dep_launch;
   if (M->tune[0].bulk) {
     int* err = err_word(M);
     if (!err) return MG_ERR_OOM;
@@ -417,6 +420,7 @@ int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st)
   if (T.n_tiles) return mg::launch_tangent_tiled(a, T, st);
   mg::TangentArgs b = a;
   b.f.batch = M->tune[1].batch;
+  b.f.pdl = M->dep_launch;
   return mg::launch_tangent(b, S_pad, st);
 }
 
@@ -425,6 +429,7 @@ int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st)
   if (T.n_tiles) return mg::launch_adjoint_tiled(a, T, st);
   mg::AdjointArgs b = a;
   b.batch = M->tune[2].batch;
+  b.pdl = M->dep_launch;
   return mg::launch_adjoint(b, S_pad, st);
 }
 
@@ -557,6 +562,50 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
     MG_TRY(do_step(M, a, pp.S_pad, st));
     M->launches += 1;
     std::swap(p, pm);
+  }
+  return MG_OK;
+}
+
+// Forward that keeps every state: slot j of `seg` holds p_{j-1}
+// (j = 0..nt+1), the layout of one adjoint segment covering the whole run.
+int run_forward_states(mg_mesh* M, const Prep& pp, int nt, float* traces, float* seg,
+                       cudaStream_t st, int flags) {
+  const size_t state = (size_t)M->hm.n * pp.S_pad;
+  MG_CU(cudaMemsetAsync(seg, 0, 2 * state * sizeof(float), st));
+  mg::StepArgs a = step_args(M, pp, pp.S_pad, nt);
+  a.traces = traces;
+  const int W = group_cols(M, 0, pp.S_pad), NG = pp.S_pad / W;
+  if (graphs_on(M, flags) && nt % 2 == 0) {
+    MG_TRY(ensure(M->step_base, 16));
+    int32_t* base = P<int32_t>(M->step_base);
+    MG_TRY(mg::launch_set_int(base, 0, st));
+    M->launches += 1;
+    const std::string key = key_of("fwdst", {seg, traces, a.wavelet, a.coef, a.ev.src_ptr, base},
+                                   {pp.S_pad, pp.S, pp.R, nt, (int64_t)M->hm.n, W});
+    return run_graph(M, key, NG * nt, st, [&](cudaStream_t cs) {
+      mg::StepArgs b = a;
+      b.step_base = base;
+      b.cols = W;
+      for (int g = 0; g < NG; ++g) {   // each shot group runs the whole history
+        b.col0 = g * W;
+        for (int l = 0; l < nt; ++l) {
+          b.p = seg + (size_t)(l + 1) * state;
+          b.pm = seg + (size_t)l * state;
+          b.pout = seg + (size_t)(l + 2) * state;
+          b.step = l;
+          MG_TRY(do_step(M, b, pp.S_pad, cs));
+        }
+      }
+      return MG_OK;
+    });
+  }
+  for (int l = 0; l < nt; ++l) {
+    a.p = seg + (size_t)(l + 1) * state;
+    a.pm = seg + (size_t)l * state;
+    a.pout = seg + (size_t)(l + 2) * state;
+    a.step = l;
+    MG_TRY(do_step(M, a, pp.S_pad, st));
+    M->launches += 1;
   }
   return MG_OK;
 }
@@ -698,6 +747,7 @@ int mg_mesh_trim(mg_mesh* M) {
   }
   M->ev_valid = false;
   M->ck_valid = false;
+  M->seg_full = false;
   return MG_OK;
 }
 
@@ -707,6 +757,7 @@ int mg_mesh_set_conductivity(mg_mesh* M, const double* sigma, void* stream, int 
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
   M->ck_valid = false;  // checkpoints of an earlier forward no longer apply
+  M->seg_full = false;
   if (!sigma) {
     M->has_sigma = false;
     return MG_OK;
@@ -793,6 +844,13 @@ int mg_mesh_set_shot_groups(mg_mesh* M, int kind, int groups) {
   drop_graphs(M);
   for (int k = 0; k < 3; ++k)
     if (kind == -1 || kind == k) M->tune[k].groups = groups;
+  return MG_OK;
+}
+
+int mg_mesh_set_dependent_launch(mg_mesh* M, int on) {
+  if (!M || (on != 0 && on != 1)) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->dep_launch = on;
   return MG_OK;
 }
 
@@ -887,6 +945,8 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
   if (!M || !traces) return MG_ERR_ARG;
   if ((flags & MG_KEEP_CHECKPOINTS) && (ckpt_every < 1 || (flags & MG_SINGLE_SOURCE)))
     return MG_ERR_ARG;
+  if ((flags & MG_KEEP_STATES) && (flags & (MG_KEEP_CHECKPOINTS | MG_SINGLE_SOURCE)))
+    return MG_ERR_ARG;
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -897,9 +957,24 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
   float* tr = P<float>(M->tr);
   if (flags & MG_SINGLE_SOURCE) {
     MG_TRY(run_forward_single(M, pp, nt, tr, st));
+  } else if (flags & MG_KEEP_STATES) {
+    M->ck_valid = false;
+    M->seg_full = false;
+    const size_t state = (size_t)M->hm.n * pp.S_pad;
+    MG_TRY(ensure(M->seg, (size_t)(nt + 2) * state * sizeof(float)));
+    MG_TRY(run_forward_states(M, pp, nt, tr, P<float>(M->seg), st, flags));
+    M->ck_valid = true;
+    M->seg_full = true;
+    M->ck_every = nt;
+    M->ck_nt = nt;
+    M->ck_S_pad = pp.S_pad;
+    M->ck_nshots = pp.S;
+    M->ck_dt = dt;
+    M->ck_ev_gen = M->ev_gen;
   } else {
     float* ck = nullptr;
     M->ck_valid = false;
+    M->seg_full = false;
     if (flags & MG_KEEP_CHECKPOINTS) {
       const int nck = (nt + ckpt_every - 1) / ckpt_every;
       MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * M->hm.n * pp.S_pad * sizeof(float)));
@@ -957,6 +1032,56 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
   a.f = step_args(M, pp, pp.S_pad, nt);
   a.tcoef = P<const float2>(M->tcoef);
   a.dtraces = tr;
+  if (flags & MG_REUSE_CHECKPOINTS) {
+    // the states kept by the last mg_forward (MG_KEEP_STATES) are read: slot
+    // j of the segment buffer holds p_{j-1}; only dp is advanced
+    const bool kept = M->ck_valid && M->seg_full && M->ck_every == nt && M->ck_nt == nt &&
+                      M->ck_S_pad == pp.S_pad && M->ck_nshots == pp.S && M->ck_dt == dt &&
+                      M->ck_ev_gen == M->ev_gen;
+    if (!kept) return MG_ERR_ARG;
+    float* seg = P<float>(M->seg);
+    a.f.batch = M->tune[1].batch;
+    a.f.pdl = M->dep_launch;
+    const int W = group_cols(M, 1, pp.S_pad), NG = pp.S_pad / W;
+    int32_t* base = nullptr;
+    const bool graph = graphs_on(M, flags);
+    if (graph) {
+      MG_TRY(ensure(M->step_base, 16));
+      base = P<int32_t>(M->step_base);
+      MG_TRY(mg::launch_set_int(base, 0, st));
+      M->launches += 1;
+    }
+    auto record = [&](cudaStream_t cs) -> int {
+      mg::TangentArgs b = a;
+      b.f.step_base = base;
+      b.f.cols = W;
+      for (int g = 0; g < NG; ++g) {   // each shot group runs the whole history
+        b.f.col0 = g * W;
+        float *u = q, *z = qm;
+        for (int j = 0; j < nt; ++j) {
+          b.f.p = seg + (size_t)(j + 1) * state;
+          b.f.pm = seg + (size_t)j * state;
+          b.pk1 = seg + (size_t)(j + 2) * state;
+          b.q = u;
+          b.qm = z;
+          b.f.step = j;
+          MG_TRY(mg::launch_tangent_kept(b, pp.S_pad, cs));
+          std::swap(u, z);
+        }
+      }
+      return MG_OK;
+    };
+    if (graph) {
+      const std::string key = key_of("tankept", {seg, q, qm, tr, a.f.coef, a.tcoef,
+                                                 a.f.ev.rec_ptr, base},
+                                     {pp.S_pad, pp.S, pp.R, nt, n, W});
+      MG_TRY(run_graph(M, key, NG * nt, st, record));
+    } else {
+      MG_TRY(record(st));
+      M->launches += (int64_t)NG * nt;
+    }
+    return deliver(M->tr, jv, tbytes, flags, st);
+  }
   int l = 0;
   const int C = M->chunk;
   if (graphs_on(M, flags) && nt >= C) {
@@ -1033,6 +1158,9 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
                      M->ck_nt == nt && M->ck_S_pad == pp.S_pad && M->ck_nshots == pp.S &&
                      M->ck_dt == dt && M->ck_ev_gen == M->ev_gen;
   if ((flags & MG_REUSE_CHECKPOINTS) && !reuse) return MG_ERR_ARG;
+  // every state of the forward kept (MG_KEEP_STATES): one segment, no recompute
+  const bool states = reuse && M->seg_full && ckpt_every == nt;
+  if (!states) M->seg_full = false;   // the segment buffer is rewritten below
   const int nck = (nt + ckpt_every - 1) / ckpt_every;
   if (!reuse) {
     M->ck_valid = false;
@@ -1088,9 +1216,11 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   for (int a = nck - 1; a >= 0; --a) {
     const int l0 = a * ckpt_every;
     const int l1 = std::min(nt, l0 + ckpt_every);
-    MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state, seg + state, (int64_t)state, st));
-    MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state + state, seg, (int64_t)state, st));
-    M->launches += 2;
+    if (!states) {
+      MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state, seg + state, (int64_t)state, st));
+      MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state + state, seg, (int64_t)state, st));
+      M->launches += 2;
+    }
     if (use_graph && l1 - l0 == ckpt_every) {
       // whole segment: recompute p_{l0+1..l1}, then reverse steps k = l1..l0+1,
       // each as one graph; indices relative to *base = l0
@@ -1098,7 +1228,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       M->launches += 1;
       const std::string kr = key_of("rec", {seg, fa.wavelet, fa.coef, fa.ev.src_ptr, base},
                                     {pp.S_pad, pp.S, pp.R, nt, ckpt_every, n, Wf});
-      MG_TRY(run_graph(M, kr, NGf * ckpt_every, st, [&](cudaStream_t cs) {
+      if (!states) MG_TRY(run_graph(M, kr, NGf * ckpt_every, st, [&](cudaStream_t cs) {
         mg::StepArgs b = fa;
         b.step_base = base;
         b.cols = Wf;
@@ -1137,7 +1267,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       }));
       continue;   // even segment length: mu / mu1 are back in place
     }
-    for (int l = l0; l < l1; ++l) {
+    for (int l = l0; l < l1 && !states; ++l) {
       const int j = l - l0 + 1;  // slot of p_l
       fa.p = seg + (size_t)j * state;
       fa.pm = seg + (size_t)(j - 1) * state;
@@ -1373,6 +1503,7 @@ int prepare_instance(mg_mesh* M, const double* eps, const mg_shots* shots, const
     v->seg = P<float>(M->seg);
     v->G = P<float>(M->G);
     M->ck_valid = false;
+    M->seg_full = false;
   }
   if (w) {
     const size_t wbytes = (size_t)pp.R * nt * sizeof(float);

@@ -43,6 +43,7 @@ struct StepArgs {
   int32_t min_blocks = 0;   // row kernel: 0, or 5 resident CTAs per SM requested (register cap)
   int32_t col0 = 0;         // first shot column advanced (multiple of the launch's shot tile)
   int32_t cols = 0;         // shot columns advanced, [col0, col0 + cols); 0 = all ld
+  int32_t pdl = 0;          // row kernels: launch dependent on the previous kernel
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -52,6 +53,8 @@ struct TangentArgs {
   float* qm;                // dp_{l-1} in, dp_{l+1} out
   const float2* tcoef;      // {gamma dm/dt^2, gamma dD/(2 dt)} per row
   float* dtraces;           // [n_traces][nt]
+  const float* pk1 = nullptr;  // kept p_{l+1}: f.p, f.pm, pk1 are kept forward states
+                               // (read, not recomputed; f.pout unused)
 };
 
 // Adjoint (reverse) step k: mu_{k+1} buffer <- mu_{k-1}, and the per-row
@@ -72,6 +75,7 @@ struct AdjointArgs {
   int32_t batch;
   int32_t col0 = 0;         // shot columns [col0, col0 + cols) as in StepArgs
   int32_t cols = 0;
+  int32_t pdl = 0;          // as in StepArgs
   float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;
@@ -102,6 +106,8 @@ size_t tiled_smem_bytes(const DevTiles& T, int kind);
 
 int launch_step_tiled(const StepArgs& a, const DevTiles& T, cudaStream_t st);
 int launch_tangent_tiled(const TangentArgs& a, const DevTiles& T, cudaStream_t st);
+// Tangent step on kept forward states (row kernel; a.pk1 set).
+int launch_tangent_kept(const TangentArgs& a, int S_pad, cudaStream_t st);
 int launch_adjoint_tiled(const AdjointArgs& a, const DevTiles& T, cudaStream_t st);
 
 // Source tiles (grid.y) of the row kernels for `cols` shot columns per

@@ -21,6 +21,16 @@ namespace {
 
 using namespace dev;
 
+// Programmatic dependent launch: wait until the kernel this launch depends
+// on has completed and its writes are visible (a no-op for a launch that was
+// not made dependent), then let the next dependent launch start.  Everything
+// a kernel does before this call reads only the stiffness slice table, which
+// no step writes.
+__device__ __forceinline__ void grid_dep_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 struct Row {
   const int2* e;  // entry 0 of the row (stride kSliceH)
   int w;          // entries of the row's slice, diagonal first
@@ -164,6 +174,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   const int tile0 = a.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
   const Row r = row_of(a.K, row);
+  grid_dep_sync();
   const float4 c = __ldg(a.coef + row);
   const size_t ro = (size_t)row * a.ld + base;
   float4 old[NV], self[NV], acc[NV];
@@ -207,6 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
   const int base = tile0 + 4 * lr;
   const int ld = a.f.ld;
   const Row r = row_of(a.f.K, row);
+  grid_dep_sync();
   const float4 c = __ldg(a.f.coef + row);
   const float2 tc = __ldg(a.tcoef + row);
   const size_t ro = (size_t)row * ld + base;
@@ -245,6 +257,50 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
   }
 }
 
+// Tangent step when the forward states are kept: p_{l-1}, p_l, p_{l+1} of
+// the row are read (the forward field is not recomputed, so only dp is
+// gathered); the dp update and its correction are those of k_tangent_rows,
+// with the same bits.
+template <int LPR, int NV>
+__global__ void __launch_bounds__(kThreads) k_tangent_kept_rows(TangentArgs a) {
+  constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
+  const unsigned mask = __ballot_sync(0xffffffffu, row < a.f.K.n);
+  if (row >= a.f.K.n) return;
+  const int lr = lane % LPR;
+  const int tile0 = a.f.col0 + blockIdx.y * TW;
+  const int base = tile0 + 4 * lr;
+  const int ld = a.f.ld;
+  const Row r = row_of(a.f.K, row);
+  grid_dep_sync();
+  const float4 c = __ldg(a.f.coef + row);
+  const float2 tc = __ldg(a.tcoef + row);
+  const size_t ro = (size_t)row * ld + base;
+  float4 pn[NV], ps[NV], pold[NV], qold[NV], qs[NV], qacc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    pn[j] = __ldg(reinterpret_cast<const float4*>(a.pk1 + ro + 4 * LPR * j));
+    ps[j] = __ldg(reinterpret_cast<const float4*>(a.f.p + ro + 4 * LPR * j));
+    pold[j] = __ldg(reinterpret_cast<const float4*>(a.f.pm + ro + 4 * LPR * j));
+    qold[j] = *reinterpret_cast<const float4*>(a.qm + ro + 4 * LPR * j);
+  }
+  row_sum<LPR, NV>(r, a.q + base, row, lr, mask, ld, qs, qacc);
+  float4 qn[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    qn[j] = tangent_fix(leap(c, qs[j], qold[j], qacc[j]), pn[j], ps[j], pold[j], tc);
+    st4(a.qm + ro + 4 * LPR * j, qn[j]);
+  }
+  const int l = a.f.step + (a.f.step_base ? *a.f.step_base : 0);
+  const int r0 = __ldg(a.f.ev.rec_ptr + row), r1 = __ldg(a.f.ev.rec_ptr + row + 1);
+  for (int q = r0; q < r1; ++q) {
+    int d;
+    const int j = owner<LPR, NV>(__ldg(a.f.ev.rec_shot + q), tile0, lr, d);
+    if (j >= 0) a.dtraces[(size_t)__ldg(a.f.ev.rec_trace + q) * a.f.nt + l] = get_from<NV>(qn, j, d);
+  }
+}
+
 template <int LPR, int NV>
 __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
@@ -258,6 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
   float t1 = 0.0f, t2 = 0.0f;
   if (valid) {
     const Row r = row_of(a.K, row);
+    grid_dep_sync();
     const float4 c = __ldg(a.coef + row);
     const size_t ro = (size_t)row * a.ld + base;
     float4 old[NV], pk[NV], self[NV], acc[NV];
@@ -324,49 +381,66 @@ bool range_ok(const Shape& sh, int col0, int cols, int ld) {
          cols % tw == 0;
 }
 
-#define MG_ROWS_SWITCH(KERN, ARGS)                                                         \
+// Launch of a row kernel, dependent on the previous kernel of the stream
+// (programmatic stream serialisation) when `pdl` is set.
+template <class A>
+cudaError_t launch_ex(void (*kern)(A), dim3 grid, int pdl, cudaStream_t st, const A& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+#define MG_ROWS_SWITCH(KERN, PDL, ARGS)                                                         \
   switch (sh.lpr * 8 + sh.nv) {                                                            \
-    case 32 * 8 + 1: KERN<32, 1><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 32 * 8 + 2: KERN<32, 2><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 32 * 8 + 4: KERN<32, 4><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 16 * 8 + 1: KERN<16, 1><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 16 * 8 + 2: KERN<16, 2><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 16 * 8 + 4: KERN<16, 4><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 8 * 8 + 1: KERN<8, 1><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 8 * 8 + 2: KERN<8, 2><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 8 * 8 + 4: KERN<8, 4><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 4 * 8 + 1: KERN<4, 1><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 4 * 8 + 2: KERN<4, 2><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 4 * 8 + 4: KERN<4, 4><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 2 * 8 + 1: KERN<2, 1><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 2 * 8 + 2: KERN<2, 2><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 2 * 8 + 4: KERN<2, 4><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 1 * 8 + 1: KERN<1, 1><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 1 * 8 + 2: KERN<1, 2><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 1 * 8 + 4: KERN<1, 4><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 32 * 8 + 1: err = launch_ex(KERN<32, 1>, sh.grid, PDL, st, ARGS); break; \
+    case 32 * 8 + 2: err = launch_ex(KERN<32, 2>, sh.grid, PDL, st, ARGS); break; \
+    case 32 * 8 + 4: err = launch_ex(KERN<32, 4>, sh.grid, PDL, st, ARGS); break; \
+    case 16 * 8 + 1: err = launch_ex(KERN<16, 1>, sh.grid, PDL, st, ARGS); break; \
+    case 16 * 8 + 2: err = launch_ex(KERN<16, 2>, sh.grid, PDL, st, ARGS); break; \
+    case 16 * 8 + 4: err = launch_ex(KERN<16, 4>, sh.grid, PDL, st, ARGS); break; \
+    case 8 * 8 + 1: err = launch_ex(KERN<8, 1>, sh.grid, PDL, st, ARGS); break; \
+    case 8 * 8 + 2: err = launch_ex(KERN<8, 2>, sh.grid, PDL, st, ARGS); break; \
+    case 8 * 8 + 4: err = launch_ex(KERN<8, 4>, sh.grid, PDL, st, ARGS); break; \
+    case 4 * 8 + 1: err = launch_ex(KERN<4, 1>, sh.grid, PDL, st, ARGS); break; \
+    case 4 * 8 + 2: err = launch_ex(KERN<4, 2>, sh.grid, PDL, st, ARGS); break; \
+    case 4 * 8 + 4: err = launch_ex(KERN<4, 4>, sh.grid, PDL, st, ARGS); break; \
+    case 2 * 8 + 1: err = launch_ex(KERN<2, 1>, sh.grid, PDL, st, ARGS); break; \
+    case 2 * 8 + 2: err = launch_ex(KERN<2, 2>, sh.grid, PDL, st, ARGS); break; \
+    case 2 * 8 + 4: err = launch_ex(KERN<2, 4>, sh.grid, PDL, st, ARGS); break; \
+    case 1 * 8 + 1: err = launch_ex(KERN<1, 1>, sh.grid, PDL, st, ARGS); break; \
+    case 1 * 8 + 2: err = launch_ex(KERN<1, 2>, sh.grid, PDL, st, ARGS); break; \
+    case 1 * 8 + 4: err = launch_ex(KERN<1, 4>, sh.grid, PDL, st, ARGS); break; \
     default: return MG_ERR_ARG;                                                            \
   }
 
-#define MG_ROWS_SWITCH_M(KERN, M, ARGS)                                                         \
+#define MG_ROWS_SWITCH_M(KERN, M, PDL, ARGS)                                                         \
   switch (sh.lpr * 8 + sh.nv) {                                                            \
-    case 32 * 8 + 1: KERN<32, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 32 * 8 + 2: KERN<32, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 32 * 8 + 4: KERN<32, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 16 * 8 + 1: KERN<16, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 16 * 8 + 2: KERN<16, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 16 * 8 + 4: KERN<16, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;               \
-    case 8 * 8 + 1: KERN<8, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 8 * 8 + 2: KERN<8, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 8 * 8 + 4: KERN<8, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 4 * 8 + 1: KERN<4, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 4 * 8 + 2: KERN<4, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 4 * 8 + 4: KERN<4, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 2 * 8 + 1: KERN<2, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 2 * 8 + 2: KERN<2, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 2 * 8 + 4: KERN<2, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 1 * 8 + 1: KERN<1, 1, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 1 * 8 + 2: KERN<1, 2, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
-    case 1 * 8 + 4: KERN<1, 4, M><<<sh.grid, kThreads, 0, st>>>(ARGS); break;                 \
+    case 32 * 8 + 1: err = launch_ex(KERN<32, 1, M>, sh.grid, PDL, st, ARGS); break; \
+    case 32 * 8 + 2: err = launch_ex(KERN<32, 2, M>, sh.grid, PDL, st, ARGS); break; \
+    case 32 * 8 + 4: err = launch_ex(KERN<32, 4, M>, sh.grid, PDL, st, ARGS); break; \
+    case 16 * 8 + 1: err = launch_ex(KERN<16, 1, M>, sh.grid, PDL, st, ARGS); break; \
+    case 16 * 8 + 2: err = launch_ex(KERN<16, 2, M>, sh.grid, PDL, st, ARGS); break; \
+    case 16 * 8 + 4: err = launch_ex(KERN<16, 4, M>, sh.grid, PDL, st, ARGS); break; \
+    case 8 * 8 + 1: err = launch_ex(KERN<8, 1, M>, sh.grid, PDL, st, ARGS); break; \
+    case 8 * 8 + 2: err = launch_ex(KERN<8, 2, M>, sh.grid, PDL, st, ARGS); break; \
+    case 8 * 8 + 4: err = launch_ex(KERN<8, 4, M>, sh.grid, PDL, st, ARGS); break; \
+    case 4 * 8 + 1: err = launch_ex(KERN<4, 1, M>, sh.grid, PDL, st, ARGS); break; \
+    case 4 * 8 + 2: err = launch_ex(KERN<4, 2, M>, sh.grid, PDL, st, ARGS); break; \
+    case 4 * 8 + 4: err = launch_ex(KERN<4, 4, M>, sh.grid, PDL, st, ARGS); break; \
+    case 2 * 8 + 1: err = launch_ex(KERN<2, 1, M>, sh.grid, PDL, st, ARGS); break; \
+    case 2 * 8 + 2: err = launch_ex(KERN<2, 2, M>, sh.grid, PDL, st, ARGS); break; \
+    case 2 * 8 + 4: err = launch_ex(KERN<2, 4, M>, sh.grid, PDL, st, ARGS); break; \
+    case 1 * 8 + 1: err = launch_ex(KERN<1, 1, M>, sh.grid, PDL, st, ARGS); break; \
+    case 1 * 8 + 2: err = launch_ex(KERN<1, 2, M>, sh.grid, PDL, st, ARGS); break; \
+    case 1 * 8 + 4: err = launch_ex(KERN<1, 4, M>, sh.grid, PDL, st, ARGS); break; \
     default: return MG_ERR_ARG;                                                            \
   }
 
@@ -378,13 +452,15 @@ int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
   const int cols = a.cols ? a.cols : S_pad;
   const Shape sh = shape_of(a.K.n, cols, a.batch);
   if (!range_ok(sh, a.col0, cols, a.ld)) return MG_ERR_ARG;
+  cudaError_t err = cudaSuccess;
   if (a.min_blocks == 5) {
-    MG_ROWS_SWITCH_M(k_step_rows, 5, a)
+    MG_ROWS_SWITCH_M(k_step_rows, 5, a.pdl, a)
   } else if (a.min_blocks == 0) {
-    MG_ROWS_SWITCH_M(k_step_rows, 1, a)
+    MG_ROWS_SWITCH_M(k_step_rows, 1, a.pdl, a)
   } else {
     return MG_ERR_ARG;
   }
+  if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();
 }
 
@@ -392,7 +468,19 @@ int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st) {
   const int cols = a.f.cols ? a.f.cols : S_pad;
   const Shape sh = shape_of(a.f.K.n, cols, a.f.batch);
   if (!range_ok(sh, a.f.col0, cols, a.f.ld)) return MG_ERR_ARG;
-  MG_ROWS_SWITCH(k_tangent_rows, a)
+  cudaError_t err = cudaSuccess;
+  MG_ROWS_SWITCH(k_tangent_rows, a.f.pdl, a)
+  if (err != cudaSuccess) return MG_ERR_CUDA;
+  return check_launch();
+}
+
+int launch_tangent_kept(const TangentArgs& a, int S_pad, cudaStream_t st) {
+  const int cols = a.f.cols ? a.f.cols : S_pad;
+  const Shape sh = shape_of(a.f.K.n, cols, a.f.batch);
+  if (!range_ok(sh, a.f.col0, cols, a.f.ld) || !a.pk1) return MG_ERR_ARG;
+  cudaError_t err = cudaSuccess;
+  MG_ROWS_SWITCH(k_tangent_kept_rows, a.f.pdl, a)
+  if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();
 }
 
@@ -400,7 +488,9 @@ int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st) {
   const int cols = a.cols ? a.cols : S_pad;
   const Shape sh = shape_of(a.K.n, cols, a.batch);
   if (!range_ok(sh, a.col0, cols, a.ld)) return MG_ERR_ARG;
-  MG_ROWS_SWITCH(k_adjoint_rows, a)
+  cudaError_t err = cudaSuccess;
+  MG_ROWS_SWITCH(k_adjoint_rows, a.pdl, a)
+  if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();
 }
 #undef MG_ROWS_SWITCH

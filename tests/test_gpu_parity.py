@@ -221,6 +221,53 @@ def test_adjoint_checkpoint_spacing_and_reuse(mg):
     assert np.array_equal(gh, g64.cpu().numpy())
 
 
+@pytest.mark.parametrize("nt,chunk", [(300, 128), (301, 128), (300, 0)])
+def test_kept_states_give_the_checkpointed_gradient(mg, nt, chunk):
+    """A forward that keeps every state lets J^T w skip its recompute and J v
+    read the forward field: same traces, gradient and tangent bits as the
+    checkpointed and recomputing paths (even and odd nt, graphs and plain
+    launches, one and two shot groups); the kept states stop applying after
+    a forward that does not keep them."""
+    w = configs.asteroid_2d(n_refine=1, S=12, nt=nt)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(chunk, -1, -1, -1)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    eps = _dev(w.eps)
+    W = _dev(np.random.default_rng(2).standard_normal((w.shots.n_traces, nt)), torch.float32)
+    y_ref = mg.forward(mesh, eps, w.shots, s, dt)
+    g_ref = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+    y = mg.forward(mesh, eps, w.shots, s, dt, keep_states=True)
+    assert torch.equal(y, y_ref)
+    n0 = mesh.launch_count()
+    g = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=nt,
+                            reuse_checkpoints=True)
+    assert torch.equal(g, g_ref)
+    assert mesh.launch_count() - n0 < nt + 64          # reverse steps only, no recompute
+    # reused twice: the kept states are still there
+    g2 = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=nt,
+                             reuse_checkpoints=True)
+    assert torch.equal(g2, g_ref)
+    # the tangent reads the kept forward field: same bits as recomputing it
+    v = _dev(np.random.default_rng(3).standard_normal(w.mesh.n_cells[1]))
+    jv_ref = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
+    for groups in (1, 2):
+        mesh.set_shot_groups(groups)
+        jv = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, reuse_states=True)
+        assert torch.equal(jv, jv_ref)
+    mesh.set_shot_groups(1)
+    # a plain forward invalidates them; the checkpointed reuse still works
+    mg.forward(mesh, eps, w.shots, s, dt, ckpt_every=64, keep_checkpoints=True)
+    with pytest.raises(RuntimeError):
+        mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=nt,
+                            reuse_checkpoints=True)
+    g3 = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64,
+                             reuse_checkpoints=True)
+    assert torch.equal(g3, g_ref)
+    with pytest.raises(RuntimeError):
+        mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, reuse_states=True)
+
+
 @pytest.mark.parametrize("chunk,batch,tile_rows,src_tile", [
     (0, 1, 0, 32), (0, 2, 0, 32), (128, 4, 0, 32), (64, 2, 256, 16), (128, 1, 128, 64),
     (128, 2, 64, 8), (0, 4, 512, 4), (128, 2, 128, 32), (0, 2, 64, 16)])
@@ -322,6 +369,39 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     out = run()
     assert torch.equal(ref[0], out[0])
     assert torch.equal(ref[1], out[1])
+
+
+@pytest.mark.parametrize("S,batch,groups,chunk", [(100, 2, 1, 128), (100, 1, 2, 128),
+                                                   (37, 4, 1, 0), (300, 2, 1, 64)])
+def test_dependent_launch_gives_identical_results(mg, S, batch, groups, chunk):
+    """Row kernels launched as programmatic dependents of the previous step
+    (the default; inside CUDA graphs and in plain stream order): the forward,
+    tangent and adjoint give the same bits as plain launches."""
+    w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(chunk, batch, 0, 32)
+    mesh.set_shot_groups(groups)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    rng = np.random.default_rng(6)
+    W = _dev(rng.standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    v = _dev(rng.standard_normal(w.mesh.n_cells[1]))
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    mesh.set_dependent_launch(False)
+    ref = run()
+    mesh.set_dependent_launch(True)
+    out = run()
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+    again = run()                                 # cached graphs replayed
+    for a, b in zip(ref, again):
+        assert torch.equal(a, b)
 
 
 @pytest.mark.parametrize("S,batch", [(100, 1), (100, 2), (6, 1), (300, 2), (64, 2)])
