@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--kept-groups", default="",
                     help="shot groups forward,adjoint,tangent of the kept-history path "
                          "(instead of timing 1, 2, 4)")
+    ap.add_argument("--cache-hints", type=int, default=-1,
+                    help="kept history: L2 evict-first on the last reads (0 or 1)")
     ap.add_argument("--hbm-only", action="store_true",
                     help="only the 3D ellipsoid forward measurement")
     return ap.parse_args()
@@ -147,19 +149,21 @@ def clocks_stop(proc, gpu_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per launch of the forward step kernel, from one
-# ncu capture of the same workload and launch shape (summaries in profiles/),
+# DRAM bytes (read + write) per leapfrog step of the roofline's kernel, from
+# one ncu capture of the same workload and launch shape (summaries in profiles/),
 # with the SHA-1 of the kernel sources at capture time: a figure is reported
 # only while those sources are unchanged, else the roofline's traffic is null.
 KERNEL_SOURCES = ["kernels_rows.cu", "device_util.cuh", "kernels.cuh"]
 TRAFFIC = {
-    # (workload, kept history, batch, tile_rows, groups, min_blocks, bulk): (bytes, sha1)
-    # k_step_rows<16,2,1> writing every state into the kept history,
-    # --cache-control none, mean of launches 3-5: 31.6 MB read + 31.1 MB
-    # written (the new state goes to HBM; part of p_l / p_{l-1} is re-read)
-    ("asteroid_2d", True, 2, 0, 1, 0, 0): (62.7e6, "deeea868f36dd3a57cc2713e08ffc4f98ffaa5a0"),
-    # k_step_rows<8,2,5>, two launches: 1228.2 MB read + 437.8 MB written
-    ("ellipsoid_3d", False, 2, 0, 1, 5, 0): (1.666e9, "deeea868f36dd3a57cc2713e08ffc4f98ffaa5a0"),
+    # (workload, kept history, batch, tile_rows, groups, min_blocks, bulk):
+    # (bytes per leapfrog step, all shot groups; sha1 of the kernel sources)
+    # k_tangent_rows<32,1> fused forward + tangent writing the kept history,
+    # one group, --cache-control none, launches 2-4: 132.2 MB read + 64.4 MB
+    # written, the algorithmic 197.4 MB
+    ("asteroid_2d_fused", True, 1, 0, 1, 0, 0): (196.6e6,
+                                                 "58797ac3fca23f88179321aa29f05fe8e8504f0c"),
+    # k_step_rows<8,2,5>, two launches: 1228.5 MB read + 438.1 MB written
+    ("ellipsoid_3d", False, 2, 0, 1, 5, 0): (1.667e9, "58797ac3fca23f88179321aa29f05fe8e8504f0c"),
 }
 
 
@@ -439,18 +443,19 @@ def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
 def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
     """Shot groups per kind for the kept-history path (the states it streams
     are larger than L2, unlike the checkpointed path the autotuner times):
-    each of forward (keeping states), J^T w and J v on kept states is timed
-    over the first nt_probe steps with 1, 2 and 4 groups; the fastest stays."""
+    the fused forward + tangent pass (keeping the history) and J^T w on it
+    are timed over the first nt_probe steps with 1, 2 and 4 groups; the
+    fastest stays."""
     stream = torch.cuda.current_stream()
     nt_probe = min(nt_probe, len(wav_d))
     wav = wav_d[:nt_probe].contiguous()
     W = torch.zeros((w.shots.n_traces, nt_probe), dtype=torch.float32, device=eps_d.device)
     calls = {
-        "forward": lambda: mg.forward(mesh, eps_d, w.shots, wav, dt, keep_states=True),
+        # the fused forward + tangent pass (tangent kind) keeps the history
+        "tangent": lambda: mg.forward_jacobian_apply(mesh, level, eps_d, w.shots, wav, dt, v_d,
+                                                     keep_states=True),
         "adjoint": lambda: mg.jacobian_T_apply(mesh, level, eps_d, w.shots, wav, dt, W,
                                                ckpt_every=nt_probe, reuse_checkpoints=True),
-        "tangent": lambda: mg.jacobian_apply(mesh, level, eps_d, w.shots, wav, dt, v_d,
-                                             reuse_states=True),
     }
     chosen = {}
     for kind, fn in calls.items():
@@ -469,8 +474,8 @@ def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
                 best = (g, t)
         mesh.set_shot_groups(best[0], kind)
         chosen[kind] = best[0]
-        if kind == "forward":
-            calls["forward"]()                     # kept states for the next kinds
+        if kind == "tangent":
+            calls["tangent"]()                     # kept history for the reverse steps
     mesh.trim()
     return chosen
 
@@ -590,6 +595,8 @@ def main():
         mesh.set_min_blocks(args.min_blocks)
     if args.dep_launch != -1:
         mesh.set_dependent_launch(args.dep_launch)
+    if args.cache_hints != -1:
+        mesh.set_cache_hints(args.cache_hints)
     n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
     eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)
@@ -638,14 +645,26 @@ def main():
     def step(record=False):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         evs[0].record(stream)
-        y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, **fwd_kw)
-        evs[1].record(stream)
-        g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=adj_ckpt,
-                                reuse_checkpoints=True)
-        allreduce(g)
-        evs[2].record(stream)
-        mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d, reuse_states=keep_states)
-        evs[3].record(stream)
+        if keep_states:
+            # forward traces and J v in one pass that keeps the history, then
+            # J^T w on it (no forward left to run)
+            y, _ = mg.forward_jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d,
+                                             keep_states=True)
+            evs[1].record(stream)
+            evs[2].record(stream)
+            g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=nt,
+                                    reuse_checkpoints=True)
+            allreduce(g)
+            evs[3].record(stream)
+        else:
+            y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, **fwd_kw)
+            evs[1].record(stream)
+            g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y,
+                                    ckpt_every=adj_ckpt, reuse_checkpoints=True)
+            allreduce(g)
+            evs[2].record(stream)
+            mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d)
+            evs[3].record(stream)
         if record:
             phase_ev.setdefault("ev", []).append(evs)
         return evs
@@ -674,12 +693,21 @@ def main():
     if args.profile:
         if rank == 0:
             print(json.dumps({"profile": True, "launches": int(launches),
-                              "step_ms": [e[0].elapsed_time(e[3]) for e in times]}))
+                              "step_ms": [e[0].elapsed_time(e[3]) for e in times],
+                              "tuning": tuning, "kept_groups": kept_groups,
+                              "adjoint": adjoint_mode}))
         return 0
     step_ms = [e[0].elapsed_time(e[3]) for e in times]
-    fwd_ms = [e[0].elapsed_time(e[1]) for e in times]
-    adj_ms = [e[1].elapsed_time(e[2]) for e in times]
-    tan_ms = [e[2].elapsed_time(e[3]) for e in times]
+    if keep_states:   # fused forward + tangent pass, then the reverse steps
+        fwt_ms = [e[0].elapsed_time(e[1]) for e in times]
+        adj_ms = [e[2].elapsed_time(e[3]) for e in times]
+        phases = {"forward_tangent": statistics.mean(fwt_ms), "adjoint": statistics.mean(adj_ms)}
+    else:
+        fwd_ms = [e[0].elapsed_time(e[1]) for e in times]
+        adj_ms = [e[1].elapsed_time(e[2]) for e in times]
+        tan_ms = [e[2].elapsed_time(e[3]) for e in times]
+        phases = {"forward": statistics.mean(fwd_ms), "adjoint": statistics.mean(adj_ms),
+                  "tangent": statistics.mean(tan_ms)}
     total_s = sum(step_ms) / 1e3
     if ws > 1:
         t = torch.tensor([total_s], device=dev)
@@ -693,15 +721,19 @@ def main():
     eps_h, wav_h, v_h = pin(w.eps, torch.float64), pin(wav, torch.float64), pin(v, torch.float64)
 
     def step_host():
-        y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, **fwd_kw)
+        if keep_states:
+            y, jv = mg.forward_jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h,
+                                              keep_states=True)
+        else:
+            y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, **fwd_kw)
         g = mg.jacobian_T_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, y, ckpt_every=adj_ckpt,
                                 reuse_checkpoints=True)
         if ws > 1:
             gt = torch.as_tensor(g, device=dev)
             allreduce(gt)
             g = gt.cpu().numpy()
-        jv = mg.jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h,
-                               reuse_states=keep_states)
+        if not keep_states:
+            jv = mg.jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h)
         return y, g, jv
 
     y, g, jv = step_host()
@@ -712,7 +744,7 @@ def main():
         y, g, jv = step_host()
     e2e_s = time.perf_counter() - t0
     R = w.shots.n_traces
-    h2d = 3 * (w.eps.nbytes + wav.nbytes) + 4 * R * nt + v.nbytes
+    h2d = (2 if keep_states else 3) * (w.eps.nbytes + wav.nbytes) + 4 * R * nt + v.nbytes
     d2h = 4 * R * nt + 8 * nlev + 4 * R * nt
 
     # plain single-source GPU path on the same workload (forward only, 4 shots)
@@ -726,7 +758,16 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     single_rate = n * 4 * nt / (e0.elapsed_time(e1) / 1e3)
-    fwd_rate = n * S * nt / (statistics.mean(fwd_ms) / 1e3)
+    if keep_states:   # the batched forward alone, for the comparison with one shot at a time
+        mg.forward(mesh, eps_d, w.shots, wav_d, dt)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mg.forward(mesh, eps_d, w.shots, wav_d, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_rate = n * S * nt / (e0.elapsed_time(e1) / 1e3)
+    else:
+        fwd_rate = n * S * nt / (statistics.mean(fwd_ms) / 1e3)
     # the kept forward history (up to ~257 GB) is not needed by the legs below
     mesh.trim()
     torch.cuda.empty_cache()
@@ -763,12 +804,30 @@ def main():
 
     if rank != 0:
         return 0
-    # roofline of the batched forward step kernel: algorithmic bytes per launch
+    # roofline of the dominant step kernel: algorithmic bytes per leapfrog
+    # step (all shot groups) / (its phase time / nt, launch gaps included)
     info = mesh.info()
     S_pad = S
-    bytes_fwd = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
-    fwd_launch_s = statistics.mean(fwd_ms) / 1e3 / nt   # includes launch gaps
     peak, peak_kind = peaks()
+    if keep_states:
+        # k_tangent_rows: p_l, p_{l-1}, dp_l, dp_{l-1} read, p_{l+1}, dp_{l+1}
+        # written per node.shot; matrix, {alpha, beta, gamma, 1/w} and the
+        # tangent coefficients per row
+        bytes_fwd = 24.0 * n * S_pad + 8.0 * info["nnz"] + 24.0 * n
+        fwd_launch_s = phases["forward_tangent"] / 1e3 / nt
+        kernel = ("k_tangent_rows (fused forward + tangent step, writing the kept history; "
+                  "per leapfrog step, all shot groups)")
+        tkey = ("asteroid_2d_fused", dict(tuning["tangent"], groups=(kept_groups or {}).get(
+            "tangent", tuning["tangent"].get("groups", 1))))
+        note = ("per-step time = fused phase / nt (includes launch gaps); p_{l+1} is written "
+                "into the kept history in HBM")
+    else:
+        bytes_fwd = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
+        fwd_launch_s = statistics.mean(fwd_ms) / 1e3 / nt   # includes launch gaps
+        kernel = "k_step (batched forward leapfrog step)"
+        tkey = ("asteroid_2d", tuning["forward"])
+        note = ("per-launch time = forward phase / nt (includes launch gaps); state "
+                "(2 x 32 MB) is L2-resident")
     achieved = bytes_fwd / fwd_launch_s / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -779,22 +838,16 @@ def main():
                    "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
                    "tuning": tuning, "adjoint": adjoint_mode, "kept_groups": kept_groups,
                    "l2": "flushed between timed steps (256 MB write)"},
-        "phases_ms": {"forward": statistics.mean(fwd_ms), "adjoint": statistics.mean(adj_ms),
-                      "tangent": statistics.mean(tan_ms)},
+        "phases_ms": phases,
         "forward_updates_per_s": fwd_rate,
         "single_source_forward_updates_per_s": single_rate,
         "batched_vs_single_source": fwd_rate / single_rate,
-        "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
+        "roofline": {"kernel": kernel, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": traffic_for("asteroid_2d", dict(
-                         tuning["forward"], groups=(kept_groups or {}).get(
-                             "forward", tuning["forward"].get("groups", 1))), keep_states),
+                     "traffic": traffic_for(tkey[0], tkey[1], keep_states),
                      "algorithmic_bytes_per_launch": bytes_fwd,
-                     "note": "per-launch time = forward phase / nt (includes launch gaps); " + (
-                         "each step writes its new 32 MB state into the kept history in HBM, "
-                         "p_l and p_{l-1} are mostly L2-resident" if keep_states else
-                         "state (2 x 32 MB) is L2-resident")},
+                     "note": note},
         "e2e": {"value": units_per_step * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

@@ -212,6 +212,24 @@ int mg_jacobian_apply(mg_mesh* mesh, int level, const double* eps,
                       int nt, const double* v, float* jv, void* stream,
                       int flags);
 
+/* The forward traces and the tangent J v in one pass: the tangent steps
+ * advance p and dp together (as mg_jacobian_apply does), so recording p's
+ * traces as well gives mg_forward's traces at no extra step.  Same traces
+ * and J v bits as mg_forward and mg_jacobian_apply.  With MG_KEEP_STATES the
+ * pass writes every forward state into the handle's kept history (as
+ * mg_forward with MG_KEEP_STATES does), so that a later mg_jacobian_T_apply
+ * with MG_REUSE_CHECKPOINTS and ckpt_every = nt needs no forward at all.
+ *   traces, jv  [rec_ptr[n_shots]][nt] FP32 outputs (device, or host with
+ *               MG_HOST_PTRS); other arguments as mg_jacobian_apply.
+ *   flags       MG_HOST_PTRS, MG_ALLOW_CFL, MG_NO_GRAPH, MG_KEEP_STATES;
+ *               MG_KEEP_CHECKPOINTS, MG_REUSE_CHECKPOINTS and
+ *               MG_SINGLE_SOURCE return MG_ERR_UNSUPPORTED.
+ * Row kernels only (the tiled tangent kernel does not record p). */
+int mg_forward_jacobian_apply(mg_mesh* mesh, int level, const double* eps,
+                              const mg_shots* shots, const double* wavelet, double dt, int nt,
+                              const double* v, float* traces, float* jv, void* stream,
+                              int flags);
+
 /* Transpose: g = J^T w, the gradient of sum_{r,l} w[r][l] y[r][l] with
  * respect to the permittivity of each cell of `level`, by the discrete
  * adjoint (reverse-time leapfrog) with checkpoints every ckpt_every steps
@@ -282,6 +300,16 @@ int mg_mesh_set_min_blocks(mg_mesh* mesh, int min_blocks);
  * warp.  on: 0 (default) or 1.  Its waits are bounded; a wait that runs out
  * is reported by mg_mesh_device_status.  Drops the cached graphs. */
 int mg_mesh_set_bulk_copies(mg_mesh* mesh, int on);
+
+/* L2 cache policy of the kept-history path (MG_KEEP_STATES): 1 makes the
+ * last read of each kept state in a pass (p_{l-1} in the forward and in the
+ * tangent on kept states, p_k in the reverse steps) carry an evict-first
+ * L2 policy, so that the lines still to be read stay in L2 while more
+ * states stream than it holds.  Results are unchanged.  Default 1
+ * (measured on the 2D bench step: forward 48.6 -> 42.7 ms and reverse steps
+ * 72.5 -> 68.1 ms per 2000 steps); 0 loads them with the default policy.
+ * Drops the cached graphs.  Errors: MG_ERR_ARG for other values. */
+int mg_mesh_set_cache_hints(mg_mesh* mesh, int on);
 
 /* Programmatic dependent launch of the row kernels (forward, tangent,
  * adjoint): 1 launches each step as a dependent of the previous kernel on

@@ -10,6 +10,7 @@ from .api import (Mesh, Shots, cfl_dt, forward, forward_batch,  # noqa: F401
                   mesh_from_workload, project, projected_jacobian_T_apply,
                   projected_jacobian_apply, projected_weights, prolong, tv_reconstruct,
                   tv_reconstruct_levels, approx_jacobian, forward_pml, jacobian_apply_pml,
+                  forward_jacobian_apply,
                   jacobian_T_apply_pml)
 
 __all__ = ["Mesh", "Shots", "mesh_create", "mesh_from_workload", "cfl_dt", "forward",
@@ -17,4 +18,5 @@ __all__ = ["Mesh", "Shots", "mesh_create", "mesh_from_workload", "cfl_dt", "forw
            "prolong", "project", "projected_weights", "projected_jacobian_apply",
            "projected_jacobian_T_apply", "tv_reconstruct", "tv_reconstruct_levels",
            "approx_jacobian",
-           "forward_pml", "jacobian_apply_pml", "jacobian_T_apply_pml"]
+           "forward_pml", "jacobian_apply_pml", "jacobian_T_apply_pml",
+           "forward_jacobian_apply"]

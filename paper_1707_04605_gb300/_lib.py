@@ -90,11 +90,15 @@ SIGNATURES = {
     "mg_mesh_set_min_blocks": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_bulk_copies": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_dependent_launch": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_cache_hints": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_device_status": (C.c_int, [C.c_void_p]),
     "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int]),
+    "mg_forward_jacobian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_tv_reconstruct_levels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -153,6 +153,12 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_bulk_copies(self.handle, int(bool(on))),
                 "mg_mesh_set_bulk_copies")
 
+    def set_cache_hints(self, on: bool):
+        """L2 evict-first on the last reads of kept states
+        (mg_mesh_set_cache_hints); results unchanged."""
+        L.check(self._lib.mg_mesh_set_cache_hints(self.handle, int(bool(on))),
+                "mg_mesh_set_cache_hints")
+
     def set_dependent_launch(self, on: bool):
         """Row kernels launched as programmatic dependents of the previous
         kernel (mg_mesh_set_dependent_launch); bit-identical results."""
@@ -305,6 +311,27 @@ def jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
                                pv, _ptr(out), st, f)
     L.check(rc, "mg_jacobian_apply")
     return out
+
+
+def forward_jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
+                           keep_states=False, allow_cfl=False, stream=None, flags=0):
+    """(traces, J v) of one fused pass (mg_forward_jacobian_apply); with
+    keep_states the forward history stays in the handle for
+    jacobian_T_apply(..., ckpt_every=nt, reuse_checkpoints=True)."""
+    lib = L.load()
+    sh = Shots.of(shots)
+    nt = int(len(wavelet) if nt is None else nt)
+    dev, (eps, pe), (wav, pw), ex, st, f0 = _prep(eps, wavelet, [(v, "float64")], stream)
+    (v, pv), = ex
+    y = _alloc(dev, (sh.n_traces, nt), "float32", eps)
+    jv = _alloc(dev, (sh.n_traces, nt), "float32", eps)
+    f = f0 | flags | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    if keep_states:
+        f |= L.MG_KEEP_STATES
+    rc = lib.mg_forward_jacobian_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw,
+                                       float(dt), nt, pv, _ptr(y), _ptr(jv), st, f)
+    L.check(rc, "mg_forward_jacobian_apply")
+    return y, jv
 
 
 def jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, w, nt=None, *,

@@ -118,6 +118,7 @@ struct mg_mesh {
     int bulk = 0;         // forward: neighbour rows staged by bulk async copies
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
+  int cache_hints = 1;                    // kept history: L2 evict-first on last reads
   Buf errbuf;                             // device status word of bounded waits
   struct TileTables {
     Buf ell_off, ell_idx, ell_val, sinfo, halo_off, halo_cnt, halo;
@@ -133,6 +134,7 @@ struct mg_mesh {
   Buf sigma;                              // conductivity per finest cell (FP64)
   bool has_sigma = false;
   Buf tr;                                 // internal trace buffer [R][nt]
+  Buf trf;                                // forward traces of the fused forward + tangent
   Buf tune_scratch;                       // autotuner inputs/outputs
 };
 
@@ -574,6 +576,7 @@ int run_forward_states(mg_mesh* M, const Prep& pp, int nt, float* traces, float*
   MG_CU(cudaMemsetAsync(seg, 0, 2 * state * sizeof(float), st));
   mg::StepArgs a = step_args(M, pp, pp.S_pad, nt);
   a.traces = traces;
+  a.hint = M->cache_hints;
   const int W = group_cols(M, 0, pp.S_pad), NG = pp.S_pad / W;
   if (graphs_on(M, flags) && nt % 2 == 0) {
     MG_TRY(ensure(M->step_base, 16));
@@ -739,7 +742,7 @@ int mg_mesh_trim(mg_mesh* M) {
   Buf* all[] = {&M->eps_h, &M->wav_h, &M->wavf, &M->coef, &M->tcoef, &M->mass, &M->scal,
                 &M->stA, &M->stB, &M->stC, &M->stD, &M->out_h, &M->w_h, &M->v_h, &M->g_h,
                 &M->ev, &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base, &M->tr,
-                &M->tune_scratch};
+                &M->trf, &M->tune_scratch};
   for (Buf* b : all) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -847,6 +850,13 @@ int mg_mesh_set_shot_groups(mg_mesh* M, int kind, int groups) {
   return MG_OK;
 }
 
+int mg_mesh_set_cache_hints(mg_mesh* M, int on) {
+  if (!M || (on != 0 && on != 1)) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->cache_hints = on;
+  return MG_OK;
+}
+
 int mg_mesh_set_dependent_launch(mg_mesh* M, int on) {
   if (!M || (on != 0 && on != 1)) return MG_ERR_ARG;
   drop_graphs(M);
@@ -912,7 +922,7 @@ int mg_mesh_get_info(const mg_mesh* M, mg_mesh_info_t* info) {
                       &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas, &M->eps_h,
                       &M->wav_h, &M->wavf, &M->coef, &M->tcoef, &M->mass, &M->scal, &M->stA,
                       &M->stB, &M->stC, &M->stD, &M->out_h, &M->w_h, &M->v_h, &M->g_h, &M->ev,
-                      &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base};
+                      &M->G, &M->ckpt, &M->seg, &M->gfine, &M->step_base, &M->tr, &M->trf};
   for (const Buf* b : all) bytes += (int64_t)b->bytes;
   info->device_bytes = bytes;
   return MG_OK;
@@ -1042,6 +1052,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
     float* seg = P<float>(M->seg);
     a.f.batch = M->tune[1].batch;
     a.f.pdl = M->dep_launch;
+    a.f.hint = M->cache_hints;
     const int W = group_cols(M, 1, pp.S_pad), NG = pp.S_pad / W;
     int32_t* base = nullptr;
     const bool graph = graphs_on(M, flags);
@@ -1132,6 +1143,124 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
   return deliver(M->tr, jv, tbytes, flags, st);
 }
 
+int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* shots,
+                              const double* wavelet, double dt, int nt, const double* v,
+                              float* traces, float* jv, void* stream, int flags) {
+  if (!M || !v || !jv || !traces) return MG_ERR_ARG;
+  if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
+  if (flags & (MG_SINGLE_SOURCE | MG_KEEP_CHECKPOINTS | MG_REUSE_CHECKPOINTS))
+    return MG_ERR_UNSUPPORTED;
+  DeviceGuard g(M->device);
+  if (!g.ok) return MG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Prep pp;
+  MG_TRY(prepare(M, eps, shots, wavelet, dt, nt, flags, st, pp));
+  MG_TRY(ensure_level(M, level));
+  const void* d;
+  MG_TRY(stage_in(M->v_h, v, M->hm.n_cells_level[level] * sizeof(double), flags, st, &d));
+  MG_TRY(ensure(M->tcoef, M->hm.n * sizeof(float2)));
+  mg::TangentCoefArgs tca;
+  tca.c = coef_args(M, pp.eps, dt);
+  tca.v = static_cast<const double*>(d);
+  tca.anc = P<int32_t>(M->anc[level]);
+  tca.tcoef = P<float2>(M->tcoef);
+  MG_TRY(mg::launch_tangent_coefs(tca, st));
+  M->launches += 1;
+  const size_t tbytes = (size_t)pp.R * nt * sizeof(float);
+  MG_TRY(ensure(M->tr, tbytes));
+  MG_TRY(ensure(M->trf, tbytes));
+  float* tr = P<float>(M->tr);
+  float* trf = P<float>(M->trf);
+  const int64_t n = M->hm.n;
+  const size_t state = (size_t)n * pp.S_pad;
+  const bool keep = flags & MG_KEEP_STATES;
+  M->ck_valid = false;
+  M->seg_full = false;
+  float *p = nullptr, *pm = nullptr, *seg = nullptr;
+  if (keep) {
+    MG_TRY(ensure(M->seg, (size_t)(nt + 2) * state * sizeof(float)));
+    seg = P<float>(M->seg);
+    MG_CU(cudaMemsetAsync(seg, 0, 2 * state * sizeof(float), st));
+  } else {
+    for (Buf* b : {&M->stA, &M->stB}) {
+      MG_TRY(ensure(*b, state * sizeof(float)));
+      MG_CU(cudaMemsetAsync(b->p, 0, state * sizeof(float), st));
+    }
+    p = P<float>(M->stA);
+    pm = P<float>(M->stB);
+  }
+  for (Buf* b : {&M->stC, &M->stD}) {
+    MG_TRY(ensure(*b, state * sizeof(float)));
+    MG_CU(cudaMemsetAsync(b->p, 0, state * sizeof(float), st));
+  }
+  float *q = P<float>(M->stC), *qm = P<float>(M->stD);
+  mg::TangentArgs a{};
+  a.f = step_args(M, pp, pp.S_pad, nt);
+  a.f.traces = trf;
+  a.f.batch = M->tune[1].batch;
+  a.f.pdl = M->dep_launch;
+  a.f.hint = keep ? M->cache_hints : 0;   // p_{l-1} is last read here only when kept
+  a.tcoef = P<const float2>(M->tcoef);
+  a.dtraces = tr;
+  const int W = group_cols(M, 1, pp.S_pad), NG = pp.S_pad / W;
+  int32_t* base = nullptr;
+  const bool graph = graphs_on(M, flags);
+  if (graph) {
+    MG_TRY(ensure(M->step_base, 16));
+    base = P<int32_t>(M->step_base);
+    MG_TRY(mg::launch_set_int(base, 0, st));
+    M->launches += 1;
+  }
+  auto record = [&](cudaStream_t cs) -> int {
+    mg::TangentArgs b = a;
+    b.f.step_base = base;
+    b.f.cols = W;
+    for (int g = 0; g < NG; ++g) {   // each shot group runs the whole history
+      b.f.col0 = g * W;
+      float *x = p, *y = pm, *u = q, *z = qm;
+      for (int j = 0; j < nt; ++j) {
+        if (keep) {
+          b.f.p = seg + (size_t)(j + 1) * state;
+          b.f.pm = seg + (size_t)j * state;
+          b.f.pout = seg + (size_t)(j + 2) * state;
+        } else {
+          b.f.p = x;
+          b.f.pm = y;
+          b.f.pout = y;
+          std::swap(x, y);
+        }
+        b.q = u;
+        b.qm = z;
+        b.f.step = j;
+        MG_TRY(mg::launch_tangent(b, pp.S_pad, cs));
+        std::swap(u, z);
+      }
+    }
+    return MG_OK;
+  };
+  if (graph) {
+    const std::string key = key_of("fwdtan", {seg, p, pm, q, qm, tr, trf, a.f.wavelet, a.f.coef,
+                                              a.tcoef, a.f.ev.src_ptr, base},
+                                   {pp.S_pad, pp.S, pp.R, nt, n, W, keep ? 1 : 0});
+    MG_TRY(run_graph(M, key, NG * nt, st, record));
+  } else {
+    MG_TRY(record(st));
+    M->launches += (int64_t)NG * nt;
+  }
+  if (keep) {
+    M->ck_valid = true;
+    M->seg_full = true;
+    M->ck_every = nt;
+    M->ck_nt = nt;
+    M->ck_S_pad = pp.S_pad;
+    M->ck_nshots = pp.S;
+    M->ck_dt = dt;
+    M->ck_ev_gen = M->ev_gen;
+  }
+  MG_TRY(deliver(M->trf, traces, tbytes, flags, st));
+  return deliver(M->tr, jv, tbytes, flags, st);
+}
+
 int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots* shots,
                         const double* wavelet, double dt, int nt, const float* w, double* g,
                         int ckpt_every, void* stream, int flags) {
@@ -1207,6 +1336,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.Gc = G + acc;
   aa.H = G + 2 * acc;
   aa.Hc = G + 3 * acc;
+  aa.hint = states ? M->cache_hints : 0;
   const bool use_graph = graphs_on(M, flags) && ckpt_every % 2 == 0 && ckpt_every <= nt;
   int32_t* base = nullptr;
   if (use_graph) {

@@ -44,11 +44,12 @@ struct StepArgs {
   int32_t col0 = 0;         // first shot column advanced (multiple of the launch's shot tile)
   int32_t cols = 0;         // shot columns advanced, [col0, col0 + cols); 0 = all ld
   int32_t pdl = 0;          // row kernels: launch dependent on the previous kernel
+  int32_t hint = 0;         // row kernels: L2 evict-first on the last read of pm
 };
 
 // Tangent step: forward and tangent states advance together.
 struct TangentArgs {
-  StepArgs f;               // forward (traces unused)
+  StepArgs f;               // forward (f.traces: forward traces, row kernel only, or null)
   const float* q;           // dp_l
   float* qm;                // dp_{l-1} in, dp_{l+1} out
   const float2* tcoef;      // {gamma dm/dt^2, gamma dD/(2 dt)} per row
@@ -76,6 +77,7 @@ struct AdjointArgs {
   int32_t col0 = 0;         // shot columns [col0, col0 + cols) as in StepArgs
   int32_t cols = 0;
   int32_t pdl = 0;          // as in StepArgs
+  int32_t hint = 0;         // row kernel: L2 evict-first on the read of pk
   float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;

@@ -31,6 +31,24 @@ __device__ __forceinline__ void grid_dep_sync() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Load of a row's float4 that is its state's last use in this pass, with
+// an L2 evict-first policy when `hint` is set (the kept history streams
+// more states than L2 holds; the lines still to be read are kept instead).
+// NC: read-only data of the launch (no store of this launch aliases it).
+template <bool NC>
+__device__ __forceinline__ float4 ld_last(const float* p, int hint) {
+  if (!hint)
+    return NC ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+  float4 v;
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], pol;\n\t}"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+
 struct Row {
   const int2* e;  // entry 0 of the row (stride kSliceH)
   int w;          // entries of the row's slice, diagonal first
@@ -179,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   const size_t ro = (size_t)row * a.ld + base;
   float4 old[NV], self[NV], acc[NV];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) old[j] = *reinterpret_cast<const float4*>(a.pm + ro + 4 * LPR * j);
+  for (int j = 0; j < NV; ++j) old[j] = ld_last<false>(a.pm + ro + 4 * LPR * j, a.hint);
   row_sum<LPR, NV>(r, a.p + base, row, lr, mask, a.ld, self, acc);
   float4 out[NV];
 #pragma unroll
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
   float4 pold[NV], qold[NV], ps[NV], qs[NV], pacc[NV], qacc[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
-    pold[j] = *reinterpret_cast<const float4*>(a.f.pm + ro + 4 * LPR * j);
+    pold[j] = ld_last<false>(a.f.pm + ro + 4 * LPR * j, a.f.hint);
     qold[j] = *reinterpret_cast<const float4*>(a.qm + ro + 4 * LPR * j);
   }
   row_sum2<LPR, NV>(r, a.f.p + base, a.q + base, row, lr, mask, ld, ps, qs, pacc, qacc);
@@ -253,7 +271,11 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
   for (int q = r0; q < r1; ++q) {
     int d;
     const int j = owner<LPR, NV>(__ldg(a.f.ev.rec_shot + q), tile0, lr, d);
-    if (j >= 0) a.dtraces[(size_t)__ldg(a.f.ev.rec_trace + q) * a.f.nt + l] = get_from<NV>(qn, j, d);
+    if (j >= 0) {
+      const size_t at = (size_t)__ldg(a.f.ev.rec_trace + q) * a.f.nt + l;
+      a.dtraces[at] = get_from<NV>(qn, j, d);
+      if (a.f.traces) a.f.traces[at] = get_from<NV>(pn, j, d);   // forward traces too
+    }
   }
 }
 
@@ -282,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_kept_rows(TangentArgs a) {
   for (int j = 0; j < NV; ++j) {
     pn[j] = __ldg(reinterpret_cast<const float4*>(a.pk1 + ro + 4 * LPR * j));
     ps[j] = __ldg(reinterpret_cast<const float4*>(a.f.p + ro + 4 * LPR * j));
-    pold[j] = __ldg(reinterpret_cast<const float4*>(a.f.pm + ro + 4 * LPR * j));
+    pold[j] = ld_last<true>(a.f.pm + ro + 4 * LPR * j, a.f.hint);
     qold[j] = *reinterpret_cast<const float4*>(a.qm + ro + 4 * LPR * j);
   }
   row_sum<LPR, NV>(r, a.q + base, row, lr, mask, ld, qs, qacc);
@@ -321,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       old[j] = *reinterpret_cast<const float4*>(a.mu1 + ro + 4 * LPR * j);  // mu_{k+1}
-      pk[j] = __ldg(reinterpret_cast<const float4*>(a.pk + ro + 4 * LPR * j));
+      pk[j] = ld_last<true>(a.pk + ro + 4 * LPR * j, a.hint);
     }
     row_sum<LPR, NV>(r, a.mu + base, row, lr, mask, a.ld, self, acc);
     float4 out[NV];

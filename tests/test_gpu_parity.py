@@ -221,8 +221,9 @@ def test_adjoint_checkpoint_spacing_and_reuse(mg):
     assert np.array_equal(gh, g64.cpu().numpy())
 
 
-@pytest.mark.parametrize("nt,chunk", [(300, 128), (301, 128), (300, 0)])
-def test_kept_states_give_the_checkpointed_gradient(mg, nt, chunk):
+@pytest.mark.parametrize("nt,chunk,hints", [(300, 128, 0), (301, 128, 1), (300, 0, 0),
+                                            (300, 128, 1)])
+def test_kept_states_give_the_checkpointed_gradient(mg, nt, chunk, hints):
     """A forward that keeps every state lets J^T w skip its recompute and J v
     read the forward field: same traces, gradient and tangent bits as the
     checkpointed and recomputing paths (even and odd nt, graphs and plain
@@ -237,6 +238,7 @@ def test_kept_states_give_the_checkpointed_gradient(mg, nt, chunk):
     W = _dev(np.random.default_rng(2).standard_normal((w.shots.n_traces, nt)), torch.float32)
     y_ref = mg.forward(mesh, eps, w.shots, s, dt)
     g_ref = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+    mesh.set_cache_hints(hints)
     y = mg.forward(mesh, eps, w.shots, s, dt, keep_states=True)
     assert torch.equal(y, y_ref)
     n0 = mesh.launch_count()
@@ -266,6 +268,44 @@ def test_kept_states_give_the_checkpointed_gradient(mg, nt, chunk):
     assert torch.equal(g3, g_ref)
     with pytest.raises(RuntimeError):
         mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, reuse_states=True)
+
+
+@pytest.mark.parametrize("nt,chunk,groups,keep", [(300, 128, 1, True), (301, 128, 2, True),
+                                                  (300, 0, 1, False), (300, 128, 2, False)])
+def test_fused_forward_tangent_gives_the_separate_results(mg, nt, chunk, groups, keep):
+    """One pass for the forward traces and J v: the bits of mg_forward and
+    mg_jacobian_apply; with the history kept, J^T w runs with no forward and
+    gives the checkpointed gradient's bits; host pointers give the same."""
+    w = configs.asteroid_2d(n_refine=1, S=12, nt=nt)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(chunk, -1, -1, -1)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    eps = _dev(w.eps)
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(w.mesh.n_cells[1])
+    W = _dev(rng.standard_normal((w.shots.n_traces, nt)), torch.float32)
+    y_ref = mg.forward(mesh, eps, w.shots, s, dt)
+    jv_ref = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, _dev(v))
+    g_ref = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+    mesh.set_shot_groups(groups, "tangent")      # the kind the fused pass runs as
+    y, jv = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, _dev(v), keep_states=keep)
+    assert torch.equal(y, y_ref)
+    assert torch.equal(jv, jv_ref)
+    if keep:
+        n0 = mesh.launch_count()
+        g = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=nt,
+                                reuse_checkpoints=True)
+        assert torch.equal(g, g_ref)
+        assert mesh.launch_count() - n0 < nt + 64
+    else:
+        with pytest.raises(RuntimeError):
+            mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=nt,
+                                reuse_checkpoints=True)
+    yh, jvh = mg.forward_jacobian_apply(mesh, 1, w.eps, w.shots, w.wavelet(dt), dt, v,
+                                        keep_states=keep)
+    assert np.array_equal(yh, y_ref.cpu().numpy())
+    assert np.array_equal(jvh, jv_ref.cpu().numpy())
 
 
 @pytest.mark.parametrize("chunk,batch,tile_rows,src_tile", [
