@@ -162,6 +162,10 @@ TRAFFIC = {
     # written, the algorithmic 197.4 MB
     ("asteroid_2d_fused", True, 1, 0, 1, 0, 0): (196.6e6,
                                                  "58797ac3fca23f88179321aa29f05fe8e8504f0c"),
+    # k_tangent_rows<16,1> with two shot groups (64 columns per launch),
+    # launches 2-4: 12.5 MB read + 24.5 MB written per launch, two per step
+    ("asteroid_2d_fused", True, 1, 0, 2, 0, 0): (73.9e6,
+                                                 "58797ac3fca23f88179321aa29f05fe8e8504f0c"),
     # k_step_rows<8,2,5>, two launches: 1228.5 MB read + 438.1 MB written
     ("ellipsoid_3d", False, 2, 0, 1, 5, 0): (1.667e9, "58797ac3fca23f88179321aa29f05fe8e8504f0c"),
 }
