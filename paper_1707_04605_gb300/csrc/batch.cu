@@ -112,6 +112,21 @@ __global__ void __launch_bounds__(32 * kBW) k_step_multi(const Inst* __restrict_
   }
 }
 
+// 4-byte asynchronous copy global -> shared, waited for by the issuing
+// thread (cp.async.wait_all): the row's accumulators are fetched while the
+// step is computed instead of after it.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void kahan_step(float& s, float& c, float term) {
+  const float y = term - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 __global__ void __launch_bounds__(32 * kBW) k_adjoint_multi(const Inst* __restrict__ insts,
                                                             const Work* __restrict__ work, int k,
                                                             int l0, int nt) {
@@ -126,6 +141,16 @@ __global__ void __launch_bounds__(32 * kBW) k_adjoint_multi(const Inst* __restri
   const float* mu = even ? I.mu : I.mu1;
   float* mu1 = even ? I.mu1 : I.mu;
   float t1 = 0.0f, t2 = 0.0f;
+  __shared__ float acc_s[kBW * 32][4];
+  float* mine = acc_s[threadIdx.x];
+  if (valid && (lane % lpr) == 0) {
+    const size_t gi = (size_t)wk.tile * I.K.n + row;
+    cp_async4(mine + 0, I.G + gi);
+    cp_async4(mine + 1, I.G + I.acc + gi);
+    cp_async4(mine + 2, I.G + 2 * I.acc + gi);
+    cp_async4(mine + 3, I.G + 3 * I.acc + gi);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   if (valid) {
     float4 self;
     const float4 acc = gather(I.K, row, mu, I.ld, src0, self);
@@ -150,9 +175,15 @@ __global__ void __launch_bounds__(32 * kBW) k_adjoint_multi(const Inst* __restri
     if (off < lpr) { t1 += a1; t2 += a2; }
   }
   if (valid && (lane % lpr) == 0) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    float g = mine[0], gc = mine[1], h = mine[2], hc = mine[3];
+    kahan_step(g, gc, t1);
+    kahan_step(h, hc, t2);
     const size_t gi = (size_t)wk.tile * I.K.n + row;
-    kahan_add(I.G + gi, I.G + I.acc + gi, t1);
-    kahan_add(I.G + 2 * I.acc + gi, I.G + 3 * I.acc + gi, t2);
+    I.G[gi] = g;
+    I.G[I.acc + gi] = gc;
+    I.G[2 * I.acc + gi] = h;
+    I.G[3 * I.acc + gi] = hc;
   }
 }
 

@@ -323,6 +323,21 @@ __global__ void __launch_bounds__(kThreads) k_tangent_kept_rows(TangentArgs a) {
   }
 }
 
+// 4-byte asynchronous copy global -> shared (no register holds the value
+// while it is in flight); the issuing thread waits with cp.async.wait_all.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// One compensated (Kahan) addition on values held in registers.
+__device__ __forceinline__ void kahan_step(float& s, float& c, float term) {
+  const float y = term - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 template <int LPR, int NV>
 __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
@@ -334,9 +349,22 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
   const int tile0 = a.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
   float t1 = 0.0f, t2 = 0.0f;
+  // the row's accumulators (one set per source tile, read and written by
+  // this row's lane 0 only in this launch) are copied to shared memory
+  // before the gathers and updated at the end
+  __shared__ float acc_s[kWarps * 32][4];
+  float* mine = acc_s[warp * RPW + lane / LPR];
   if (valid) {
     const Row r = row_of(a.K, row);
     grid_dep_sync();
+    if (lr == 0) {
+      const size_t gi = (size_t)(tile0 / TW) * a.K.n + row;
+      cp_async4(mine + 0, a.G + gi);
+      cp_async4(mine + 1, a.Gc + gi);
+      cp_async4(mine + 2, a.H + gi);
+      cp_async4(mine + 3, a.Hc + gi);
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     const float4 c = __ldg(a.coef + row);
     const size_t ro = (size_t)row * a.ld + base;
     float4 old[NV], pk[NV], self[NV], acc[NV];
@@ -369,9 +397,15 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
     t2 += __shfl_xor_sync(0xffffffffu, t2, off);
   }
   if (valid && lr == 0) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    float g = mine[0], gc = mine[1], h = mine[2], hc = mine[3];
+    kahan_step(g, gc, t1);
+    kahan_step(h, hc, t2);
     const size_t gi = (size_t)(tile0 / TW) * a.K.n + row;
-    kahan_add(a.G + gi, a.Gc + gi, t1);
-    kahan_add(a.H + gi, a.Hc + gi, t2);
+    a.G[gi] = g;
+    a.Gc[gi] = gc;
+    a.H[gi] = h;
+    a.Hc[gi] = hc;
   }
 }
 
