@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--kept-groups", default="",
                     help="shot groups forward,adjoint,tangent of the kept-history path "
                          "(instead of timing 1, 2, 4)")
+    ap.add_argument("--uniform-ell", type=int, default=-1,
+                    help="uniformly strided stiffness copy for the row kernels (0 or 1)")
     ap.add_argument("--cache-hints", type=int, default=-1,
                     help="kept history: L2 evict-first on the last reads (0 or 1)")
     ap.add_argument("--hbm-only", action="store_true",
@@ -155,15 +157,19 @@ def clocks_stop(proc, gpu_index):
 # only while those sources are unchanged, else the roofline's traffic is null.
 KERNEL_SOURCES = ["kernels_rows.cu", "device_util.cuh", "kernels.cuh"]
 TRAFFIC = {
-    # (workload, kept history, batch, tile_rows, groups, min_blocks, bulk):
-    # (bytes per leapfrog step, all shot groups; sha1 of the kernel sources)
+    # (workload, kept history, batch, tile_rows, groups, min_blocks, bulk,
+    #  uniform ELL): (bytes per leapfrog step, all shot groups; sha1 of the
+    #  kernel sources)
     # k_tangent_rows<16,1>, fused forward + tangent writing the kept history,
-    # two shot groups (64 columns per launch), --cache-control none,
-    # launches 22-24: 12.6 MB read + 24.6 MB written per launch, two per step
-    ("asteroid_2d_fused", True, 1, 0, 2, 0, 0): (74.3e6,
-                                                 "7b2eaa14bdb435509c78f3b901baf87b1ee3485b"),
-    # k_step_rows<8,2,5>, two launches: 1228.5 MB read + 438.3 MB written
-    ("ellipsoid_3d", False, 2, 0, 1, 5, 0): (1.667e9, "7b2eaa14bdb435509c78f3b901baf87b1ee3485b"),
+    # two shot groups (64 columns per launch), uniformly strided stiffness,
+    # --cache-control none, launches 22-24: 12.3 MB read + 24.6 MB written
+    # per launch, two per step
+    ("asteroid_2d_fused", True, 1, 0, 2, 0, 0, True): (
+        73.8e6, "8714da4412172775de3ff1b4f018c7730eb755d5"),
+    # k_step_rows<8,2,5>, sliced stiffness, two launches: 1228.5 MB read +
+    # 438.3 MB written
+    ("ellipsoid_3d", False, 2, 0, 1, 5, 0, False): (
+        1.667e9, "8714da4412172775de3ff1b4f018c7730eb755d5"),
 }
 
 
@@ -179,9 +185,9 @@ def sources_sha1():
     return h.hexdigest()
 
 
-def traffic_for(workload, fwd, kept=False):
+def traffic_for(workload, fwd, kept=False, uniform=False):
     key = (workload, bool(kept), fwd["batch"], fwd["tile_rows"], fwd.get("groups", 1),
-           fwd.get("min_blocks", 0), fwd.get("bulk", 0))
+           fwd.get("min_blocks", 0), fwd.get("bulk", 0), bool(uniform))
     hit = TRAFFIC.get(key)
     return hit[0] if hit and hit[1] == sources_sha1() else None
 
@@ -614,6 +620,16 @@ def main():
         mesh.set_dependent_launch(args.dep_launch)
     if args.cache_hints != -1:
         mesh.set_cache_hints(args.cache_hints)
+    # uniformly strided stiffness copy for the row kernels unless refused
+    # (measured +1.7% on this step) or switched off
+    uniform = False
+    if args.uniform_ell != 0:
+        try:
+            mesh.set_uniform_ell(True)
+            uniform = True
+        except mg._lib.MgError:
+            if args.uniform_ell == 1:
+                raise
     n, S, nt = w.n_nodes, w.shots.n_shots, w.nt
     eps_d = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps_d)
@@ -854,6 +870,7 @@ def main():
         "config": {"workload": describe(w), "nodes": n, "shots": S, "nt": nt,
                    "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
                    "tuning": tuning, "adjoint": adjoint_mode, "kept_groups": kept_groups,
+                   "stiffness": "uniformly strided ELL" if uniform else "sliced ELL",
                    "l2": "flushed between timed steps (256 MB write)"},
         "phases_ms": phases,
         "forward_updates_per_s": fwd_rate,
@@ -862,7 +879,7 @@ def main():
         "roofline": {"kernel": kernel, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": traffic_for(tkey[0], tkey[1], keep_states),
+                     "traffic": traffic_for(tkey[0], tkey[1], keep_states, uniform),
                      "algorithmic_bytes_per_launch": bytes_fwd,
                      "note": note},
         "e2e": {"value": units_per_step * e2e_steps / e2e_s, "unit": UNIT,

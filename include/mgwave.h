@@ -311,6 +311,16 @@ int mg_mesh_set_bulk_copies(mg_mesh* mesh, int on);
  * Drops the cached graphs.  Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_cache_hints(mg_mesh* mesh, int on);
 
+/* Uniformly strided stiffness copy for the row kernels: 1 builds (once) a
+ * copy of the sliced ELL with every slice padded to the widest slice's
+ * column count (padding {row, 0}), so a row's first entry address is
+ * arithmetic and its entry loads need not wait for the slice offset.  Same
+ * entries in the same order: same results.  Refused with
+ * MG_ERR_UNSUPPORTED when the padding would more than double the stored
+ * entries (meshes with very uneven row lengths).  0 returns to the sliced
+ * layout.  Drops the cached graphs.  Errors: MG_ERR_ARG for other values. */
+int mg_mesh_set_uniform_ell(mg_mesh* mesh, int on);
+
 /* Programmatic dependent launch of the row kernels (forward, tangent,
  * adjoint): 1 launches each step as a dependent of the previous kernel on
  * the stream, so that its CTAs are scheduled while the previous step's last

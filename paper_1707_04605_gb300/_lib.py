@@ -91,6 +91,7 @@ SIGNATURES = {
     "mg_mesh_set_bulk_copies": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_dependent_launch": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_cache_hints": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_uniform_ell": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_device_status": (C.c_int, [C.c_void_p]),
     "mg_tv_reconstruct": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,

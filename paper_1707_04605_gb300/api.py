@@ -153,6 +153,12 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_bulk_copies(self.handle, int(bool(on))),
                 "mg_mesh_set_bulk_copies")
 
+    def set_uniform_ell(self, on: bool):
+        """Uniformly strided stiffness copy for the row kernels
+        (mg_mesh_set_uniform_ell); same results."""
+        L.check(self._lib.mg_mesh_set_uniform_ell(self.handle, int(bool(on))),
+                "mg_mesh_set_uniform_ell")
+
     def set_cache_hints(self, on: bool):
         """L2 evict-first on the last reads of kept states
         (mg_mesh_set_cache_hints); results unchanged."""

@@ -118,6 +118,9 @@ struct mg_mesh {
     int bulk = 0;         // forward: neighbour rows staged by bulk async copies
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
+  Buf ellu;                               // ELL with every slice padded to wu columns
+  int wu = 0;
+  bool uniform_ell = false;
   int cache_hints = 1;                    // kept history: L2 evict-first on last reads
   Buf errbuf;                             // device status word of bounded waits
   struct TileTables {
@@ -145,8 +148,13 @@ const char* kErr[] = {"ok", "invalid argument", "invalid nesting", "out of devic
                       "unsupported combination"};
 
 mg::DevEll dev_ell(mg_mesh* M) {
-  return {P<const int2>(M->ell), P<const int64_t>(M->slice_off), P<const int32_t>(M->slice_w),
-          (int32_t)M->hm.n};
+  mg::DevEll K{P<const int2>(M->ell), P<const int64_t>(M->slice_off),
+               P<const int32_t>(M->slice_w), (int32_t)M->hm.n};
+  if (M->uniform_ell && M->ellu.p) {
+    K.ellu = P<const int2>(M->ellu);
+    K.wu = M->wu;
+  }
+  return K;
 }
 
 mg::CoefArgs coef_args(mg_mesh* M, const double* eps, double dt) {
@@ -717,7 +725,7 @@ void mg_mesh_destroy(mg_mesh* M) {
   DeviceGuard g(M->device);
   Buf* all[] = {&M->ell, &M->slice_off, &M->slice_w, &M->nc_ptr, &M->nc_cell, &M->nc_w,
                 &M->nf_ptr, &M->nf_cell, &M->nf_w, &M->is_bnd, &M->row_abs, &M->cells,
-                &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas};
+                &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas, &M->ellu};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto* v : {&M->anc, &M->lvl_ptr, &M->lvl_idx})
@@ -854,6 +862,48 @@ int mg_mesh_set_cache_hints(mg_mesh* M, int on) {
   if (!M || (on != 0 && on != 1)) return MG_ERR_ARG;
   drop_graphs(M);
   M->cache_hints = on;
+  return MG_OK;
+}
+
+int mg_mesh_set_uniform_ell(mg_mesh* M, int on) {
+  if (!M || (on != 0 && on != 1)) return MG_ERR_ARG;
+  drop_graphs(M);
+  if (!on) {
+    M->uniform_ell = false;
+    return MG_OK;
+  }
+  if (!M->ellu.p) {
+    const mg::HostMesh& h = M->hm;
+    int w = 0;
+    for (int32_t x : h.slice_w) w = std::max(w, (int)x);
+    const size_t total = (size_t)h.n_slices * w * mg::kSliceH;
+    const size_t stored = h.slice_off.empty() ? 0 : (size_t)h.slice_off.back();
+    if (stored == 0 || total > 2 * stored) return MG_ERR_UNSUPPORTED;   // padding would double K
+    DeviceGuard g(M->device);
+    if (!g.ok) return MG_ERR_CUDA;
+    // the host copy of the entries is released after upload: read them back
+    std::vector<mg::EllEntry> ell(stored);
+    if (cudaMemcpy(ell.data(), M->ell.p, stored * sizeof(mg::EllEntry),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return MG_ERR_CUDA;
+    std::vector<int32_t> u(2 * total);
+    for (int64_t s = 0; s < h.n_slices; ++s)
+      for (int k = 0; k < w; ++k)
+        for (int r = 0; r < mg::kSliceH; ++r) {
+          const size_t o = ((size_t)s * w + k) * mg::kSliceH + r;
+          if (k < h.slice_w[s]) {
+            const mg::EllEntry& e = ell[h.slice_off[s] + (size_t)k * mg::kSliceH + r];
+            std::memcpy(&u[2 * o], &e, sizeof(e));
+          } else {
+            const float zero = 0.0f;
+            u[2 * o] = (int32_t)(s * mg::kSliceH + r);
+            std::memcpy(&u[2 * o + 1], &zero, sizeof(zero));
+          }
+        }
+    MG_TRY(upload(M->ellu, u));
+    M->wu = w;
+  }
+  M->uniform_ell = true;
   return MG_OK;
 }
 

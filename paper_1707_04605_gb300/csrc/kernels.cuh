@@ -13,6 +13,8 @@ struct DevEll {
   const int64_t* slice_off;
   const int32_t* slice_w;
   int32_t n;                // rows
+  const int2* ellu = nullptr;  // row kernels: the same entries with every slice
+  int32_t wu = 0;              // padded to wu columns (slice s at s * wu * 32)
 };
 
 // Per-row event lists built from a shot batch: sources and receivers.

@@ -54,10 +54,14 @@ struct Row {
   int w;          // entries of the row's slice, diagonal first
 };
 
+// With the uniformly strided copy (K.ellu) the row's first entry address is
+// arithmetic, so the entry loads need not wait for the slice offset.
 __device__ __forceinline__ Row row_of(const DevEll& K, int row) {
   const int slice = row / kSliceH;
   Row r;
-  r.e = K.ell + __ldg(K.slice_off + slice) + (row - slice * kSliceH);
+  const int2* base = K.ellu ? K.ellu + (size_t)slice * K.wu * kSliceH
+                            : K.ell + __ldg(K.slice_off + slice);
+  r.e = base + (row - slice * kSliceH);
   r.w = __ldg(K.slice_w + slice);
   return r;
 }

@@ -444,6 +444,36 @@ def test_dependent_launch_gives_identical_results(mg, S, batch, groups, chunk):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("S,batch", [(100, 2), (37, 1), (300, 2)])
+def test_uniform_ell_gives_identical_results(mg, S, batch):
+    """The uniformly strided stiffness copy holds the same entries in the
+    same order: forward, fused forward + tangent and J^T w keep their bits;
+    the 3D mesh with uneven row lengths may refuse it."""
+    w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(-1, batch, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    rng = np.random.default_rng(9)
+    W = _dev(rng.standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    v = _dev(rng.standard_normal(w.mesh.n_cells[1]))
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                *mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    mesh.set_uniform_ell(True)
+    out = run()
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+    mesh.set_uniform_ell(False)
+    for a, b in zip(ref, run()):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("S,batch", [(100, 1), (100, 2), (6, 1), (300, 2), (64, 2)])
 def test_bulk_copied_forward_gives_identical_results(mg, S, batch):
     """Neighbour rows staged by bulk asynchronous copies: same arithmetic in
