@@ -206,7 +206,13 @@ int mg_forward_noalloc(mg_mesh* mesh, const double* eps, const mg_shots* shots,
  * (linearized2), exact for the lumped scheme).
  *  level  0..n_levels-1, the mesh level that carries v
  *  v      data, [cells of level] float64
- *  jv     data, [rec_ptr[n_shots]][nt] float32 output */
+ *  jv     data, [rec_ptr[n_shots]][nt] float32 output
+ *  flags  as mg_forward; with MG_REUSE_CHECKPOINTS the forward field is read
+ *         from the history kept by the last mg_forward (or
+ *         mg_forward_jacobian_apply) with MG_KEEP_STATES on this handle (same
+ *         eps, shots, wavelet, dt, nt) instead of being advanced alongside:
+ *         same bits, one sparse product per row instead of two; MG_ERR_ARG
+ *         when no such history is kept. */
 int mg_jacobian_apply(mg_mesh* mesh, int level, const double* eps,
                       const mg_shots* shots, const double* wavelet, double dt,
                       int nt, const double* v, float* jv, void* stream,
