@@ -300,6 +300,33 @@ int mg_mesh_set_shot_groups(mg_mesh* mesh, int kind, int groups);
  * Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_min_blocks(mg_mesh* mesh, int min_blocks);
 
+/* Gather ring of the row kernels of a kernel kind (kind = -1: all kinds):
+ * depth 4 or 8 makes every lane copy the float4s it needs of the neighbour
+ * rows depth - 1 stiffness entries ahead into its own slots of a
+ * shared-memory ring (16-byte cp.async through L1, one commit group per
+ * entry) and read each back once it has landed, so several gathers per
+ * lane are in flight without holding registers; 0 (default) gathers with
+ * plain loads, one neighbour at a time.  Same arithmetic in the same
+ * order: same results.  A launch shape whose ring exceeds a CTA's shared
+ * memory (two gathered states of 4 float4 per lane at depth 8) fails with
+ * MG_ERR_UNSUPPORTED.  Applies to the row kernels only (not to tiles or
+ * the bulk-copy forward).  Drops the cached graphs.  Errors: MG_ERR_ARG
+ * for other values. */
+int mg_mesh_set_gather_ring(mg_mesh* mesh, int kind, int depth);
+
+/* Row sweep of the forward row kernel: blocks > 1 makes each CTA advance
+ * `blocks` consecutive row blocks (256 threads' rows each) one after
+ * another instead of one, with a grid that many times smaller, so that the
+ * neighbour rows a block shares with the next are still in the SM's L1.
+ * 0 or 1 (default): one row block per CTA.  Same arithmetic: same results.
+ * Drops the cached graphs.  Errors: MG_ERR_ARG outside 0..65536. */
+int mg_mesh_set_row_sweep(mg_mesh* mesh, int blocks);
+/* The forward row sweep (>= 0), or MG_ERR_ARG for a null handle. */
+int mg_mesh_get_row_sweep(const mg_mesh* mesh);
+
+/* Gather ring depth of the forward, tangent and adjoint kinds into out[3]. */
+int mg_mesh_get_gather_ring(const mg_mesh* mesh, int32_t* out);
+
 /* Forward step with the neighbour rows of each warp staged in shared
  * memory by bulk asynchronous copies (cp.async.bulk on an mbarrier) instead
  * of per-lane loads: same arithmetic and bits, more bytes in flight per
@@ -356,7 +383,11 @@ int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
  * returns it in chosen[17] (may be NULL).  Candidates: row kernels with 1,
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
  * per pass; for the forward also the 2- and 4-vector row kernels with the
- * register cap of mg_mesh_set_min_blocks; then 2, 4 and 8 shot groups on
+ * register cap of mg_mesh_set_min_blocks; row kernels with 1, 2 or 4 float4
+ * per lane and a gather ring of 4 or 8 slots (mg_mesh_set_gather_ring; the
+ * chosen depths are read with mg_mesh_get_gather_ring); for the forward the
+ * row kernels with 1 vector per lane, and with 2 and 4 under the register
+ * cap, sweeping 4 row blocks per CTA (mg_mesh_get_row_sweep); then 2, 4 and 8 shot groups on
  * the two fastest of those.  Each
  * candidate is timed as the best of three runs after the GPU has been
  * warmed up; shapes within 1% of the fastest count as equal (the earliest

@@ -88,6 +88,10 @@ SIGNATURES = {
     "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_set_conductivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_mesh_set_min_blocks": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_gather_ring": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_mesh_get_gather_ring": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mg_mesh_set_row_sweep": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_get_row_sweep": (C.c_int, [C.c_void_p]),
     "mg_mesh_set_bulk_copies": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_dependent_launch": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_cache_hints": (C.c_int, [C.c_void_p, C.c_int]),

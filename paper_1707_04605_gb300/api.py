@@ -143,6 +143,19 @@ class Mesh:
             rc = self._lib.mg_mesh_set_conductivity(self.handle, ps, None, L.MG_HOST_PTRS)
         L.check(rc, "mg_mesh_set_conductivity")
 
+    def set_gather_ring(self, depth: int, kind=None):
+        """Gather ring of the row kernels (mg_mesh_set_gather_ring): depth 0,
+        4 or 8 for one kind ("forward", "tangent", "adjoint") or all (None)."""
+        k = -1 if kind is None else self.KINDS[kind]
+        L.check(self._lib.mg_mesh_set_gather_ring(self.handle, int(k), int(depth)),
+                "mg_mesh_set_gather_ring")
+
+    def set_row_sweep(self, blocks: int):
+        """Consecutive row blocks per CTA of the forward row kernel
+        (mg_mesh_set_row_sweep); 0 or 1: one."""
+        L.check(self._lib.mg_mesh_set_row_sweep(self.handle, int(blocks)),
+                "mg_mesh_set_row_sweep")
+
     def set_min_blocks(self, min_blocks: int):
         """Register cap of the forward row kernel (mg_mesh_set_min_blocks): 0 or 5."""
         L.check(self._lib.mg_mesh_set_min_blocks(self.handle, int(min_blocks)),
@@ -185,6 +198,12 @@ class Mesh:
                        "src_tile": int(out[3 + 5 * k]), "groups": int(out[4 + 5 * k]),
                        "min_blocks": int(out[5 + 5 * k])}
         d["forward"]["bulk"] = int(out[16])
+        ring = np.zeros(3, dtype=np.int32)
+        L.check(self._lib.mg_mesh_get_gather_ring(self.handle, C.c_void_p(ring.ctypes.data)),
+                "mg_mesh_get_gather_ring")
+        for name, k in self.KINDS.items():
+            d[name]["ring"] = int(ring[k])
+        d["forward"]["sweep"] = int(self._lib.mg_mesh_get_row_sweep(self.handle))
         return d
 
     def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,

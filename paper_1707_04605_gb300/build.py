@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmgwave.so")
-SOURCES = ["mesh_host.cpp", "kernels.cu", "kernels_rows.cu", "kernels_tiled.cu",
+SOURCES = ["mesh_host.cpp", "kernels.cu", "kernels_rows.cu", "kernels_ring.cu", "kernels_tiled.cu",
            "kernels_bulk.cu", "capi.cu",
            "static_scratch.cu", "batch.cu", "projected.cu",
            "inversion.cu", "approx.cu", "mixed.cu"]

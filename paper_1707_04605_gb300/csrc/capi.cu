@@ -116,6 +116,8 @@ struct mg_mesh {
     int groups = 1;
     int min_blocks = 0;   // forward row kernel: 0, or 5 resident CTAs per SM
     int bulk = 0;         // forward: neighbour rows staged by bulk async copies
+    int ring = 0;         // row kernels: gather ring of 4 or 8 slots per lane, 0 = plain loads
+    int sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
@@ -416,6 +418,8 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   mg::StepArgs b = a;
   b.batch = M->tune[0].batch;
   b.min_blocks = M->tune[0].min_blocks;
+  b.ring = M->tune[0].ring;
+  b.sweep = M->tune[0].sweep;
   b.pdl = M->dep_launch;
   if (M->tune[0].bulk) {
     int* err = err_word(M);
@@ -430,6 +434,7 @@ int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st)
   if (T.n_tiles) return mg::launch_tangent_tiled(a, T, st);
   mg::TangentArgs b = a;
   b.f.batch = M->tune[1].batch;
+  b.f.ring = M->tune[1].ring;
   b.f.pdl = M->dep_launch;
   return mg::launch_tangent(b, S_pad, st);
 }
@@ -439,6 +444,7 @@ int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st)
   if (T.n_tiles) return mg::launch_adjoint_tiled(a, T, st);
   mg::AdjointArgs b = a;
   b.batch = M->tune[2].batch;
+  b.ring = M->tune[2].ring;
   b.pdl = M->dep_launch;
   return mg::launch_adjoint(b, S_pad, st);
 }
@@ -933,6 +939,29 @@ int mg_mesh_device_status(mg_mesh* M) {
   return word == 0 ? MG_OK : word == 1 ? MG_ERR_TIMEOUT : MG_ERR_ARG;
 }
 
+int mg_mesh_set_gather_ring(mg_mesh* M, int kind, int depth) {
+  if (!M || kind < -1 || kind > 2 || (depth != 0 && depth != 4 && depth != 8)) return MG_ERR_ARG;
+  drop_graphs(M);
+  for (int k = 0; k < 3; ++k)
+    if (kind == -1 || kind == k) M->tune[k].ring = depth;
+  return MG_OK;
+}
+
+int mg_mesh_set_row_sweep(mg_mesh* M, int blocks) {
+  if (!M || blocks < 0 || blocks > 65536) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->tune[0].sweep = blocks;
+  return MG_OK;
+}
+
+int mg_mesh_get_row_sweep(const mg_mesh* M) { return M ? M->tune[0].sweep : MG_ERR_ARG; }
+
+int mg_mesh_get_gather_ring(const mg_mesh* M, int32_t* out) {
+  if (!M || !out) return MG_ERR_ARG;
+  for (int k = 0; k < 3; ++k) out[k] = M->tune[k].ring;
+  return MG_OK;
+}
+
 int mg_mesh_set_min_blocks(mg_mesh* M, int min_blocks) {
   if (!M || (min_blocks != 0 && min_blocks != 5)) return MG_ERR_ARG;
   drop_graphs(M);
@@ -1101,6 +1130,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
     if (!kept) return MG_ERR_ARG;
     float* seg = P<float>(M->seg);
     a.f.batch = M->tune[1].batch;
+    a.f.ring = M->tune[1].ring;
     a.f.pdl = M->dep_launch;
     a.f.hint = M->cache_hints;
     const int W = group_cols(M, 1, pp.S_pad), NG = pp.S_pad / W;
@@ -1248,6 +1278,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
   a.f = step_args(M, pp, pp.S_pad, nt);
   a.f.traces = trf;
   a.f.batch = M->tune[1].batch;
+  a.f.ring = M->tune[1].ring;
   a.f.pdl = M->dep_launch;
   a.f.hint = keep ? M->cache_hints : 0;   // p_{l-1} is last read here only when kept
   a.tcoef = P<const float2>(M->tcoef);
@@ -1382,6 +1413,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.nt = nt;
   aa.step_base = nullptr;
   aa.batch = M->tune[2].batch;
+  aa.ring = M->tune[2].ring;
   aa.G = G;
   aa.Gc = G + acc;
   aa.H = G + 2 * acc;
@@ -1540,12 +1572,19 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
                                           stream, flags);
     }
   };
-  // the last two (a register cap for 5 CTAs per SM) apply to the forward
-  // only; the bulk-copy kernel is not a candidate (measured slower on every
-  // workload: 2D 41.6 vs 19.7 us, 3D 769 vs 532 us per step)
-  const mg_mesh::Tuning shapes[] = {{1, 0, 32},   {2, 0, 32},   {4, 0, 32},   {1, 64, 32},
-                                    {1, 64, 16},  {1, 128, 32}, {1, 128, 16}, {1, 256, 32},
-                                    {1, 256, 16}, {2, 0, 32, 1, 5}, {4, 0, 32, 1, 5}};
+  // the register-capped shapes (5 CTAs per SM) and the row sweeps of 4
+  // blocks per CTA (mg_mesh_set_row_sweep) apply to the forward only;
+  // the row kernels with a gather ring of 4 or 8 slots to every kind (a
+  // ring that exceeds a CTA's shared memory is skipped); the bulk-copy
+  // kernel is not a candidate (measured slower on every workload: 2D 41.6
+  // vs 19.7 us, 3D 769 vs 532 us per step)
+  const mg_mesh::Tuning shapes[] = {
+      {1, 0, 32},          {2, 0, 32},          {4, 0, 32},          {1, 64, 32},
+      {1, 64, 16},         {1, 128, 32},        {1, 128, 16},        {1, 256, 32},
+      {1, 256, 16},        {2, 0, 32, 1, 5},    {4, 0, 32, 1, 5},    {1, 0, 32, 1, 0, 0, 4},
+      {2, 0, 32, 1, 0, 0, 4}, {4, 0, 32, 1, 0, 0, 4}, {1, 0, 32, 1, 0, 0, 8},
+      {2, 0, 32, 1, 0, 0, 8}, {4, 0, 32, 1, 0, 0, 8}, {1, 0, 32, 1, 0, 0, 0, 4},
+      {2, 0, 32, 1, 5, 0, 0, 4}, {4, 0, 32, 1, 5, 0, 0, 4}};
   const int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
   cudaEvent_t e0, e1;
   MG_CU(cudaEventCreate(&e0));
@@ -1571,7 +1610,7 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
       cand = std::min(cand, ms);
     }
     *out = cand;
-    return r;
+    return r == MG_ERR_UNSUPPORTED ? MG_OK : r;   // a ring too large for the shape: skipped
   };
   for (int kind = 0; kind < 3 && rc == MG_OK; ++kind) {
     // launch shapes with one shot group, then 2, 4 and 8 groups on the two
@@ -1579,7 +1618,7 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
     float ms[n_shapes];
     for (int i = 0; i < n_shapes && rc == MG_OK; ++i) {
       ms[i] = 1e30f;
-      if ((shapes[i].min_blocks || shapes[i].bulk) && kind != 0) continue;
+      if ((shapes[i].min_blocks || shapes[i].bulk || shapes[i].sweep) && kind != 0) continue;
       rc = time_of(kind, shapes[i], &ms[i]);
     }
     if (rc != MG_OK) break;

@@ -47,6 +47,8 @@ struct StepArgs {
   int32_t cols = 0;         // shot columns advanced, [col0, col0 + cols); 0 = all ld
   int32_t pdl = 0;          // row kernels: launch dependent on the previous kernel
   int32_t hint = 0;         // row kernels: L2 evict-first on the last read of pm
+  int32_t ring = 0;         // row kernels: gather ring of 4 or 8 slots per lane (0 = plain loads)
+  int32_t sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -80,6 +82,7 @@ struct AdjointArgs {
   int32_t cols = 0;
   int32_t pdl = 0;          // as in StepArgs
   int32_t hint = 0;         // row kernel: L2 evict-first on the read of pk
+  int32_t ring = 0;         // row kernel: gather ring depth as in StepArgs
   float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;
@@ -128,6 +131,14 @@ int launch_step_bulk(const StepArgs& a, int S_pad, int* err, cudaStream_t st);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);
 int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st);
 int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st);
+// The same with the neighbour gathers pipelined through a shared-memory
+// ring (kernels_ring.cu; called by the launchers above when ring > 0).
+// MG_ERR_UNSUPPORTED when the ring of the launch shape exceeds a CTA's
+// shared memory.
+int launch_step_ring(const StepArgs& a, int S_pad, cudaStream_t st);
+int launch_tangent_ring(const TangentArgs& a, int S_pad, cudaStream_t st);
+int launch_tangent_kept_ring(const TangentArgs& a, int S_pad, cudaStream_t st);
+int launch_adjoint_ring(const AdjointArgs& a, int S_pad, cudaStream_t st);
 
 // Coefficients from eps (FP64 arithmetic, FP32 storage).
 struct CoefArgs {

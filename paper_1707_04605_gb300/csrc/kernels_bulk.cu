@@ -222,7 +222,7 @@ int launch_step_bulk(const StepArgs& a, int S_pad, int* err, cudaStream_t st) {
   int lpr = 0;
   for (;; nv >>= 1) {
     lpr = cols / (4 * nv) >= 32 ? 32 : cols / (4 * nv);
-    if (nv == 1 || (lpr >= 1 && cols % (4 * nv * lpr) == 0)) break;
+    if (nv == 1 || (lpr >= 1 && (lpr & (lpr - 1)) == 0 && cols % (4 * nv * lpr) == 0)) break;
   }
   const int tw = 4 * nv * lpr;
   if (lpr < 1 || a.col0 < 0 || a.col0 % tw || cols % tw || a.col0 + cols > a.ld || !err)

@@ -390,7 +390,8 @@ def test_wide_batch_row_shapes_cover_every_shot(mg):
 
 @pytest.mark.parametrize("batch", [1, 2, 4])
 def test_register_capped_forward_gives_identical_results(mg, batch):
-    """mg_mesh_set_min_blocks(5) only changes register allocation: same bits."""
+    """mg_mesh_set_min_blocks(5) only changes register allocation, and
+    mg_mesh_set_row_sweep only which CTA advances which rows: same bits."""
     w = configs.asteroid_2d(n_refine=1, S=100, nt=300)
     eps = _dev(w.eps)
     mesh = mg.mesh_from_workload(w)
@@ -409,6 +410,12 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     out = run()
     assert torch.equal(ref[0], out[0])
     assert torch.equal(ref[1], out[1])
+    # consecutive row blocks per CTA (a ragged last sweep included)
+    for sweep in (3, 7):
+        mesh.set_row_sweep(sweep)
+        out = run()
+        assert torch.equal(ref[0], out[0])
+        assert torch.equal(ref[1], out[1])
 
 
 @pytest.mark.parametrize("S,batch,groups,chunk", [(100, 2, 1, 128), (100, 1, 2, 128),
@@ -562,3 +569,62 @@ def test_jacobian_square_disc_2d(mg):
     g = mg.jacobian_T_apply(mesh, level, _dev(w.eps), w.shots, _dev(s), dt,
                             _dev(W, torch.float32), ckpt_every=256).cpu().numpy()
     assert rel_l2(g, oracle_gradient(w, dt, s, w.shots, W.astype(np.float64), level)) < JAC_TOL
+
+
+@pytest.mark.parametrize("S,batch,depth", [(100, 2, 4), (100, 1, 8), (37, 4, 4), (300, 2, 8),
+                                           (6, 1, 4), (64, 2, 8)])
+def test_gather_ring_gives_identical_results(mg, S, batch, depth):
+    """Neighbour gathers pipelined through the shared-memory ring do the
+    plain gathers' FMAs in the same order: the forward (kept history and
+    checkpoints), the lockstep and fused tangents, the tangent on kept
+    states and both J^T w paths carry the same bits."""
+    w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(-1, batch, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    rng = np.random.default_rng(10)
+    W = _dev(rng.standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    v = _dev(rng.standard_normal(w.mesh.n_cells[1]))
+
+    def run():
+        y = mg.forward(mesh, eps, w.shots, s, dt, keep_states=True)
+        gk = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
+                                 reuse_checkpoints=True)
+        jvk = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, reuse_states=True)
+        jv = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
+        yf, jvf = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
+        g = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+        return y, gk, jvk, jv, yf, jvf, g
+
+    ref = run()
+    mesh.set_gather_ring(depth)
+    assert all(mesh.tuning()[k]["ring"] == depth for k in ("forward", "tangent", "adjoint"))
+    out = run()
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+    mesh.set_gather_ring(0)
+    for a, b in zip(ref, run()):
+        assert torch.equal(a, b)
+
+
+def test_gather_ring_too_large_is_refused(mg):
+    """Two gathered states of four float4 per lane at depth 8 need more
+    shared memory than a CTA has: the lockstep tangent is refused with
+    MG_ERR_UNSUPPORTED while the forward with the same ring runs."""
+    from paper_1707_04605_gb300 import _lib as L
+
+    w = configs.asteroid_2d(n_refine=1, S=128, nt=40)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(0, 4, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    v = _dev(np.random.default_rng(11).standard_normal(w.mesh.n_cells[1]))
+    ref = mg.forward(mesh, eps, w.shots, s, dt)
+    mesh.set_gather_ring(8)
+    assert torch.equal(mg.forward(mesh, eps, w.shots, s, dt), ref)
+    with pytest.raises(L.MgError) as e:
+        mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
+    assert e.value.code == L.MG_ERR_UNSUPPORTED
