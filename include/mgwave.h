@@ -76,7 +76,8 @@ extern "C" {
 #define MG_HOST_PTRS        0x01  /* data pointers are host memory          */
 #define MG_SINGLE_SOURCE    0x02  /* run the plain one-shot-at-a-time path   */
 #define MG_NO_GRAPH         0x04  /* plain launches, no CUDA graph           */
-#define MG_PERSISTENT       0x08  /* multi-step persistent launch            */
+#define MG_PERSISTENT       0x08  /* mg_forward: several steps per cooperative
+                                     launch (mg_mesh_set_persistent)          */
 #define MG_ALLOW_CFL        0x10  /* do not reject dt above the CFL bound    */
 #define MG_KEEP_CHECKPOINTS 0x20  /* mg_forward: keep (p_l, p_{l-1}) every
                                      ckpt_every steps in the handle for a
@@ -165,7 +166,11 @@ int mg_cfl_dt(mg_mesh* mesh, const double* eps, int flags, void* stream,
  *  traces   data, [rec_ptr[n_shots]][nt] float32 output
  *  ckpt_every  checkpoint spacing when MG_KEEP_CHECKPOINTS is set (>0)
  * All shots advance together in one node-major FP32 state (sources in the
- * fast dimension); MG_SINGLE_SOURCE runs them one at a time instead. */
+ * fast dimension); MG_SINGLE_SOURCE runs them one at a time instead;
+ * MG_PERSISTENT runs several steps per cooperative launch
+ * (mg_mesh_set_persistent).  Flags: MG_HOST_PTRS, MG_NO_GRAPH,
+ * MG_ALLOW_CFL, MG_SINGLE_SOURCE, MG_PERSISTENT, MG_KEEP_CHECKPOINTS,
+ * MG_KEEP_STATES; any other bit is MG_ERR_UNSUPPORTED. */
 int mg_forward(mg_mesh* mesh, const double* eps, const mg_shots* shots,
                const double* wavelet, double dt, int nt, float* traces,
                int ckpt_every, void* stream, int flags);
@@ -323,6 +328,27 @@ int mg_mesh_set_gather_ring(mg_mesh* mesh, int kind, int depth);
 int mg_mesh_set_row_sweep(mg_mesh* mesh, int blocks);
 /* The forward row sweep (>= 0), or MG_ERR_ARG for a null handle. */
 int mg_mesh_get_row_sweep(const mg_mesh* mesh);
+
+/* The multi-step forward (mg_forward with MG_PERSISTENT; App. A, Eqs.
+ * (leap-frog1)-(leap-frog2), the same step as the single-step launches and
+ * the same bits).  One cooperative launch advances `steps` leapfrog steps
+ * (1..2^20, default 128; launches also end at every checkpoint): its CTAs,
+ * all resident (at most the occupancy of the row kernel times the SM
+ * count), sweep the row blocks of a step, then meet at a grid-wide barrier
+ * before the next step.  A barrier wait is bounded by `wait_cycles` SM
+ * clock cycles (>= 1000, default 2^31, about a second): a CTA that waits
+ * longer, or that sees another CTA give up, records the time-out in the
+ * handle's status word and leaves; mg_forward then synchronises with the
+ * stream, clears the word and returns MG_ERR_TIMEOUT (its traces are
+ * incomplete).  `extra_arrivals` (0..2^20; 0 in normal use) makes every
+ * barrier wait for that many CTAs beyond the grid, which never arrive: it
+ * exists to exercise the time-out path.  MG_PERSISTENT applies to
+ * mg_forward only, without MG_SINGLE_SOURCE or MG_KEEP_STATES
+ * (MG_ERR_UNSUPPORTED), uses the row kernel with the handle's float4 per
+ * lane whatever the other tuning says, one shot group, no CUDA graph, and
+ * ends with a stream synchronisation.  Errors: MG_ERR_ARG outside the
+ * ranges above. */
+int mg_mesh_set_persistent(mg_mesh* mesh, int steps, long long wait_cycles, int extra_arrivals);
 
 /* Gather ring depth of the forward, tangent and adjoint kinds into out[3]. */
 int mg_mesh_get_gather_ring(const mg_mesh* mesh, int32_t* out);

@@ -156,6 +156,14 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_row_sweep(self.handle, int(blocks)),
                 "mg_mesh_set_row_sweep")
 
+    def set_persistent(self, steps: int = 128, wait_cycles: int = 1 << 31,
+                       extra_arrivals: int = 0):
+        """Steps per cooperative launch of the MG_PERSISTENT forward, the SM
+        clock cycles one grid-barrier wait may take, and (tests only) barrier
+        arrivals awaited beyond the grid (mg_mesh_set_persistent)."""
+        L.check(self._lib.mg_mesh_set_persistent(self.handle, int(steps), int(wait_cycles),
+                                                 int(extra_arrivals)), "mg_mesh_set_persistent")
+
     def set_min_blocks(self, min_blocks: int):
         """Register cap of the forward row kernel (mg_mesh_set_min_blocks): 0 or 5."""
         L.check(self._lib.mg_mesh_set_min_blocks(self.handle, int(min_blocks)),
@@ -293,11 +301,12 @@ def _ptr(x):
 
 def forward(mesh: Mesh, eps, shots, wavelet, dt, nt=None, *, ckpt_every=0,
             keep_checkpoints=False, keep_states=False, single_source=False, allow_cfl=False,
-            stream=None, flags=0):
+            persistent=False, stream=None, flags=0):
     """Traces [n_traces, nt] float32 of mg_forward.  keep_states keeps every
     state in the handle (MG_KEEP_STATES; (nt + 2) n S_pad floats), so that
     jacobian_T_apply(..., ckpt_every=nt, reuse_checkpoints=True) runs no
-    recompute."""
+    recompute.  persistent runs several steps per cooperative launch
+    (MG_PERSISTENT; see Mesh.set_persistent)."""
     lib = L.load()
     sh = Shots.of(shots)
     nt = int(len(wavelet) if nt is None else nt)
@@ -312,6 +321,8 @@ def forward(mesh: Mesh, eps, shots, wavelet, dt, nt=None, *, ckpt_every=0,
         f |= L.MG_SINGLE_SOURCE
     if allow_cfl:
         f |= L.MG_ALLOW_CFL
+    if persistent:
+        f |= L.MG_PERSISTENT
     rc = lib.mg_forward(mesh.handle, pe, C.byref(sh.c), pw, float(dt), nt, _ptr(out),
                         int(ckpt_every), st, f)
     L.check(rc, "mg_forward")

@@ -124,7 +124,11 @@ struct mg_mesh {
   int wu = 0;
   bool uniform_ell = false;
   int cache_hints = 1;                    // kept history: L2 evict-first on last reads
-  Buf errbuf;                             // device status word of bounded waits
+  Buf errbuf;                             // device status word of bounded waits, then the
+                                          // persistent forward's barrier counter
+  int persist_steps = 128;                // MG_PERSISTENT: steps per cooperative launch
+  long long persist_budget = 1LL << 31;   // SM clock cycles one barrier wait may take
+  int persist_extra = 0;                  // barrier arrivals awaited beyond the grid (tests)
   struct TileTables {
     Buf ell_off, ell_idx, ell_val, sinfo, halo_off, halo_cnt, halo;
     int n_tiles = 0, max_ell = 0, max_halo = 0;
@@ -273,6 +277,9 @@ int deliver(Buf& b, void* dst, size_t bytes, int flags, cudaStream_t st) {
   if (!host) return MG_OK;
   return cudaStreamSynchronize(st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
+
+// Flags every propagation call accepts; each adds its own.
+constexpr int kCommonFlags = MG_HOST_PTRS | MG_NO_GRAPH | MG_ALLOW_CFL;
 
 #define MG_TRY(x) do { int _rc = (x); if (_rc != MG_OK) return _rc; } while (0)
 #define MG_CU(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); return MG_ERR_CUDA; } } while (0)
@@ -527,6 +534,38 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
   mg::StepArgs a = step_args(M, pp, pp.S_pad, nt);
   a.traces = traces;
   int l = 0;
+  if (flags & MG_PERSISTENT) {
+    // several steps per cooperative launch, ending at every checkpoint; the
+    // status word is cleared first (a stale time-out would stop the barrier)
+    int* status = err_word(M);
+    if (!status) return MG_ERR_OOM;
+    MG_CU(cudaMemsetAsync(status, 0, sizeof(int), st));
+    mg::PersistArgs pa{};
+    pa.count = reinterpret_cast<unsigned*>(status + 1);
+    pa.status = status;
+    pa.budget = M->persist_budget;
+    pa.extra = M->persist_extra;
+    while (l < nt) {
+      if (ckpt && l % ckpt_every == 0) {
+        float* slot = ckpt + (size_t)(l / ckpt_every) * 2 * state;
+        MG_TRY(mg::launch_copy_f4(p, slot, (int64_t)state, st));
+        MG_TRY(mg::launch_copy_f4(pm, slot + state, (int64_t)state, st));
+        M->launches += 2;
+      }
+      int end = std::min(nt, l + M->persist_steps);
+      if (ckpt) end = std::min(end, (l / ckpt_every + 1) * ckpt_every);
+      a.p = p;
+      a.pm = pm;
+      a.pout = pm;
+      a.step = l;
+      pa.steps = end - l;
+      MG_TRY(mg::launch_step_persist(a, pp.S_pad, pa, st));
+      M->launches += 1;
+      if ((end - l) % 2) std::swap(p, pm);
+      l = end;
+    }
+    return MG_OK;
+  }
   const int C = M->chunk;
   if (graphs_on(M, flags) && nt >= C && (!ckpt || ckpt_every % C == 0)) {
     MG_TRY(ensure(M->step_base, 16));
@@ -956,6 +995,16 @@ int mg_mesh_set_row_sweep(mg_mesh* M, int blocks) {
 
 int mg_mesh_get_row_sweep(const mg_mesh* M) { return M ? M->tune[0].sweep : MG_ERR_ARG; }
 
+int mg_mesh_set_persistent(mg_mesh* M, int steps, long long wait_cycles, int extra_arrivals) {
+  if (!M || steps < 1 || steps > (1 << 20) || wait_cycles < 1000 || extra_arrivals < 0 ||
+      extra_arrivals > (1 << 20))
+    return MG_ERR_ARG;
+  M->persist_steps = steps;
+  M->persist_budget = wait_cycles;
+  M->persist_extra = extra_arrivals;
+  return MG_OK;
+}
+
 int mg_mesh_get_gather_ring(const mg_mesh* M, int32_t* out) {
   if (!M || !out) return MG_ERR_ARG;
   for (int k = 0; k < 3; ++k) out[k] = M->tune[k].ring;
@@ -1032,10 +1081,15 @@ int mg_cfl_dt(mg_mesh* M, const double* eps, int flags, void* stream, double* dt
 int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const double* wavelet,
                double dt, int nt, float* traces, int ckpt_every, void* stream, int flags) {
   if (!M || !traces) return MG_ERR_ARG;
+  if (flags & ~(kCommonFlags | MG_SINGLE_SOURCE | MG_PERSISTENT | MG_KEEP_CHECKPOINTS |
+                MG_KEEP_STATES))
+    return MG_ERR_UNSUPPORTED;
   if ((flags & MG_KEEP_CHECKPOINTS) && (ckpt_every < 1 || (flags & MG_SINGLE_SOURCE)))
     return MG_ERR_ARG;
   if ((flags & MG_KEEP_STATES) && (flags & (MG_KEEP_CHECKPOINTS | MG_SINGLE_SOURCE)))
     return MG_ERR_ARG;
+  if ((flags & MG_PERSISTENT) && (flags & (MG_SINGLE_SOURCE | MG_KEEP_STATES)))
+    return MG_ERR_UNSUPPORTED;
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1070,6 +1124,16 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
       ck = P<float>(M->ckpt);
     }
     MG_TRY(run_forward(M, pp, nt, tr, ckpt_every, ck, st, flags));
+    if (flags & MG_PERSISTENT) {
+      // the barrier waits are bounded: read (and clear) the status word
+      int word = 0;
+      MG_CU(cudaMemcpyAsync(&word, M->errbuf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      MG_CU(cudaStreamSynchronize(st));
+      if (word != 0) {
+        MG_CU(cudaMemset(M->errbuf.p, 0, sizeof(int)));
+        return MG_ERR_TIMEOUT;
+      }
+    }
     if (ck) {
       M->ck_valid = true;
       M->ck_every = ckpt_every;
@@ -1088,7 +1152,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
                       void* stream, int flags) {
   if (!M || !v || !jv) return MG_ERR_ARG;
   if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
-  if (flags & MG_SINGLE_SOURCE) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(kCommonFlags | MG_REUSE_CHECKPOINTS)) return MG_ERR_UNSUPPORTED;
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1228,8 +1292,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
                               float* traces, float* jv, void* stream, int flags) {
   if (!M || !v || !jv || !traces) return MG_ERR_ARG;
   if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
-  if (flags & (MG_SINGLE_SOURCE | MG_KEEP_CHECKPOINTS | MG_REUSE_CHECKPOINTS))
-    return MG_ERR_UNSUPPORTED;
+  if (flags & ~(kCommonFlags | MG_KEEP_STATES)) return MG_ERR_UNSUPPORTED;
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1347,7 +1410,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
                         int ckpt_every, void* stream, int flags) {
   if (!M || !w || !g || ckpt_every < 1) return MG_ERR_ARG;
   if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
-  if (flags & MG_SINGLE_SOURCE) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(kCommonFlags | MG_REUSE_CHECKPOINTS)) return MG_ERR_UNSUPPORTED;
   DeviceGuard guard(M->device);
   if (!guard.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

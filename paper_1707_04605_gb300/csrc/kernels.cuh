@@ -131,6 +131,24 @@ int launch_step_bulk(const StepArgs& a, int S_pad, int* err, cudaStream_t st);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);
 int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st);
 int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st);
+// Several forward steps in one cooperative launch (kernels_rows.cu): every
+// CTA advances its row blocks (grid-stride) for step l, then all CTAs meet
+// at a grid-wide barrier before step l + 1.  The barrier's wait is bounded:
+// after `budget` SM clock cycles, or once another CTA has given up, a CTA
+// sets *status = 1 and returns (the launch then ends without finishing its
+// steps).  `extra` > 0 makes every barrier wait for arrivals that never
+// come (tests of the time-out path); 0 otherwise.
+struct PersistArgs {
+  int32_t steps;            // leapfrog steps of the launch (a.step is the first)
+  unsigned* count;          // barrier counter, zeroed by the launcher on the stream
+  int* status;              // the handle's status word
+  long long budget;         // SM clock cycles one barrier wait may take
+  int32_t extra;            // arrivals awaited beyond the grid's CTAs
+};
+// a.pout must equal a.pm (in-place update).  MG_ERR_UNSUPPORTED when the
+// device cannot hold the launch's source tiles as co-resident CTAs.
+int launch_step_persist(const StepArgs& a, int S_pad, const PersistArgs& pa, cudaStream_t st);
+
 // The same with the neighbour gathers pipelined through a shared-memory
 // ring (kernels_ring.cu; called by the launchers above when ring > 0).
 // MG_ERR_UNSUPPORTED when the ring of the launch shape exceeds a CTA's

@@ -1,11 +1,115 @@
 // Launchers of the row kernels (rows_common.cuh) with plain neighbour
 // gathers; a launch that asks for the gather ring (a.ring / a.f.ring > 0)
-// goes to kernels_ring.cu.
+// goes to kernels_ring.cu.  Also the multi-step cooperative forward.
+#include <algorithm>
+
 #include "rows_common.cuh"
 
 namespace mg {
+namespace {
+
+// Grid-wide barrier of a cooperative launch: thread 0 of every CTA adds one
+// to *count (after a fence that publishes the CTA's stores) and polls it with
+// acquire loads until it reaches `target`.  Bounded: past `budget` SM clock
+// cycles, or when *status shows that another CTA gave up, the CTA sets
+// *status = 1 and every thread of it gets false.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* status,
+                                             long long budget) {
+  __syncthreads();
+  int fail = 0;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (*reinterpret_cast<volatile int*>(status) != 0) { fail = 1; break; }
+      if (clock64() - t0 > budget) {
+        atomicExch(status, 1);
+        fail = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  return __syncthreads_or(fail) == 0;
+}
+
+// pa.steps forward steps from a.step: states x (p_l) and y (p_{l-1}, then
+// p_{l+1}) swap roles after every step, as in the stream of single-step
+// launches, and every step is the same block computation (same bits).
+template <int LPR, int NV>
+__global__ void __launch_bounds__(kThreads) k_step_persist(StepArgs a, PersistArgs pa) {
+  constexpr int RPB = kWarps * 32 / LPR;
+  const int nblk = (a.K.n + RPB - 1) / RPB;
+  const unsigned nctas = gridDim.x * gridDim.y;
+  const float* x = a.p;
+  float* y = a.pout;
+  StepArgs b = a;
+  for (int j = 0; j < pa.steps; ++j) {
+    b.p = x;
+    b.pm = y;
+    b.pout = y;
+    b.step = a.step + j;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) step_rows_block<LPR, NV, 0>(b, blk);
+    if (j + 1 < pa.steps &&
+        !grid_barrier(pa.count, (unsigned)(j + 1) * (nctas + (unsigned)pa.extra), pa.status,
+                      pa.budget))
+      return;
+    float* t = const_cast<float*>(x);
+    x = y;
+    y = t;
+  }
+}
+
+}  // namespace
 
 int rows_tiles(int cols, int nv) { return (int)shape_of(1, cols, nv).grid.y; }
+
+int launch_step_persist(const StepArgs& a, int S_pad, const PersistArgs& pa, cudaStream_t st) {
+  const int cols = a.cols ? a.cols : S_pad;
+  Shape sh = shape_of(a.K.n, cols, a.batch);
+  if (!range_ok(sh, a.col0, cols, a.ld) || pa.steps < 1 || a.pout != a.pm || !pa.count ||
+      !pa.status || pa.budget < 1 || pa.extra < 0)
+    return MG_ERR_ARG;
+  void (*kern)(StepArgs, PersistArgs) = nullptr;
+  switch (sh.lpr * 8 + sh.nv) {
+#define MG_P(L, V) case L * 8 + V: kern = k_step_persist<L, V>; break;
+    MG_P(32, 1) MG_P(32, 2) MG_P(32, 4) MG_P(16, 1) MG_P(16, 2) MG_P(16, 4)
+    MG_P(8, 1) MG_P(8, 2) MG_P(8, 4) MG_P(4, 1) MG_P(4, 2) MG_P(4, 4)
+    MG_P(2, 1) MG_P(2, 2) MG_P(2, 4) MG_P(1, 1) MG_P(1, 2) MG_P(1, 4)
+#undef MG_P
+    default: return MG_ERR_ARG;
+  }
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  const long resident = (long)occ * nsm;   // every CTA of a cooperative launch is resident
+  if (resident < (long)sh.grid.y) return MG_ERR_UNSUPPORTED;
+  sh.grid.x = (unsigned)std::min<long>(sh.grid.x, resident / sh.grid.y);
+  if (cudaMemsetAsync(pa.count, 0, sizeof(unsigned), st) != cudaSuccess) return MG_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = sh.grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kern, a, pa) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  return check_launch();
+}
 
 int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
   if (a.ring) return launch_step_ring(a, S_pad, st);

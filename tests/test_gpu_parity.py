@@ -628,3 +628,86 @@ def test_gather_ring_too_large_is_refused(mg):
     with pytest.raises(L.MgError) as e:
         mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
     assert e.value.code == L.MG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("make,kw,steps", [
+    (configs.square_disc_2d, {}, 128),
+    (configs.asteroid_2d, dict(n_refine=1, S=100, nt=300), 64),
+    (configs.asteroid_2d, dict(n_refine=1, S=37, nt=301), 7),
+    (configs.tiny_3d, {}, 1000)])
+def test_persistent_forward_gives_the_graph_bits(mg, make, kw, steps):
+    """Several steps per cooperative launch with grid barriers between them
+    (MG_PERSISTENT): each step is the block computation of the single-step
+    launches, so the traces carry the same bits; its checkpoints serve
+    J^T w like those of the graph path."""
+    w = make(**kw)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    ref = mg.forward(mesh, eps, w.shots, s, dt)
+    mesh.set_persistent(steps)
+    n0 = mesh.launch_count()
+    y = mg.forward(mesh, eps, w.shots, s, dt, persistent=True)
+    assert torch.equal(y, ref)
+    assert mesh.launch_count() - n0 < w.nt // steps + 8
+    W = _dev(np.random.default_rng(12).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    g_ref = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+    y2 = mg.forward(mesh, eps, w.shots, s, dt, ckpt_every=64, keep_checkpoints=True,
+                    persistent=True)
+    assert torch.equal(y2, ref)
+    g = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64,
+                            reuse_checkpoints=True)
+    assert torch.equal(g, g_ref)
+
+
+def test_persistent_barrier_wait_times_out_and_reports(mg):
+    """A grid barrier that waits for CTAs which never arrive (a test-only
+    count beyond the grid) gives up after its cycle budget: every CTA leaves,
+    mg_forward returns MG_ERR_TIMEOUT, the status word is cleared and the
+    handle keeps working."""
+    from paper_1707_04605_gb300 import _lib as L
+
+    w = configs.asteroid_2d(n_refine=1, S=12, nt=40)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    ref = mg.forward(mesh, eps, w.shots, s, dt)
+    mesh.set_persistent(16, wait_cycles=200_000, extra_arrivals=1)
+    with pytest.raises(L.MgError) as e:
+        mg.forward(mesh, eps, w.shots, s, dt, persistent=True)
+    assert e.value.code == L.MG_ERR_TIMEOUT
+    assert mesh.device_status() == 0
+    mesh.set_persistent(16)
+    assert torch.equal(mg.forward(mesh, eps, w.shots, s, dt, persistent=True), ref)
+    assert torch.equal(mg.forward(mesh, eps, w.shots, s, dt), ref)
+
+
+def test_unknown_and_unsupported_flags_are_refused(mg):
+    from paper_1707_04605_gb300 import _lib as L
+
+    w = configs.tiny_2d()
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    v = _dev(np.ones(w.mesh.n_cells[1]))
+    W = _dev(np.ones((w.shots.n_traces, w.nt)), torch.float32)
+    calls = [
+        lambda f: mg.forward(mesh, eps, w.shots, s, dt, flags=f),
+        lambda f: mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, flags=f),
+        lambda f: mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=32, flags=f),
+    ]
+    for call in calls:
+        for f in (0x100, 0x4000):
+            with pytest.raises(L.MgError) as e:
+                call(f)
+            assert e.value.code == L.MG_ERR_UNSUPPORTED
+    for call in calls[1:]:
+        with pytest.raises(L.MgError) as e:
+            call(L.MG_PERSISTENT)
+        assert e.value.code == L.MG_ERR_UNSUPPORTED
+    with pytest.raises(L.MgError) as e:
+        mg.forward(mesh, eps, w.shots, s, dt, persistent=True, keep_states=True)
+    assert e.value.code == L.MG_ERR_UNSUPPORTED
