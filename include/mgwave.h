@@ -193,9 +193,10 @@ int mg_forward(mg_mesh* mesh, const double* eps, const mg_shots* shots,
  *    its 14 parts (S_pad = shot count rounded up to a power of two >= 4, or
  *    to a multiple of 128 above 128), must fit in 64 MiB; larger work
  *    returns MG_ERR_ARG before anything runs.
- *  - The first call on a device looks up the array's device address on that
- *    device (cudaGetSymbolAddress); make that first call before any stream
- *    capture is started.
+ *  - The array is reserved on a device, and its device address looked up
+ *    there (cudaGetSymbolAddress), by mg_mesh_create on that device (a call
+ *    that allocates anyway): the 64 MiB are taken then, even if this entry
+ *    point is never called, and the call itself reserves no memory.
  *  - Every call on a device shares the one array, which keeps the previous
  *    call's contents (the call clears what must start at zero).  Calls whose
  *    work overlaps on the GPU (other streams, other threads, other handles)
@@ -328,6 +329,17 @@ int mg_mesh_set_gather_ring(mg_mesh* mesh, int kind, int depth);
 int mg_mesh_set_row_sweep(mg_mesh* mesh, int blocks);
 /* The forward row sweep (>= 0), or MG_ERR_ARG for a null handle. */
 int mg_mesh_get_row_sweep(const mg_mesh* mesh);
+
+/* Generation of the handle's checkpoints and kept forward states: a count
+ * (>= 0) that changes whenever a call writes, drops or invalidates them
+ * (mg_forward, mg_forward_jacobian_apply, mg_jacobian_T_apply without
+ * MG_REUSE_CHECKPOINTS, the batch calls, mg_mesh_trim, a conductivity
+ * change).  A caller that keeps checkpoints for a later
+ * mg_jacobian_T_apply with MG_REUSE_CHECKPOINTS records the generation
+ * after its forward and asks for reuse only while it is unchanged: the
+ * reuse check compares sizes, dt and shots, not the permittivity or the
+ * wavelet.  MG_ERR_ARG for a null handle. */
+int64_t mg_mesh_checkpoint_generation(const mg_mesh* mesh);
 
 /* The multi-step forward (mg_forward with MG_PERSISTENT; App. A, Eqs.
  * (leap-frog1)-(leap-frog2), the same step as the single-step launches and

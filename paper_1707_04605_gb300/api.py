@@ -113,6 +113,11 @@ class Mesh:
     def trim(self):
         L.check(self._lib.mg_mesh_trim(self.handle), "mg_mesh_trim")
 
+    def checkpoint_generation(self) -> int:
+        """mg_mesh_checkpoint_generation: changes whenever the handle's
+        checkpoints or kept states are written or dropped."""
+        return int(self._lib.mg_mesh_checkpoint_generation(self.handle))
+
     def launch_count(self) -> int:
         return int(self._lib.mg_launch_count(self.handle))
 

@@ -102,6 +102,7 @@ struct mg_mesh {
   int ck_every = 0, ck_nt = 0, ck_S_pad = 0, ck_nshots = 0;
   double ck_dt = 0.0;
   int64_t ck_ev_gen = -1;
+  int64_t ck_gen = 0;                     // bumped whenever checkpoints or kept states change
   int64_t launches = 0;
   // CUDA graphs of step chunks, keyed by kind, buffers and sizes
   int chunk = 128;                        // steps per graph (even), 0 = off
@@ -754,6 +755,10 @@ int mg_mesh_create(int dim, int n_levels, const double* coords, int64_t n_nodes,
   M->anc.resize(h.n_levels);
   M->lvl_ptr.resize(h.n_levels);
   M->lvl_idx.resize(h.n_levels);
+  // the fixed array of mg_forward_noalloc: its module is loaded and its
+  // address looked up here (an allocating call anyway), so that the
+  // no-allocation entry point itself reserves nothing on this device
+  if (!rc) rc = mg::noalloc_prepare(M->device);
   if (rc != MG_OK) {
     mg_mesh_destroy(M);
     return rc;
@@ -802,7 +807,7 @@ int mg_mesh_trim(mg_mesh* M) {
     b->bytes = 0;
   }
   M->ev_valid = false;
-  M->ck_valid = false;
+  M->ck_valid = false;  M->ck_gen++;
   M->seg_full = false;
   return MG_OK;
 }
@@ -812,7 +817,7 @@ int mg_mesh_set_conductivity(mg_mesh* M, const double* sigma, void* stream, int 
   if (flags & ~MG_HOST_PTRS) return MG_ERR_UNSUPPORTED;
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
-  M->ck_valid = false;  // checkpoints of an earlier forward no longer apply
+  M->ck_valid = false;  M->ck_gen++;  // checkpoints of an earlier forward no longer apply
   M->seg_full = false;
   if (!sigma) {
     M->has_sigma = false;
@@ -995,6 +1000,8 @@ int mg_mesh_set_row_sweep(mg_mesh* M, int blocks) {
 
 int mg_mesh_get_row_sweep(const mg_mesh* M) { return M ? M->tune[0].sweep : MG_ERR_ARG; }
 
+int64_t mg_mesh_checkpoint_generation(const mg_mesh* M) { return M ? M->ck_gen : MG_ERR_ARG; }
+
 int mg_mesh_set_persistent(mg_mesh* M, int steps, long long wait_cycles, int extra_arrivals) {
   if (!M || steps < 1 || steps > (1 << 20) || wait_cycles < 1000 || extra_arrivals < 0 ||
       extra_arrivals > (1 << 20))
@@ -1101,12 +1108,12 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
   if (flags & MG_SINGLE_SOURCE) {
     MG_TRY(run_forward_single(M, pp, nt, tr, st));
   } else if (flags & MG_KEEP_STATES) {
-    M->ck_valid = false;
+    M->ck_valid = false;  M->ck_gen++;
     M->seg_full = false;
     const size_t state = (size_t)M->hm.n * pp.S_pad;
     MG_TRY(ensure(M->seg, (size_t)(nt + 2) * state * sizeof(float)));
     MG_TRY(run_forward_states(M, pp, nt, tr, P<float>(M->seg), st, flags));
-    M->ck_valid = true;
+    M->ck_valid = true;  M->ck_gen++;
     M->seg_full = true;
     M->ck_every = nt;
     M->ck_nt = nt;
@@ -1116,7 +1123,7 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
     M->ck_ev_gen = M->ev_gen;
   } else {
     float* ck = nullptr;
-    M->ck_valid = false;
+    M->ck_valid = false;  M->ck_gen++;
     M->seg_full = false;
     if (flags & MG_KEEP_CHECKPOINTS) {
       const int nck = (nt + ckpt_every - 1) / ckpt_every;
@@ -1135,7 +1142,7 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
       }
     }
     if (ck) {
-      M->ck_valid = true;
+      M->ck_valid = true;  M->ck_gen++;
       M->ck_every = ckpt_every;
       M->ck_nt = nt;
       M->ck_S_pad = pp.S_pad;
@@ -1317,7 +1324,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
   const int64_t n = M->hm.n;
   const size_t state = (size_t)n * pp.S_pad;
   const bool keep = flags & MG_KEEP_STATES;
-  M->ck_valid = false;
+  M->ck_valid = false;  M->ck_gen++;
   M->seg_full = false;
   float *p = nullptr, *pm = nullptr, *seg = nullptr;
   if (keep) {
@@ -1392,7 +1399,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
     M->launches += (int64_t)NG * nt;
   }
   if (keep) {
-    M->ck_valid = true;
+    M->ck_valid = true;  M->ck_gen++;
     M->seg_full = true;
     M->ck_every = nt;
     M->ck_nt = nt;
@@ -1436,7 +1443,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   if (!states) M->seg_full = false;   // the segment buffer is rewritten below
   const int nck = (nt + ckpt_every - 1) / ckpt_every;
   if (!reuse) {
-    M->ck_valid = false;
+    M->ck_valid = false;  M->ck_gen++;
     MG_TRY(ensure(M->ckpt, (size_t)nck * 2 * state * sizeof(float)));
     MG_TRY(run_forward(M, pp, nt, nullptr, ckpt_every, P<float>(M->ckpt), st, flags));
   }
@@ -1784,7 +1791,7 @@ int prepare_instance(mg_mesh* M, const double* eps, const mg_shots* shots, const
     v->ckpt = P<float>(M->ckpt);
     v->seg = P<float>(M->seg);
     v->G = P<float>(M->G);
-    M->ck_valid = false;
+    M->ck_valid = false;  M->ck_gen++;
     M->seg_full = false;
   }
   if (w) {

@@ -27,6 +27,10 @@ int mesh_view(mg_mesh* mesh, MeshView* out);
 // Padded shot count (row stride of the states) of a batch of S shots.
 int padded_shots(int S);
 
+// Loads the module of mg_forward_noalloc's fixed device array and its
+// kernels on device `dev` (current) and caches the array's address there.
+int noalloc_prepare(int dev);
+
 struct HostMesh;
 // Host image of a handle's mesh (read-only), its device, and a way to count
 // launches made on its behalf by entry points outside capi.cu.

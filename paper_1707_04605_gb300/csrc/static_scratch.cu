@@ -31,7 +31,8 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device `dev`, looked up once
-// per device (the first call on a device does this set-up).
+// per device (normally by mg::noalloc_prepare when a mesh handle is created
+// on that device).
 int scratch_address(int dev, unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) return MG_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -115,20 +116,30 @@ __global__ void k_ev_fill(int S, const int32_t* src, int64_t R, const int64_t* s
   }
 }
 
-int pad_shots(int S) {
-  if (S <= 4) return 4;
-  if (S <= 128) {
-    int p = 4;
-    while (p < S) p <<= 1;
-    return p;
-  }
-  return (S + 127) / 128 * 128;
-}
-
 #define NA_TRY(x) do { const int _rc = (x); if (_rc != MG_OK) return _rc; } while (0)
 #define NA_CU(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); return MG_ERR_CUDA; } } while (0)
 
 }  // namespace
+
+namespace mg {
+
+int noalloc_prepare(int dev) {
+  unsigned char* base = nullptr;
+  const int rc = scratch_address(dev, &base);
+  if (rc != MG_OK) return rc;
+  // load the entry point's own kernels too (lazy module loading would
+  // otherwise load them, and reserve their code memory, at its first call)
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_ev_count) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_scan2) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_ev_fill) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
+
+}  // namespace mg
 
 extern "C" int mg_forward_noalloc(mg_mesh* mesh, const double* eps, const mg_shots* shots,
                                   const double* wavelet, double dt, int nt, float* traces,
@@ -147,7 +158,7 @@ extern "C" int mg_forward_noalloc(mg_mesh* mesh, const double* eps, const mg_sho
   if (R > 0 && !shots->rec) return MG_ERR_ARG;
   for (int64_t r = 0; r < R; ++r)
     if (shots->rec[r] < 0 || shots->rec[r] >= v.n) return MG_ERR_ARG;
-  const int S_pad = pad_shots(S);
+  const int S_pad = mg::padded_shots(S);
   const int64_t n = v.n;
   // carve the fixed array; reject work that does not fit
   Carve c;

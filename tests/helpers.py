@@ -38,3 +38,26 @@ def oracle_gradient(w, dt, wavelet, shots, W, level):
     pb = oracle_problem(w)
     g = wave.adjoint_eps(pb, dt, wavelet, shots.src, shots.rec_ptr, shots.rec, W)
     return wave.restrict(g, w.mesh.ancestor(level), w.mesh.n_cells[level])
+
+
+def golden(name):
+    """A file of stored oracle values under tests/golden/ (written by
+    tests/golden/make_golden.py, which calls only oracle/ and workloads/)."""
+    import os
+
+    return np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name))
+
+
+def check_fingerprint(d, w):
+    """The workload generators still give the inputs a golden file was made
+    from: node and cell counts, coordinate, permittivity and squared
+    permittivity sums, shot nodes and Ricker frequency."""
+    m = w.mesh
+    assert int(d["fp_n_nodes"]) == m.coords.shape[0], "mesh changed since the golden file"
+    assert int(d["fp_n_cells"]) == m.cells.shape[0], "mesh changed since the golden file"
+    assert abs(float(d["fp_coords_sum"]) / np.abs(m.coords).sum() - 1) < 1e-12
+    assert abs(float(d["fp_eps_sum"]) / w.eps.sum() - 1) < 1e-12, "permittivity changed"
+    assert abs(float(d["fp_eps_sq_sum"]) / (w.eps * w.eps).sum() - 1) < 1e-12
+    assert np.array_equal(d["fp_src"], w.shots.src), "shot nodes changed"
+    assert np.array_equal(d["fp_rec"], w.shots.rec), "receiver nodes changed"
+    assert abs(float(d["fp_freq"]) / w.freq - 1) < 1e-12

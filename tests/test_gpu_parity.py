@@ -131,27 +131,6 @@ def test_forward_ellipsoid_3d_level2(mg):
     assert rel_l2(y[w.shots.trace_rows(pick)], ref) < TRACE_TOL
 
 
-def test_forward_ellipsoid_3d_full(mg):
-    """Full 3D workload (1,814,385 nodes, 10.6M tets, 64 shots, 6000 steps,
-    one launch per step over all shots): the first 150 samples of shots 0
-    and 40 against the oracle (causality), and shot 40's whole trace
-    against the plain one-shot path (batching invariance)."""
-    w = configs.ellipsoid_3d()
-    mesh = mg.mesh_from_workload(w)
-    dt = oracle_dt(w)
-    s = w.wavelet(dt)
-    y = mg.forward(mesh, _dev(w.eps), w.shots, _dev(s), dt).cpu().numpy()
-    assert np.isfinite(y).all() and np.abs(y).max() > 0
-    pick = [0, 40]
-    rows = w.shots.trace_rows(pick)
-    k = 150
-    ref = oracle_traces(w, dt, s[:k], w.shots.subset(pick))
-    assert rel_l2(y[rows, :k], ref) < TRACE_TOL
-    y1 = mg.forward(mesh, _dev(w.eps), w.shots.subset([40]), _dev(s), dt,
-                    single_source=True).cpu().numpy()
-    assert rel_l2(y1, y[w.shots.trace_rows([40])]) < 1e-6
-
-
 def test_jacobian_ellipsoid_3d_level1(mg):
     w = configs.ellipsoid_3d(n_refine=1, S=6, nt=160)
     mesh = mg.mesh_from_workload(w)
@@ -199,7 +178,7 @@ def test_tangent_and_adjoint_tiny(mg, make, bc):
     # dot-product test on the GPU outputs, inner products in FP64
     lhs = float(np.sum(jv.astype(np.float64) * W.astype(np.float32)))
     rhs = float(np.sum(v * g))
-    assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), 1e-30)
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1e-30)
 
 
 def test_adjoint_checkpoint_spacing_and_reuse(mg):

@@ -43,28 +43,42 @@ def _call(lib, L, mesh, eps, shots, wav, dt, nt, out, flags=0):
 
 
 def test_noalloc_forward_matches_forward_twice(env):
+    """Two calls in a row with different inputs: the second has another
+    permittivity, fewer shots at other nodes with other receivers, and a
+    shorter run, so contents the first call left in the shared array
+    (coefficients, event lists, the FP32 wavelet) would show in its traces.
+    Neither call changes the device's free memory: the array was reserved
+    when the mesh handle was created."""
     mg, L, lib = env
     w = configs.asteroid_2d(n_refine=2, S=37, nt=400)
     mesh = mg.mesh_from_workload(w)
     dt = oracle_dt(w)
-    eps = torch.as_tensor(w.eps, dtype=torch.float64, device="cuda")
-    wav = torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device="cuda")
-    ref = mg.forward(mesh, eps, w.shots, wav, dt).cpu().numpy()
-    shots = mg.Shots.of(w.shots)
-    outs = [torch.full((shots.n_traces, w.nt), np.nan, dtype=torch.float32, device="cuda")
-            for _ in range(2)]
+    cases = []
+    for eps_h, sh, nt in ((w.eps, w.shots, w.nt),
+                          (w.eps * np.where(np.arange(len(w.eps)) % 3 == 0, 1.1, 1.0),
+                           configs.asteroid_2d(n_refine=2, S=12, rotation=0.3).shots, 250)):
+        eps = torch.as_tensor(eps_h, dtype=torch.float64, device="cuda")
+        wav = torch.as_tensor(w.wavelet(dt, nt), dtype=torch.float64, device="cuda")
+        ref = mg.forward(mesh, eps, sh, wav, dt).cpu().numpy()
+        cases.append((eps, mg.Shots.of(sh), wav, nt, ref))
+    assert cases[1][1].n_traces != cases[0][1].n_traces
     torch.cuda.synchronize()
-    for i, out in enumerate(outs):
+    for eps, shots, wav, nt, ref in cases:
+        out = torch.full((shots.n_traces, nt), np.nan, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
         free_before = torch.cuda.mem_get_info()[0]
-        rc = _call(lib, L, mesh, eps, shots, wav, dt, w.nt, out)
+        rc = _call(lib, L, mesh, eps, shots, wav, dt, nt, out)
         torch.cuda.synchronize()
         assert rc == L.MG_OK, lib.mg_strerror(rc)
-        if i == 1:
-            # no device memory was reserved by the call
-            assert torch.cuda.mem_get_info()[0] == free_before
+        assert torch.cuda.mem_get_info()[0] == free_before
         y = out.cpu().numpy()
         assert np.isfinite(y).all()
         assert rel_l2(y, ref) < TRACE_TOL
+    # dt above the stability bound is refused unless MG_ALLOW_CFL is given
+    eps, shots, wav, nt, _ = cases[0]
+    out = torch.zeros((shots.n_traces, nt), dtype=torch.float32, device="cuda")
+    dt_big = 1.01 * mg.cfl_dt(mesh, eps)
+    assert _call(lib, L, mesh, eps, shots, wav, dt_big, nt, out) == L.MG_ERR_CFL
 
 
 def test_noalloc_rejects_work_beyond_its_array(env):
