@@ -2,16 +2,20 @@
 
 One step = one pass of the whole path over the 2D asteroid workload
 (62,641 nodes, 124,416 P1 triangles, 128 backscatter shots, 8000 leapfrog
-steps): the batched forward (keeping checkpoints every 256 steps), the
-adjoint gradient J^T w on the 7,776 level-1 cells (w = the traces, i.e. the
-gradient of 0.5 |y|^2; recomputation from the checkpoints), and one tangent
-J v.  Units per step: n * S * nt for each of the three wave fields that the
-method needs (forward, adjoint, tangent); the recomputation inside the
-adjoint pass and the forward re-run inside the tangent pass are overhead and
-are not counted.
+steps): the batched forward traces, the adjoint gradient J^T w on the 7,776
+level-1 cells (w = the traces, i.e. the gradient of 0.5 |y|^2) and one
+tangent J v.  Units per step: n * S * nt for each of the three wave fields
+the method needs (forward, adjoint, tangent); recomputation is overhead and
+is not counted.
+
+The headline step keeps every forward state in HBM when it fits (256.6 GB:
+the fused forward + tangent pass writes the history, J^T w runs on it with
+no recompute); the same step with forward checkpoints every 256 steps (a
+recompute per segment, a bounded memory) is timed as `c3_checkpointed`.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Prints one JSON line (rank 0).
+With --gpus N > 1 and no launcher environment, the script re-executes itself
+under torch.distributed.run with N ranks.  Prints one JSON line (rank 0).
 """
 from __future__ import annotations
 
@@ -79,7 +83,26 @@ def parse():
                     help="kept history: L2 evict-first on the last reads (0 or 1)")
     ap.add_argument("--hbm-only", action="store_true",
                     help="only the 3D ellipsoid forward measurement")
+    ap.add_argument("--no-c3-leg", action="store_true",
+                    help="skip the step with checkpoints every 256 steps")
+    ap.add_argument("--tuning", default="",
+                    help="JSON tuning per kernel kind (as printed in config.tuning) applied "
+                         "instead of the autotuner; with --hbm-only, of the 3D forward")
     return ap.parse_args()
+
+
+def apply_tuning(mesh, spec):
+    """Applies a tuning dict {kind: {batch, tile_rows, src_tile, groups,
+    ring, min_blocks, sweep}} (the shape of Mesh.tuning()) to a handle."""
+    for kind, t in spec.items():
+        if kind not in ("forward", "tangent", "adjoint"):
+            continue
+        mesh.set_kernel_tuning(kind, t["batch"], t["tile_rows"], t["src_tile"])
+        mesh.set_shot_groups(t.get("groups", 1), kind)
+        mesh.set_gather_ring(t.get("ring", 0), kind)
+        if kind == "forward":
+            mesh.set_min_blocks(t.get("min_blocks", 0))
+            mesh.set_row_sweep(t.get("sweep", 0))
 
 
 def dist_env():
@@ -87,6 +110,27 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def relaunch_or_check(args):
+    """--gpus N means N ranks: without a launcher environment, re-execute
+    under torch.distributed.run (one process per GPU on this node); under a
+    launcher, the world size must equal N."""
+    if "WORLD_SIZE" not in os.environ:
+        if args.gpus <= 1:
+            return
+        import socket
+
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               f"--nproc-per-node={args.gpus}", "--master-addr=127.0.0.1",
+               f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+        os.execv(sys.executable, cmd)
+    ws = int(os.environ["WORLD_SIZE"])
+    if ws != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but the launcher started {ws} ranks")
 
 
 def workload_for_rank(rank: int, nt=None):
@@ -102,12 +146,15 @@ def workload_for_rank(rank: int, nt=None):
     return w
 
 
-def describe(w):
+def describe(w, layout="checkpoints"):
+    """The workload and the memory layout timed: "kept" (every forward state
+    in HBM, no recompute) or "checkpoints" (every CKPT steps, recompute)."""
     m = w.mesh
+    how = ("every forward state kept in HBM, J^T w without recompute" if layout == "kept" else
+           f"forward checkpoints every {CKPT} steps, J^T w recomputes each segment")
     return (f"asteroid_2d: {m.coords.shape[0]} nodes, {m.cells.shape[0]} P1 triangles "
             f"(level 0: {m.n_cells[0]}), {w.shots.n_shots} backscatter shots, {w.nt} steps; "
-            f"forward + J^T w on {m.n_cells[LEVEL]} level-{LEVEL} cells (checkpoints every "
-            f"{CKPT}) + J v")
+            f"forward + J^T w on {m.n_cells[LEVEL]} level-{LEVEL} cells + J v ({how})")
 
 
 def clocks_start():
@@ -151,26 +198,32 @@ def clocks_stop(proc, gpu_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per leapfrog step of the roofline's kernel, from
-# one ncu capture of the same workload and launch shape (summaries in profiles/),
-# with the SHA-1 of the kernel sources at capture time: a figure is reported
-# only while those sources are unchanged, else the roofline's traffic is null.
-KERNEL_SOURCES = ["kernels_rows.cu", "device_util.cuh", "kernels.cuh"]
+# DRAM bytes (read + write) per leapfrog step of a roofline's kernel, from
+# one ncu capture of the same workload, layout and launch shape (summaries in
+# profiles/), with the SHA-1 of the kernel sources at capture time: a figure
+# is reported only while those sources are unchanged, else `traffic` is null.
+KERNEL_SOURCES = ["rows_common.cuh", "kernels_rows.cu", "device_util.cuh", "kernels.cuh"]
 TRAFFIC = {
-    # (workload, kept history, batch, tile_rows, groups, min_blocks, bulk,
-    #  uniform ELL): (bytes per leapfrog step, all shot groups; sha1 of the
-    #  kernel sources)
-    # k_tangent_rows<16,1>, fused forward + tangent writing the kept history,
-    # two shot groups (64 columns per launch), uniformly strided stiffness,
-    # --cache-control none, launches 22-24: 12.3 MB read + 24.6 MB written
-    # per launch, two per step
-    ("asteroid_2d_fused", True, 1, 0, 2, 0, 0, True): (
-        73.8e6, "8714da4412172775de3ff1b4f018c7730eb755d5"),
-    # k_step_rows<8,2,5>, sliced stiffness, two launches: 1228.5 MB read +
-    # 438.3 MB written
-    ("ellipsoid_3d", False, 2, 0, 1, 5, 0, False): (
-        1.667e9, "8714da4412172775de3ff1b4f018c7730eb755d5"),
+    # key: (workload and kernel, shape_key of the kind's tuning, uniformly
+    # strided stiffness); value: (DRAM bytes per leapfrog step, all shot
+    # groups; sha1 of the kernel sources)
+    # k_tangent_rows<16, 1, 0>, fused forward + tangent writing the kept
+    # history, two shot groups of 64 columns: launches 42-47 of the profiled
+    # steps, 11.6 MB read + 24.4 MB written per launch, two per step
+    # (profiles/fused_tangent_adjoint_asteroid_2d_kept.md)
+    ("asteroid_2d fused", (1, 0, 2, 0, 0, 0, 0), True): (
+        72.1e6, "597f49e1abb100c3a6280617ec747f56fbb9be83"),
+    # k_step_rows<8, 2, 5, 0>, register cap, 4 row blocks per CTA: 1237.9 MB
+    # read + 466.6 MB written per launch (profiles/forward_ellipsoid_3d_s64.md)
+    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4), False): (
+        1.7045e9, "597f49e1abb100c3a6280617ec747f56fbb9be83"),
 }
+
+
+def shape_key(t):
+    """The launch-shape fields of a kind's tuning that change its traffic."""
+    return (t["batch"], t["tile_rows"], t.get("groups", 1), t.get("min_blocks", 0),
+            t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0))
 
 
 def sources_sha1():
@@ -185,11 +238,23 @@ def sources_sha1():
     return h.hexdigest()
 
 
-def traffic_for(workload, fwd, kept=False, uniform=False):
-    key = (workload, bool(kept), fwd["batch"], fwd["tile_rows"], fwd.get("groups", 1),
-           fwd.get("min_blocks", 0), fwd.get("bulk", 0), bool(uniform))
-    hit = TRAFFIC.get(key)
+def traffic_for(kernel, tuning, uniform=False):
+    hit = TRAFFIC.get((kernel, shape_key(tuning), bool(uniform)))
     return hit[0] if hit and hit[1] == sources_sha1() else None
+
+
+def roofline(kernel, algorithmic, seconds_per_step, traffic, peak, peak_kind, limiter, note):
+    """HBM roofline of a kernel: algorithmic bytes per leapfrog step over its
+    time per step; with ncu DRAM bytes (`traffic`) also the DRAM fraction
+    actually moved and the ratio of moved to algorithmic bytes."""
+    achieved = algorithmic / seconds_per_step / 1e9
+    out = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+           "algorithmic_bytes_per_launch": algorithmic,
+           "dram_frac": None if traffic is None else traffic / seconds_per_step / 1e9 / peak,
+           "traffic_ratio": None if traffic is None else traffic / algorithmic,
+           "limiter": limiter, "note": note}
+    return out
 
 
 def peaks():
@@ -206,68 +271,79 @@ def peaks():
 
 def hbm_leg(mg, torch, dev, nt=300, args=None):
     """The 3D ellipsoid workload (1,814,385 nodes, 64 shots; each state is
-    464 MB, far beyond L2): the batched forward step over `nt` leapfrog steps,
-    where the step kernel is bound by HBM bandwidth."""
+    464 MB, far beyond L2): the batched forward step over `nt` of its 6000
+    leapfrog steps, where the step kernel is bound by HBM bandwidth."""
     w = configs.ellipsoid_3d(nt=nt)
     mesh = mg.mesh_from_workload(w)
     eps = torch.as_tensor(w.eps, dtype=torch.float64, device=dev)
     dt = w.cfl_fraction * mg.cfl_dt(mesh, eps)
     wav = torch.as_tensor(w.wavelet(dt), dtype=torch.float64, device=dev)
-    if args is not None and (args.tile_rows != -1 or args.src_tile != -1 or args.lane_vec != -1):
+    stream = torch.cuda.current_stream(dev)
+
+    def run_ms(reps=3):
+        best = None
+        for _ in range(reps):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            mg.forward(mesh, eps, w.shots, wav, dt)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms = a0.elapsed_time(a1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    if args is not None and args.tuning:
+        apply_tuning(mesh, {"forward": json.loads(args.tuning)})
+    elif args is not None and (args.tile_rows != -1 or args.src_tile != -1 or args.lane_vec != -1):
         mesh.set_kernel_tuning("forward", args.lane_vec, args.tile_rows, args.src_tile)
         if args.min_blocks != -1:
             mesh.set_min_blocks(args.min_blocks)
     else:
         mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
-        # the register cap of the chosen row shape: both timed over the whole
-        # run (the 32-step autotune windows do not always separate them)
+        # register cap and row sweep of the chosen row shape, each timed as
+        # the best of three whole runs (the 32-step autotune windows do not
+        # always separate them)
         if mesh.tuning()["forward"]["tile_rows"] == 0:
             best = None
             for cap in (0, 5):
-                mesh.set_min_blocks(cap)
-                mg.forward(mesh, eps, w.shots, wav, dt)
-                torch.cuda.synchronize()
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record()
-                mg.forward(mesh, eps, w.shots, wav, dt)
-                a1.record()
-                torch.cuda.synchronize()
-                ms = a0.elapsed_time(a1)
-                if best is None or ms < best[1] * 0.99:
-                    best = (cap, ms)
+                for sweep in (0, 4):
+                    mesh.set_min_blocks(cap)
+                    mesh.set_row_sweep(sweep)
+                    mg.forward(mesh, eps, w.shots, wav, dt)
+                    torch.cuda.synchronize()
+                    ms = run_ms()
+                    if best is None or ms < best[2] * 0.99:
+                        best = (cap, sweep, ms)
             mesh.set_min_blocks(best[0])
+            mesh.set_row_sweep(best[1])
     if args is not None and args.dep_launch != -1:
         mesh.set_dependent_launch(args.dep_launch)
     tuning = mesh.tuning()
     mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stream = torch.cuda.current_stream(dev)
     if args is not None and args.profile:
         torch.cuda.profiler.start()
-    e0.record(stream)
-    mg.forward(mesh, eps, w.shots, wav, dt)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    s = run_ms(1 if args is not None and args.profile else 3) / 1e3
     if args is not None and args.profile:
         torch.cuda.profiler.stop()
-    s = e0.elapsed_time(e1) / 1e3
     n, S = w.n_nodes, w.shots.n_shots
     info = mesh.info()
     S_pad = 64
     bytes_step = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
     peak, kind = peaks()
-    achieved = bytes_step / (s / nt) / 1e9
+    traffic = traffic_for("ellipsoid_3d forward", tuning["forward"])
     mesh.close()
     return {"workload": f"ellipsoid_3d: {n} nodes, {w.mesh.cells.shape[0]} tets, {S} "
-                        f"backscatter shots, {nt} steps (forward only)",
+                        f"backscatter shots, {nt} of its 6000 steps timed (forward only; the "
+                        f"rate per step does not depend on the step count)",
             "forward_updates_per_s": n * S * nt / s, "us_per_leapfrog_step": 1e6 * s / nt,
             "tuning": tuning["forward"],
-            "roofline": {"kernel": "k_step (batched forward leapfrog step)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind_note(kind),
-                         "algorithmic_bytes_per_launch": bytes_step,
-                         "traffic": traffic_for("ellipsoid_3d", tuning["forward"])}}
+            "roofline": roofline(
+                "k_step (batched forward leapfrog step)", bytes_step, s / nt, traffic, peak,
+                peak_kind_note(kind),
+                "bytes in flight: DRAM traffic is the algorithmic bytes (ncu), the kernel is "
+                "latency bound (long-scoreboard stalls, issue ~35%)",
+                f"best of three runs of {nt} steps, CUDA events on the launching stream")}
 
 
 def peak_kind_note(kind):
@@ -416,7 +492,7 @@ def pml_leg(mg, torch, mesh, w, eps_d, wav_d, dt, nt=1000, ckpt=100):
                     "adjoint includes its checkpointed forward and the recompute"}
 
 
-def batch_leg(mg, torch, dev, nt=1000, ckpt=50):
+def batch_leg(mg, torch, dev, nt=4000, ckpt=256):
     """The uneven batch: 24 asteroid instances (levels 1-4, 8-256 shots, own
     eps, shots, f and dt) advanced by one launch per step for all of them
     (forward, and J^T with its recompute and reverse steps), against the
@@ -512,27 +588,87 @@ def guarded(fn, *a, **k):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
-def cpu_baseline(w, dt, budget_s=20.0):
-    """The FP64 oracle as it stands on the host cores, on a bounded sample of
-    the same workload: 2 shots, forward + tangent + adjoint over nt_s steps."""
+ORACLE_STEPS = 200      # leapfrog steps of the oracle sample (of the workload's 8000)
+
+
+def _oracle_shot(task):
+    """One worker of the oracle sample: shot `shot` of the bench workload,
+    forward + tangent (J e_0) + adjoint (w = its traces) over `nt_s` steps on
+    the full mesh, single-threaded.  Returns (seconds, node*shot updates)."""
+    shot, nt_s, dt = task
     from oracle import wave
 
+    w = configs.asteroid_2d()
     m = w.mesh
     pb = wave.Problem(m.coords, m.cells, m.bnd, w.eps, w.bc)
-    sub = w.shots.subset([0, 1])
-    nt_s = 400
+    sub = w.shots.subset([shot])
     s = w.wavelet(dt, nt_s)
-    t0 = time.perf_counter()
-    y = wave.forward(pb, dt, s, sub.src, sub.rec_ptr, sub.rec)
     v = np.zeros(m.n_cells[LEVEL])
     v[0] = 1.0
-    wave.tangent(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, wave.prolong(v, m.ancestor(LEVEL)))
+    de = wave.prolong(v, m.ancestor(LEVEL))
+    t0 = time.perf_counter()
+    y = wave.forward(pb, dt, s, sub.src, sub.rec_ptr, sub.rec)
+    wave.tangent(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, de)
     wave.adjoint_eps(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, y)
-    el = time.perf_counter() - t0
-    units = 3.0 * m.coords.shape[0] * sub.n_shots * nt_s
-    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"2 of {w.shots.n_shots} shots, {nt_s} of {w.nt} steps, forward + tangent "
-                      f"+ adjoint on the full mesh ({el:.1f} s, single-threaded numpy/scipy)"}
+    return time.perf_counter() - t0, 3.0 * m.coords.shape[0] * sub.n_shots * nt_s
+
+
+class OracleSample:
+    """The FP64 oracle as it stands, timed on the host's cores: one
+    single-threaded process per core (spawned, so that none inherits a CUDA
+    context), each running one shot of the bench workload for ORACLE_STEPS
+    steps; the rate is the updates of all processes over the slowest one's
+    compute time.  A one-process figure is kept beside it."""
+
+    def __init__(self, dt, cores=None):
+        import multiprocessing as mp
+
+        self.dt = dt
+        self.cores = cores or os.cpu_count() or 1
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                 "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self):
+        tasks = [(k, ORACLE_STEPS, self.dt) for k in range(self.cores)]
+        res = self.pool.map(_oracle_shot, tasks, chunksize=1)
+        return sum(u for _, u in res) / max(t for t, _ in res), res
+
+    def single(self):
+        t, u = self.pool.apply(_oracle_shot, ((0, ORACLE_STEPS, self.dt),))
+        return u / t
+
+    def sample_text(self):
+        return (f"{self.cores} shots of 128 (one per process, {self.cores} single-threaded "
+                f"processes on {self.cores} cores), {ORACLE_STEPS} of 8000 steps each, forward "
+                f"+ tangent + adjoint on the full 62,641-node mesh (numpy/scipy FP64)")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(dt):
+    """The oracle's rate on the host's cores (bounded sample, about 10-20 s)."""
+    ora = OracleSample(dt)
+    try:
+        ora.run()                                  # imports and page-in
+        val, res = ora.run()
+        one = ora.single()
+    finally:
+        ora.close()
+    return {"value": val, "unit": UNIT, "cores": ora.cores, "kind": "oracle",
+            "sample": ora.sample_text(), "cores_1_value": one,
+            "seconds_per_process": [round(t, 2) for t, _ in res]}
 
 
 def run_reference(args):
@@ -545,35 +681,23 @@ def run_reference(args):
     m = w.mesh
     pb = wave.Problem(m.coords, m.cells, m.bnd, w.eps, w.bc)
     dt = w.cfl_fraction * pb.cfl_dt()
-    sub = w.shots.subset([0])
-    nt_s = 200
-    s = w.wavelet(dt, nt_s)
-    v = np.zeros(m.n_cells[LEVEL])
-    v[0] = 1.0
-    de = wave.prolong(v, m.ancestor(LEVEL))
-
-    def step():
-        y = wave.forward(pb, dt, s, sub.src, sub.rec_ptr, sub.rec)
-        wave.tangent(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, de)
-        wave.adjoint_eps(pb, dt, s, sub.src, sub.rec_ptr, sub.rec, y)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
-    units = 3.0 * m.coords.shape[0] * sub.n_shots * nt_s * args.steps
-    val = units / el
-    sample = (f"1 of {w.shots.n_shots} shots, {nt_s} of {w.nt} steps per step, forward + "
-              f"tangent + adjoint on the full mesh, single-threaded numpy/scipy FP64")
+    ora = OracleSample(dt)
+    try:
+        for _ in range(args.warmup):
+            ora.run()
+        vals = [ora.run()[0] for _ in range(args.steps)]
+    finally:
+        ora.close()
+    # every step is one parallel sample: report its mean rate and time
+    val = statistics.mean(vals)
+    units = 3.0 * m.coords.shape[0] * ora.cores * ORACLE_STEPS
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * units / val,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": describe(w)},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic", "config": {"workload": describe(w, "kept")},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": ora.cores, "kind": "oracle",
+                         "sample": ora.sample_text()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
     return 0
@@ -581,6 +705,7 @@ def run_reference(args):
 
 def main():
     args = parse()
+    relaunch_or_check(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -639,7 +764,13 @@ def main():
     v = np.zeros(nlev)
     v[np.random.default_rng(0).integers(nlev)] = 1.0
     v_d = torch.as_tensor(v, dtype=torch.float64, device=dev)
-    if (args.tile_rows == -1 and args.src_tile == -1 and args.lane_vec == -1
+    if args.tuning:
+        spec = json.loads(args.tuning)
+        apply_tuning(mesh, spec)
+        if args.kept_groups == "":    # the groups of the given tuning apply as they are
+            args.kept_groups = ",".join(str(spec[k].get("groups", 1))
+                                        for k in ("forward", "adjoint", "tangent"))
+    elif (args.tile_rows == -1 and args.src_tile == -1 and args.lane_vec == -1
             and not args.no_autotune):
         # launch shapes per kernel kind, timed on this problem (setup, untimed)
         mesh.autotune(eps_d, w.shots, wav_d, dt, steps=128, level=LEVEL)
@@ -652,17 +783,13 @@ def main():
             pdist.gradient_allreduce(g)
         return g
 
-    phase_ev = {}
-    # Adjoint strategy: every forward state kept in HBM when it fits (one
-    # segment, no recompute), else checkpoints every CKPT steps and a
-    # recompute per segment.
+    # Adjoint strategy of the headline: every forward state kept in HBM when
+    # it fits (one segment, no recompute), else checkpoints every CKPT steps.
     S_pad = max(4, 1 << (S - 1).bit_length()) if S <= 128 else (S + 127) // 128 * 128
     states_bytes = 4 * n * S_pad * (nt + 2)
     free_bytes = torch.cuda.mem_get_info(dev)[0]
     keep_states = not args.checkpoints and free_bytes > states_bytes + (16 << 30)
-    fwd_kw = dict(keep_states=True) if keep_states else dict(ckpt_every=CKPT,
-                                                             keep_checkpoints=True)
-    adj_ckpt = nt if keep_states else CKPT
+    layout = "kept" if keep_states else "checkpoints"
     kept_groups = None
     if keep_states and args.kept_groups:
         kept_groups = dict(zip(("forward", "adjoint", "tangent"),
@@ -671,81 +798,84 @@ def main():
             mesh.set_shot_groups(g, kind)
     elif keep_states and not args.no_autotune:
         kept_groups = tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, LEVEL)
+    tuning_kept = mesh.tuning()
     adjoint_mode = (f"every forward state kept in HBM ({states_bytes / 1e9:.1f} GB): J^T w "
-                    "without recompute, J v reads the forward field" if keep_states else
+                    "without recompute, J v in the forward pass" if keep_states else
                     f"checkpoints every {CKPT} steps, recompute per segment")
 
-    def step(record=False):
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    def step_kept():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         evs[0].record(stream)
-        if keep_states:
-            # forward traces and J v in one pass that keeps the history, then
-            # J^T w on it (no forward left to run)
-            y, _ = mg.forward_jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d,
-                                             keep_states=True)
-            evs[1].record(stream)
-            evs[2].record(stream)
-            g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=nt,
-                                    reuse_checkpoints=True)
-            allreduce(g)
-            evs[3].record(stream)
-        else:
-            y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, **fwd_kw)
-            evs[1].record(stream)
-            g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y,
-                                    ckpt_every=adj_ckpt, reuse_checkpoints=True)
-            allreduce(g)
-            evs[2].record(stream)
-            mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d)
-            evs[3].record(stream)
-        if record:
-            phase_ev.setdefault("ev", []).append(evs)
+        # forward traces and J v in one pass that keeps the history, then
+        # J^T w on it (no forward left to run)
+        y, _ = mg.forward_jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d,
+                                         keep_states=True)
+        evs[1].record(stream)
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=nt,
+                                reuse_checkpoints=True)
+        allreduce(g)
+        evs[2].record(stream)
         return evs
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    clk = clocks_start() if rank == 0 else None
-    launches0 = mesh.launch_count()
-    times = []
-    if args.profile:
-        torch.cuda.profiler.start()            # profilers capture the timed steps only
-    for _ in range(args.steps):
-        flush.fill_(1.0)                       # evict L2 between timed steps
-        evs = step(record=True)
-        times.append(evs)
-    torch.cuda.synchronize()
-    if args.profile:
-        torch.cuda.profiler.stop()
-    if ws > 1:
-        torch.distributed.barrier()
-    launches = mesh.launch_count() - launches0
-    clocks = clocks_stop(clk, dev.index) if rank == 0 else None
+    def step_ckpt():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        evs[0].record(stream)
+        y = mg.forward(mesh, eps_d, w.shots, wav_d, dt, ckpt_every=CKPT, keep_checkpoints=True)
+        evs[1].record(stream)
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, y, ckpt_every=CKPT,
+                                reuse_checkpoints=True)
+        allreduce(g)
+        evs[2].record(stream)
+        mg.jacobian_apply(mesh, LEVEL, eps_d, w.shots, wav_d, dt, v_d)
+        evs[3].record(stream)
+        return evs
+
+    def timed_steps(step, K, clocks=False, profile=False):
+        """W (>= 3) warm-up steps, then K steps with L2 flushed before each;
+        barriers and device synchronisation on both sides."""
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        clk = clocks_start() if clocks and rank == 0 else None
+        l0 = mesh.launch_count()
+        if profile:
+            torch.cuda.profiler.start()        # profilers capture the timed steps only
+        out = []
+        for _ in range(K):
+            flush.fill_(1.0)                   # evict L2 between timed steps
+            out.append(step())
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
+        if ws > 1:
+            torch.distributed.barrier()
+        return out, mesh.launch_count() - l0, (clocks_stop(clk, dev.index) if clk else None)
+
+    def total_seconds(times):
+        t = sum(e[0].elapsed_time(e[-1]) for e in times) / 1e3
+        if ws > 1:
+            x = torch.tensor([t], device=dev)
+            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+            t = float(x.item())
+        return t
+
+    times, launches, clocks = timed_steps(step_kept if keep_states else step_ckpt, args.steps,
+                                          clocks=True, profile=args.profile)
     if args.profile:
         if rank == 0:
             print(json.dumps({"profile": True, "launches": int(launches),
-                              "step_ms": [e[0].elapsed_time(e[3]) for e in times],
+                              "step_ms": [e[0].elapsed_time(e[-1]) for e in times],
                               "tuning": tuning, "kept_groups": kept_groups,
                               "adjoint": adjoint_mode}))
         return 0
-    step_ms = [e[0].elapsed_time(e[3]) for e in times]
+    mean_ms = lambda a, b: statistics.mean(e[a].elapsed_time(e[b]) for e in times)
     if keep_states:   # fused forward + tangent pass, then the reverse steps
-        fwt_ms = [e[0].elapsed_time(e[1]) for e in times]
-        adj_ms = [e[2].elapsed_time(e[3]) for e in times]
-        phases = {"forward_tangent": statistics.mean(fwt_ms), "adjoint": statistics.mean(adj_ms)}
+        phases = {"forward_tangent": mean_ms(0, 1), "adjoint": mean_ms(1, 2)}
     else:
-        fwd_ms = [e[0].elapsed_time(e[1]) for e in times]
-        adj_ms = [e[1].elapsed_time(e[2]) for e in times]
-        tan_ms = [e[2].elapsed_time(e[3]) for e in times]
-        phases = {"forward": statistics.mean(fwd_ms), "adjoint": statistics.mean(adj_ms),
-                  "tangent": statistics.mean(tan_ms)}
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+        phases = {"forward": mean_ms(0, 1), "adjoint": mean_ms(1, 2), "tangent": mean_ms(2, 3)}
+    total_s = total_seconds(times)
     units_per_step = 3.0 * n * S * nt
     value = units_per_step * args.steps * ws / total_s
 
@@ -758,9 +888,10 @@ def main():
             y, jv = mg.forward_jacobian_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, v_h,
                                               keep_states=True)
         else:
-            y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, **fwd_kw)
-        g = mg.jacobian_T_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, y, ckpt_every=adj_ckpt,
-                                reuse_checkpoints=True)
+            y = mg.forward(mesh, eps_h, w.shots, wav_h, dt, ckpt_every=CKPT,
+                           keep_checkpoints=True)
+        g = mg.jacobian_T_apply(mesh, LEVEL, eps_h, w.shots, wav_h, dt, y,
+                                ckpt_every=nt if keep_states else CKPT, reuse_checkpoints=True)
         if ws > 1:
             gt = torch.as_tensor(g, device=dev)
             allreduce(gt)
@@ -791,19 +922,52 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     single_rate = n * 4 * nt / (e0.elapsed_time(e1) / 1e3)
-    if keep_states:   # the batched forward alone, for the comparison with one shot at a time
-        mg.forward(mesh, eps_d, w.shots, wav_d, dt)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        mg.forward(mesh, eps_d, w.shots, wav_d, dt)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fwd_rate = n * S * nt / (e0.elapsed_time(e1) / 1e3)
-    else:
-        fwd_rate = n * S * nt / (statistics.mean(fwd_ms) / 1e3)
+    # the batched forward alone, for the comparison with one shot at a time
+    mg.forward(mesh, eps_d, w.shots, wav_d, dt)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    mg.forward(mesh, eps_d, w.shots, wav_d, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_rate = n * S * nt / (e0.elapsed_time(e1) / 1e3)
     # the kept forward history (up to ~257 GB) is not needed by the legs below
     mesh.trim()
     torch.cuda.empty_cache()
+
+    peak, peak_kind = peaks()
+    peak_kind = peak_kind_note(peak_kind)
+    info = mesh.info()
+    # algorithmic bytes per leapfrog step (all shot groups): states, matrix,
+    # per-row coefficients; see the kernel table of the design notes
+    b_fwd = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
+    b_tan = 24.0 * n * S_pad + 8.0 * info["nnz"] + 24.0 * n
+    b_adj = 16.0 * n * S_pad + 8.0 * info["nnz"] + 48.0 * n
+    l2_note = ("latency bound with the states L2-resident (ncu: DRAM and L2 at a fifth of their "
+               "peaks, long-scoreboard stalls): the fraction is of algorithmic bytes, "
+               "dram_frac of the bytes DRAM moved")
+
+    # the same step with C3's memory bound: checkpoints every 256 steps
+    c3 = None
+    if keep_states and not args.no_c3_leg:
+        for kind in ("forward", "tangent", "adjoint"):   # the autotuned groups
+            mesh.set_shot_groups(tuning[kind].get("groups", 1), kind)
+        tc, _, _ = timed_steps(step_ckpt, max(1, min(args.steps, 2)))
+        tcs = total_seconds(tc)
+        ph = {"forward": statistics.mean(e[0].elapsed_time(e[1]) for e in tc),
+              "adjoint": statistics.mean(e[1].elapsed_time(e[2]) for e in tc),
+              "tangent": statistics.mean(e[2].elapsed_time(e[3]) for e in tc)}
+        tname = "k_tangent_tiled" if tuning["tangent"]["tile_rows"] else "k_tangent_rows"
+        c3 = {"value": units_per_step * len(tc) * ws / tcs, "unit": UNIT,
+              "ms_per_step": 1e3 * tcs / len(tc), "phases_ms": ph,
+              "workload": describe(w, "checkpoints"), "tuning": tuning,
+              "memory": f"checkpoints {2 * ((nt + CKPT - 1) // CKPT) * 4 * n * S_pad / 1e9:.1f} "
+                        f"GB + segment {(CKPT + 2) * 4 * n * S_pad / 1e9:.1f} GB",
+              "roofline": roofline(
+                  f"{tname} (lockstep forward + tangent step, J v)", b_tan,
+                  ph["tangent"] / 1e3 / nt,
+                  traffic_for("asteroid_2d tangent", tuning["tangent"], uniform), peak,
+                  peak_kind, l2_note, "per-step time = J v phase / nt (launch gaps included)")}
+        mesh.trim()
 
     # projected data (Sec. II): the two time inner products of every trace
     # pair and the adjoint weights of the projected Jacobian, on this step's
@@ -829,59 +993,55 @@ def main():
         inversion_leg, mg, torch, mesh, w, eps_d, wav_d, dt, y)
     approx = None if args.no_inversion_leg else guarded(
         approx_jacobian_leg, mg, torch, mesh, w, eps_d, wav_d, dt, y)
-    batch = None if args.no_batch_leg or ws > 1 else guarded(batch_leg, mg, torch, dev)
     pml = None if args.no_pml_leg else guarded(pml_leg, mg, torch, mesh, w, eps_d, wav_d, dt)
+    mesh.trim()
+    batch = None if args.no_batch_leg or ws > 1 else guarded(batch_leg, mg, torch, dev)
     proj["note"] = (f"{R} traces x {nt} samples; FP64 accumulation; inputs L2-resident; "
                     "the projected Jacobian products cost one jacobian_apply / "
                     "jacobian_T_apply each (the forward and adjoint phases above)")
 
     if rank != 0:
         return 0
-    # roofline of the dominant step kernel: algorithmic bytes per leapfrog
-    # step (all shot groups) / (its phase time / nt, launch gaps included)
-    info = mesh.info()
-    S_pad = S
-    peak, peak_kind = peaks()
+    # roofline of the dominant kernel of the headline step: algorithmic bytes
+    # per leapfrog step (all shot groups) / (its phase time / nt)
     if keep_states:
         # k_tangent_rows: p_l, p_{l-1}, dp_l, dp_{l-1} read, p_{l+1}, dp_{l+1}
         # written per node.shot; matrix, {alpha, beta, gamma, 1/w} and the
         # tangent coefficients per row
-        bytes_fwd = 24.0 * n * S_pad + 8.0 * info["nnz"] + 24.0 * n
-        fwd_launch_s = phases["forward_tangent"] / 1e3 / nt
-        kernel = ("k_tangent_rows (fused forward + tangent step, writing the kept history; "
-                  "per leapfrog step, all shot groups)")
-        tkey = ("asteroid_2d_fused", dict(tuning["tangent"], groups=(kept_groups or {}).get(
-            "tangent", tuning["tangent"].get("groups", 1))))
-        note = ("per-step time = fused phase / nt (includes launch gaps); p_{l+1} is written "
-                "into the kept history in HBM")
+        rf = roofline(
+            "k_tangent_rows (fused forward + tangent step, writing the kept history; per "
+            "leapfrog step, all shot groups)", b_tan, phases["forward_tangent"] / 1e3 / nt,
+            traffic_for("asteroid_2d fused", tuning_kept["tangent"], uniform), peak, peak_kind,
+            l2_note, "per-step time = fused phase / nt (includes launch gaps); p_{l+1} is "
+                     "written into the kept history in HBM")
+        adj_rf = roofline(
+            "k_adjoint_rows (reverse step on the kept history)", b_adj,
+            phases["adjoint"] / 1e3 / nt,
+            traffic_for("asteroid_2d reverse", tuning_kept["adjoint"], uniform), peak,
+            peak_kind, l2_note, "per-step time = reverse phase / nt")
     else:
-        bytes_fwd = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
-        fwd_launch_s = statistics.mean(fwd_ms) / 1e3 / nt   # includes launch gaps
-        kernel = "k_step (batched forward leapfrog step)"
-        tkey = ("asteroid_2d", tuning["forward"])
-        note = ("per-launch time = forward phase / nt (includes launch gaps); state "
-                "(2 x 32 MB) is L2-resident")
-    achieved = bytes_fwd / fwd_launch_s / 1e9
+        rf = roofline("k_step (batched forward leapfrog step)", b_fwd,
+                      phases["forward"] / 1e3 / nt,
+                      traffic_for("asteroid_2d forward", tuning["forward"], uniform), peak,
+                      peak_kind, l2_note, "per-launch time = forward phase / nt")
+        adj_rf = None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": describe(w), "nodes": n, "shots": S, "nt": nt,
+        "config": {"workload": describe(w, layout), "nodes": n, "shots": S, "nt": nt,
                    "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
-                   "tuning": tuning, "adjoint": adjoint_mode, "kept_groups": kept_groups,
+                   "tuning": tuning_kept, "adjoint": adjoint_mode, "kept_groups": kept_groups,
                    "stiffness": "uniformly strided ELL" if uniform else "sliced ELL",
                    "l2": "flushed between timed steps (256 MB write)"},
         "phases_ms": phases,
         "forward_updates_per_s": fwd_rate,
         "single_source_forward_updates_per_s": single_rate,
         "batched_vs_single_source": fwd_rate / single_rate,
-        "roofline": {"kernel": kernel, "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": traffic_for(tkey[0], tkey[1], keep_states, uniform),
-                     "algorithmic_bytes_per_launch": bytes_fwd,
-                     "note": note},
+        "roofline": rf,
+        "adjoint_roofline": adj_rf,
+        "c3_checkpointed": c3,
         "e2e": {"value": units_per_step * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -895,7 +1055,7 @@ def main():
     if not args.no_hbm_leg:
         out["hbm_workload"] = guarded(hbm_leg, mg, torch, dev)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, dt)
+        out["cpu_baseline"] = cpu_baseline(dt)
     print(json.dumps(out))
     return 0
 
