@@ -103,6 +103,7 @@ def apply_tuning(mesh, spec):
         if kind == "forward":
             mesh.set_min_blocks(t.get("min_blocks", 0))
             mesh.set_row_sweep(t.get("sweep", 0))
+            mesh.set_tma_tiles(t.get("tma", 0))
 
 
 def dist_env():
@@ -223,7 +224,8 @@ TRAFFIC = {
 def shape_key(t):
     """The launch-shape fields of a kind's tuning that change its traffic."""
     return (t["batch"], t["tile_rows"], t.get("groups", 1), t.get("min_blocks", 0),
-            t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0))
+            t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0)) + (
+        (t["tma"],) if t.get("tma", 0) else ())
 
 
 def sources_sha1():
@@ -303,7 +305,7 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
         # register cap and row sweep of the chosen row shape, each timed as
         # the best of three whole runs (the 32-step autotune windows do not
         # always separate them)
-        if mesh.tuning()["forward"]["tile_rows"] == 0:
+        if mesh.tuning()["forward"]["tile_rows"] == 0 and mesh.tuning()["forward"]["tma"] == 0:
             best = None
             for cap in (0, 5):
                 for sweep in (0, 4):

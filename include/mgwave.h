@@ -330,6 +330,26 @@ int mg_mesh_set_row_sweep(mg_mesh* mesh, int blocks);
 /* The forward row sweep (>= 0), or MG_ERR_ARG for a null handle. */
 int mg_mesh_get_row_sweep(const mg_mesh* mesh);
 
+/* Forward step on row tiles staged by the bulk-copy engine: rows > 0 (a
+ * multiple of 32, at most 1024) makes the forward kind (forward, recompute
+ * and kept-history steps) run a persistent kernel of one CTA per SM in
+ * which a producer warp copies, per work item (a tile of `rows` Morton
+ * rows and 32 shot columns), the tile's own and halo rows of p_l and its
+ * local stiffness into one of two shared-memory buffers (cp.async.bulk on
+ * mbarriers) while eight consumer warps compute the previous item from
+ * shared memory.  Same arithmetic and bits as the row kernels.  Needs whole
+ * 32-column items (padded shot counts of 32 or more) and a double buffer
+ * that fits a CTA's shared memory, else the propagation call fails with
+ * MG_ERR_UNSUPPORTED.  Its waits are bounded; a wait that runs out is
+ * reported by mg_mesh_device_status.  0 (default) turns it off.  Measured
+ * slower than the row kernels (ellipsoid_3d 2620 vs 538 us per step: the
+ * copy engine takes the 128-byte row copies one at a time), so it is not
+ * an autotuner candidate.  Drops the cached graphs.  Errors: MG_ERR_ARG for
+ * other values. */
+int mg_mesh_set_tma_tiles(mg_mesh* mesh, int rows);
+/* Rows per tile of that kernel (0: off), or MG_ERR_ARG for a null handle. */
+int mg_mesh_get_tma_tiles(const mg_mesh* mesh);
+
 /* Generation of the handle's checkpoints and kept forward states: a count
  * (>= 0) that changes whenever a call writes, drops or invalidates them
  * (mg_forward, mg_forward_jacobian_apply, mg_jacobian_T_apply without

@@ -92,6 +92,8 @@ SIGNATURES = {
     "mg_mesh_get_gather_ring": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_mesh_set_row_sweep": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_get_row_sweep": (C.c_int, [C.c_void_p]),
+    "mg_mesh_set_tma_tiles": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_get_tma_tiles": (C.c_int, [C.c_void_p]),
     "mg_mesh_checkpoint_generation": (C.c_int64, [C.c_void_p]),
     "mg_mesh_set_persistent": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_int]),
     "mg_mesh_set_bulk_copies": (C.c_int, [C.c_void_p, C.c_int]),

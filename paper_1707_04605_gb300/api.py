@@ -155,6 +155,12 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_gather_ring(self.handle, int(k), int(depth)),
                 "mg_mesh_set_gather_ring")
 
+    def set_tma_tiles(self, rows: int):
+        """Rows per tile of the bulk-copy tiled forward (mg_mesh_set_tma_tiles);
+        0: off."""
+        L.check(self._lib.mg_mesh_set_tma_tiles(self.handle, int(rows)),
+                "mg_mesh_set_tma_tiles")
+
     def set_row_sweep(self, blocks: int):
         """Consecutive row blocks per CTA of the forward row kernel
         (mg_mesh_set_row_sweep); 0 or 1: one."""
@@ -217,6 +223,7 @@ class Mesh:
         for name, k in self.KINDS.items():
             d[name]["ring"] = int(ring[k])
         d["forward"]["sweep"] = int(self._lib.mg_mesh_get_row_sweep(self.handle))
+        d["forward"]["tma"] = int(self._lib.mg_mesh_get_tma_tiles(self.handle))
         return d
 
     def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmgwave.so")
 SOURCES = ["mesh_host.cpp", "kernels.cu", "kernels_rows.cu", "kernels_ring.cu", "kernels_tiled.cu",
-           "kernels_bulk.cu", "capi.cu",
+           "kernels_bulk.cu", "kernels_tma.cu", "capi.cu",
            "static_scratch.cu", "batch.cu", "projected.cu",
            "inversion.cu", "approx.cu", "mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

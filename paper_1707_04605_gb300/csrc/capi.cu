@@ -119,6 +119,7 @@ struct mg_mesh {
     int bulk = 0;         // forward: neighbour rows staged by bulk async copies
     int ring = 0;         // row kernels: gather ring of 4 or 8 slots per lane, 0 = plain loads
     int sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
+    int tma = 0;          // forward: rows per tile of the bulk-copy tiled kernel (0 = off)
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
@@ -340,15 +341,15 @@ int prepare(mg_mesh* M, const double* eps, const mg_shots* shots, const double* 
   MG_TRY(build_events(M, shots, pp.ev));
   MG_TRY(ensure_tiles(M));
   // the status word of bounded device waits exists before any graph capture
-  if (M->tune[0].bulk && !err_word(M)) return MG_ERR_OOM;
+  if ((M->tune[0].bulk || M->tune[0].tma) && !err_word(M)) return MG_ERR_OOM;
   return MG_OK;
 }
 
 // Tile tables for every tile size the kernel kinds use, built on the host
 // and uploaded on first use.
 int ensure_tiles(mg_mesh* M) {
-  for (const auto& t : M->tune) {
-    const int P = t.tile_rows;
+  for (int k = 0; k < 4; ++k) {
+    const int P = k < 3 ? M->tune[k].tile_rows : M->tune[0].tma;
     if (P <= 0 || M->tiles.count(P)) continue;
     mg::HostTiles T;
     MG_TRY(mg::build_tiles(M->hm, P, T));
@@ -387,6 +388,26 @@ int group_cols(const mg_mesh* M, int kind, int S_pad) {
 // the row kernel (no tiles, or the tiled footprint exceeds shared memory).
 // The tangent stages two states per pass, so it passes half as many shots
 // to stay within the one-state footprint.
+// Device tables of the P-row tiling (built by ensure_tiles), or n_tiles = 0.
+mg::DevTiles tile_tables(mg_mesh* M, int P) {
+  mg::DevTiles T{};
+  auto it = M->tiles.find(P);
+  if (P <= 0 || it == M->tiles.end()) return T;
+  const mg_mesh::TileTables& D = it->second;
+  T.P = P;
+  T.n_tiles = D.n_tiles;
+  T.ell_off = P_<const int64_t>(D.ell_off);
+  T.ell_idx = P_<const uint16_t>(D.ell_idx);
+  T.ell_val = P_<const float>(D.ell_val);
+  T.slice_info = P_<const int32_t>(D.sinfo);
+  T.halo_off = P_<const int64_t>(D.halo_off);
+  T.halo_cnt = P_<const int32_t>(D.halo_cnt);
+  T.halo = P_<const int32_t>(D.halo);
+  T.max_ell = D.max_ell;
+  T.max_halo = D.max_halo;
+  return T;
+}
+
 mg::DevTiles dev_tiles(mg_mesh* M, int cols, int kind) {
   mg::DevTiles T{};
   const int P = M->tune[kind].tile_rows;
@@ -429,6 +450,13 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   b.ring = M->tune[0].ring;
   b.sweep = M->tune[0].sweep;
   b.pdl = M->dep_launch;
+  if (M->tune[0].tma) {
+    const mg::DevTiles TT = tile_tables(M, M->tune[0].tma);
+    int* err = err_word(M);
+    if (!err) return MG_ERR_OOM;
+    if (!TT.n_tiles) return MG_ERR_ARG;
+    return mg::launch_step_tma(b, TT, S_pad, err, st);
+  }
   if (M->tune[0].bulk) {
     int* err = err_word(M);
     if (!err) return MG_ERR_OOM;
@@ -999,6 +1027,15 @@ int mg_mesh_set_row_sweep(mg_mesh* M, int blocks) {
 }
 
 int mg_mesh_get_row_sweep(const mg_mesh* M) { return M ? M->tune[0].sweep : MG_ERR_ARG; }
+
+int mg_mesh_set_tma_tiles(mg_mesh* M, int rows) {
+  if (!M || rows < 0 || rows > 1024 || rows % mg::kSliceH) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->tune[0].tma = rows;
+  return MG_OK;
+}
+
+int mg_mesh_get_tma_tiles(const mg_mesh* M) { return M ? M->tune[0].tma : MG_ERR_ARG; }
 
 int64_t mg_mesh_checkpoint_generation(const mg_mesh* M) { return M ? M->ck_gen : MG_ERR_ARG; }
 
@@ -1646,8 +1683,9 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
   // blocks per CTA (mg_mesh_set_row_sweep) apply to the forward only;
   // the row kernels with a gather ring of 4 or 8 slots to every kind (a
   // ring that exceeds a CTA's shared memory is skipped); the bulk-copy
-  // kernel is not a candidate (measured slower on every workload: 2D 41.6
-  // vs 19.7 us, 3D 769 vs 532 us per step)
+  // kernel and the bulk-copy tiled kernel are not candidates (measured
+  // slower on every workload: 2D 41.6 and 92.7 vs 19.7 us, 3D 769 and
+  // 2620 vs 532 us per step)
   const mg_mesh::Tuning shapes[] = {
       {1, 0, 32},          {2, 0, 32},          {4, 0, 32},          {1, 64, 32},
       {1, 64, 16},         {1, 128, 32},        {1, 128, 16},        {1, 256, 32},
@@ -1688,7 +1726,9 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
     float ms[n_shapes];
     for (int i = 0; i < n_shapes && rc == MG_OK; ++i) {
       ms[i] = 1e30f;
-      if ((shapes[i].min_blocks || shapes[i].bulk || shapes[i].sweep) && kind != 0) continue;
+      if ((shapes[i].min_blocks || shapes[i].bulk || shapes[i].sweep || shapes[i].tma) &&
+          kind != 0)
+        continue;
       rc = time_of(kind, shapes[i], &ms[i]);
     }
     if (rc != MG_OK) break;

@@ -128,6 +128,14 @@ int launch_step(const StepArgs& a, int S_pad, cudaStream_t st);
 // (kernels_bulk.cu); err: device int set to 1 when a bounded wait ran out,
 // 2 when a copy address was misaligned.
 int launch_step_bulk(const StepArgs& a, int S_pad, int* err, cudaStream_t st);
+// Forward step on row tiles staged by bulk copies with a producer warp and
+// consumer warps (kernels_tma.cu); persistent grid of one CTA per SM, each
+// sweeping a contiguous range of tiles in items of 32 shot columns.
+// MG_ERR_UNSUPPORTED when the launch's columns are not whole 32-column
+// items or its double buffer exceeds a CTA's shared memory; err: device int
+// set to 1 when a bounded wait ran out.
+int launch_step_tma(const StepArgs& a, const DevTiles& T, int S_pad, int* err, cudaStream_t st);
+size_t tma_smem_bytes(const DevTiles& T);
 int launch_step_single(const StepArgs& a, int shot, cudaStream_t st);
 int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st);
 int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st);

@@ -21,6 +21,7 @@
 #include "device_util.cuh"
 #include "kernels.cuh"
 #include "mg_internal.h"
+#include "async_copy.cuh"
 
 namespace mg {
 namespace {
@@ -29,54 +30,12 @@ using namespace dev;
 
 constexpr int kBulkWarps = 4;
 constexpr int kBulkThreads = 32 * kBulkWarps;
-constexpr long long kWaitLimit = 1ll << 20;   // try_wait polls before giving up (~1 s)
 
-__device__ __forceinline__ uint32_t s_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+using namespace ac;
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile(
-      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
-      ::"r"(s_addr(bar)), "r"(bytes)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(s_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase `parity`; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < kWaitLimit; ++i)
-    if (mbar_test(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(s_addr(dst)), "l"(src), "r"(bytes), "r"(s_addr(bar))
-      : "memory");
-}
-
-// Orders this thread's generic-proxy accesses to shared memory before later
-// async-proxy writes (the next chunk's copies into the same slots).
-__device__ __forceinline__ void fence_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  ac::mbar_init(bar, 1);
+  mbar_init_fence();
 }
 
 __device__ __forceinline__ int2 entry_at(const int2* e, int w, int k, int row) {

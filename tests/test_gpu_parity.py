@@ -690,3 +690,49 @@ def test_unknown_and_unsupported_flags_are_refused(mg):
     with pytest.raises(L.MgError) as e:
         mg.forward(mesh, eps, w.shots, s, dt, persistent=True, keep_states=True)
     assert e.value.code == L.MG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("make,kw,rows", [
+    (configs.asteroid_2d, dict(n_refine=1, S=100, nt=300), 128),
+    (configs.asteroid_2d, dict(n_refine=2, S=37, nt=200), 64),
+    (configs.asteroid_2d, dict(n_refine=1, S=300, nt=150), 256),
+    (configs.ellipsoid_3d, dict(n_refine=1, S=64, nt=120), 128)])
+def test_tma_tiled_forward_gives_identical_results(mg, make, kw, rows):
+    """Row tiles staged by bulk copies (producer and consumer warps, double
+    buffer) do the row kernel's FMAs in the same order: the forward traces
+    and the gradient (whose recompute runs the forward kind) carry the same
+    bits, with graphs and plain launches; no bounded wait runs out."""
+    w = make(**kw)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    W = _dev(np.random.default_rng(13).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    level = w.mesh.n_levels - 1 if w.mesh.n_levels < 2 else 1
+
+    def run(flags=0):
+        return (mg.forward(mesh, eps, w.shots, s, dt, flags=flags),
+                mg.jacobian_T_apply(mesh, level, eps, w.shots, s, dt, W, ckpt_every=64,
+                                    flags=flags))
+
+    ref = run()
+    mesh.set_tma_tiles(rows)
+    assert mesh.tuning()["forward"]["tma"] == rows
+    for flags in (0, mg._lib.MG_NO_GRAPH):
+        out = run(flags)
+        assert mesh.device_status() == 0
+        assert torch.equal(ref[0], out[0])
+        assert torch.equal(ref[1], out[1])
+
+
+def test_tma_tiled_forward_refuses_narrow_batches(mg):
+    """Fewer than 32 padded shot columns cannot form a work item."""
+    from paper_1707_04605_gb300 import _lib as L
+
+    w = configs.asteroid_2d(n_refine=1, S=6, nt=20)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tma_tiles(128)
+    dt = oracle_dt(w)
+    with pytest.raises(L.MgError) as e:
+        mg.forward(mesh, _dev(w.eps), w.shots, _dev(w.wavelet(dt)), dt)
+    assert e.value.code == L.MG_ERR_UNSUPPORTED
