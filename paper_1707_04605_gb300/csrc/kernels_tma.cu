@@ -58,6 +58,7 @@ constexpr int kHW = 32;                 // shot columns per work item
 constexpr int kLPR = kHW / 4;           // lanes per row (one float4 each)
 constexpr int kRPW = 32 / kLPR;         // rows per consumer warp and pass
 constexpr int kRPP = kCW * kRPW;        // rows per pass of the consumers
+constexpr int kBatch = 8;               // producer: row copies per lane per batch
 
 __host__ __device__ __forceinline__ size_t al128(size_t x) { return (x + 127) / 128 * 128; }
 
@@ -145,10 +146,21 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_tma(StepArgs a, DevTile
         bulk_copy(buf + L.val, T.ell_val + e0, (uint32_t)(ne * sizeof(float)), &full[b]);
       }
       const float* src = a.p + a.col0 + ch * kHW;
-      for (int j = lane; j < Pt + nh; j += 32) {
-        const int64_t g = j < Pt ? t0 + j : (int64_t)__ldg(T.halo + h0 + (j - Pt));
-        bulk_copy(buf + (size_t)j * kHW * sizeof(float), src + g * a.ld,
-                  kHW * sizeof(float), &full[b]);
+      // the halo row ids of a batch are loaded together, then copied
+      for (int j0 = 0; j0 < Pt + nh; j0 += 32 * kBatch) {
+        int64_t gs[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int j = j0 + 32 * u + lane;
+          gs[u] = j < Pt ? t0 + j : j < Pt + nh ? (int64_t)__ldg(T.halo + h0 + (j - Pt)) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int j = j0 + 32 * u + lane;
+          if (gs[u] >= 0)
+            bulk_copy(buf + (size_t)j * kHW * sizeof(float), src + gs[u] * a.ld,
+                      kHW * sizeof(float), &full[b]);
+        }
       }
       issued = i + 1;
     }
