@@ -40,6 +40,14 @@ namespace {
 
 constexpr int kMaxDim = 3;
 
+// Step kernels run as programmatic dependents of the previous kernel on
+// the stream: each waits for it to complete (and its stores to be visible)
+// before touching any state, then lets the next launch be scheduled.
+__device__ __forceinline__ void pdl_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // per node: {dt / C_i, R_i + S_i}
 __global__ void k_flux_coefs(CoefArgs c, const double* __restrict__ xi, double dt,
                              float2* __restrict__ out) {
@@ -60,6 +68,7 @@ template <int D>
 __global__ void k_flux_q(int64_t m, int ld4, const int32_t* __restrict__ cells,
                          const float* __restrict__ grad, const float* __restrict__ damp,
                          const float4* __restrict__ p, float4* __restrict__ q, float dt) {
+  pdl_sync();
   const int64_t total = m * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -88,17 +97,18 @@ __global__ void k_flux_q(int64_t m, int ld4, const int32_t* __restrict__ cells,
   }
 }
 
-// p <- p + dt/C (f delta_src - (R+S) p - sum_{e ni i} sum_k w[e,i,k] q^(k)_e);
-// sources and traces of the row's shots
+// pout <- p + dt/C (f delta_src - (R+S) p - sum_{e ni i} sum_k w[e,i,k] q^(k)_e)
+// (pout may be p); sources and traces of the row's shots
 template <int D>
 __global__ void k_flux_p(int64_t n, int64_t m, int ld4, const int64_t* __restrict__ nc_ptr,
                          const int32_t* __restrict__ nc_cell, const float* __restrict__ w,
                          const float2* __restrict__ coef, const float4* __restrict__ q,
-                         float4* __restrict__ p, const int32_t* __restrict__ src_ptr,
+                         const float4* p, float4* pout, const int32_t* __restrict__ src_ptr,
                          const int32_t* __restrict__ src_shot, const int32_t* __restrict__ rec_ptr,
                          const int32_t* __restrict__ rec_shot,
                          const int32_t* __restrict__ rec_trace, float f, float* __restrict__ traces,
                          int nt, int l) {
+  pdl_sync();
   const int64_t total = n * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -132,7 +142,7 @@ __global__ void k_flux_p(int64_t n, int64_t m, int ld4, const int64_t* __restric
     pv.y = fmaf(c.x, fmaf(-c.y, pv.y, rhs.y), pv.y);
     pv.z = fmaf(c.x, fmaf(-c.y, pv.z, rhs.z), pv.z);
     pv.w = fmaf(c.x, fmaf(-c.y, pv.w, rhs.w), pv.w);
-    p[t] = pv;
+    pout[t] = pv;
     const int r0 = __ldg(rec_ptr + i), r1 = __ldg(rec_ptr + i + 1);
     for (int r = r0; r < r1; ++r) {
       const int d = __ldg(rec_shot + r) - 4 * c4;
@@ -172,6 +182,7 @@ __global__ void k_flux_p_tan(int64_t n, int64_t m, int ld4, const int64_t* __res
                              const int32_t* __restrict__ rec_shot,
                              const int32_t* __restrict__ rec_trace, float f,
                              float* __restrict__ traces, int nt, int l) {
+  pdl_sync();
   const int64_t total = n * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -231,8 +242,13 @@ __global__ void k_flux_p_tan(int64_t n, int64_t m, int ld4, const int64_t* __res
 
 // Adjoint node kernel of reverse step l.  a = adjoint of p_{l+1}: what step
 // l+1 sent back (tp + dt sum_k B^(k)T Qt^(k); zero when l = nt-1) plus the
-// weights of the row's receivers at sample l.  Accumulates a (p_{l+1} - p_l)
-// in FP64, then stores r = a dt/C and tp = a - (R+S) r.
+// weights of the row's receivers at sample l.  Sums a (p_{l+1} - p_l) over
+// the node's shots in FP32 (the threads of a node are consecutive lanes:
+// the float4s of a node within a warp are summed by a fixed shuffle tree)
+// and adds one partial per warp segment of 32 float4 to the FP64 time
+// accumulator hacc[i][segment] (GB300's FP64 rate is a small fraction of
+// its FP32 rate: one FP64 add per node and step), then stores r = a dt/C
+// and tp = a - (R+S) r.
 template <int D>
 __global__ void k_flux_adj_p(int64_t n, int64_t m, int ld4, const int64_t* __restrict__ nc_ptr,
                              const int32_t* __restrict__ nc_cell, const float* __restrict__ w,
@@ -243,6 +259,7 @@ __global__ void k_flux_adj_p(int64_t n, int64_t m, int ld4, const int64_t* __res
                              const int32_t* __restrict__ rec_shot,
                              const int32_t* __restrict__ rec_trace,
                              const float* __restrict__ W, int nt, int l, int first, float dt) {
+  pdl_sync();
   const int64_t total = n * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -278,11 +295,21 @@ __global__ void k_flux_adj_p(int64_t n, int64_t m, int ld4, const int64_t* __res
       if (d == 3) a.w += v;
     }
     const float4 x1 = __ldg(p1 + t), x0 = __ldg(p0 + t);
-    double* h = hacc + 4 * t;
-    h[0] += (double)a.x * ((double)x1.x - (double)x0.x);
-    h[1] += (double)a.y * ((double)x1.y - (double)x0.y);
-    h[2] += (double)a.z * ((double)x1.z - (double)x0.z);
-    h[3] += (double)a.w * ((double)x1.w - (double)x0.w);
+    float h = a.x * (x1.x - x0.x);
+    h = fmaf(a.y, x1.y - x0.y, h);
+    h = fmaf(a.z, x1.z - x0.z, h);
+    h = fmaf(a.w, x1.w - x0.w, h);
+    // ld4 is a power of two or a multiple of 32, and t mod 32 is the lane:
+    // the gw lanes of a node's segment are active together
+    const int gw = ld4 < 32 ? ld4 : 32;
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask =
+        gw == 32 ? 0xffffffffu : (((1u << gw) - 1u) << (lane & ~(gw - 1)));
+    for (int off = gw / 2; off > 0; off >>= 1) h += __shfl_xor_sync(gmask, h, off);
+    if ((c4 & (gw - 1)) == 0) {
+      const int nseg = ld4 < 32 ? 1 : ld4 / 32;
+      hacc[i * nseg + c4 / 32] += (double)h;
+    }
     const float2 c = __ldg(coef + i);
     const float4 r = make_float4(a.x * c.x, a.y * c.x, a.z * c.x, a.w * c.x);
     rr[t] = r;
@@ -296,6 +323,7 @@ template <int D>
 __global__ void k_flux_adj_q(int64_t m, int ld4, const int32_t* __restrict__ cells,
                              const float* __restrict__ grad, const float* __restrict__ damp,
                              const float4* __restrict__ rr, float4* __restrict__ Qt, float dt) {
+  pdl_sync();
   const int64_t total = m * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -325,13 +353,13 @@ __global__ void k_flux_adj_q(int64_t m, int ld4, const int32_t* __restrict__ cel
   }
 }
 
-// gC_i = -sum_s hacc[i][s] / C_i (fixed order over the shots)
-__global__ void k_flux_hsum(int64_t n, int ld, const double* __restrict__ hacc,
+// gC_i = -sum_seg hacc[i][seg] / C_i (fixed order over the shot segments)
+__global__ void k_flux_hsum(int64_t n, int nseg, const double* __restrict__ hacc,
                             const double* __restrict__ C, double* __restrict__ gC) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = 0.0;
-  for (int j = 0; j < ld; ++j) s += hacc[i * ld + j];
+  for (int j = 0; j < nseg; ++j) s += hacc[i * nseg + j];
   gC[i] = -s / C[i];
 }
 
@@ -379,6 +407,21 @@ struct Scratch {
   }
 };
 
+// Launch of a step kernel as a programmatic dependent (see pdl_sync).
+template <class... KArgs, class... Args>
+void launch_pdl(void (*kern)(KArgs...), int grid, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 int grid_for(int64_t total) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
 }
@@ -403,26 +446,28 @@ struct Flux {
   void step_q(float* p, float* q) const {
     const int g = grid_for(m * ld4);
     if (d == 2)
-      k_flux_q<2><<<g, 256, 0, st>>>(m, ld4, cells, grad, damp,
+      launch_pdl(k_flux_q<2>, g, st, m, ld4, cells, grad, damp,
                                       reinterpret_cast<const float4*>(p),
                                       reinterpret_cast<float4*>(q), (float)dt);
     else
-      k_flux_q<3><<<g, 256, 0, st>>>(m, ld4, cells, grad, damp,
+      launch_pdl(k_flux_q<3>, g, st, m, ld4, cells, grad, damp,
                                       reinterpret_cast<const float4*>(p),
                                       reinterpret_cast<float4*>(q), (float)dt);
   }
-  void step_p(const float* q, float* p, float* traces, int l) const {
+  // p_{l+1} into pout (nullptr: in place over p)
+  void step_p(const float* q, float* p, float* traces, int l, float* pout = nullptr) const {
     const int g = grid_for(n * ld4);
+    float4* po = reinterpret_cast<float4*>(pout ? pout : p);
     if (d == 2)
-      k_flux_p<2><<<g, 256, 0, st>>>(n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
+      launch_pdl(k_flux_p<2>, g, st, n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
                                       reinterpret_cast<const float4*>(q),
-                                      reinterpret_cast<float4*>(p), sp, ss, rp, rs, rt, fl[l],
-                                      traces, nt, l);
+                                      reinterpret_cast<const float4*>(p), po, sp, ss, rp, rs, rt,
+                                      fl[l], traces, nt, l);
     else
-      k_flux_p<3><<<g, 256, 0, st>>>(n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
+      launch_pdl(k_flux_p<3>, g, st, n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
                                       reinterpret_cast<const float4*>(q),
-                                      reinterpret_cast<float4*>(p), sp, ss, rp, rs, rt, fl[l],
-                                      traces, nt, l);
+                                      reinterpret_cast<const float4*>(p), po, sp, ss, rp, rs, rt,
+                                      fl[l], traces, nt, l);
   }
 };
 
@@ -676,13 +721,13 @@ extern "C" int mg_jacobian_apply_pml(mg_mesh* M, int level, const double* eps,
     F.step_q(p, q);
     F.step_q(dp, dq);
     if (F.d == 2)
-      k_flux_p_tan<2><<<gp, 256, 0, st>>>(
+      launch_pdl(k_flux_p_tan<2>, gp, st,
           n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef, ratio,
           reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
           reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp, F.rs,
           F.rt, F.fl[l], tr, nt, l);
     else
-      k_flux_p_tan<3><<<gp, 256, 0, st>>>(
+      launch_pdl(k_flux_p_tan<3>, gp, st,
           n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef, ratio,
           reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
           reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp, F.rs,
@@ -716,7 +761,11 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   const int64_t n = F.n, m = F.m, R = F.R, nc = hm->n_cells_level[level];
   const int K = std::min(ckpt_every, nt);
   const int nck = (nt + K - 1) / K;
+  // one segment (ckpt_every >= nt): the forward keeps every state, and the
+  // reverse steps run with no recompute
+  const bool keep = nck == 1;
   const size_t ns = (size_t)n * F.ld, qs = (size_t)F.d * m * F.ld;
+  const int nseg = F.ld4 < 32 ? 1 : F.ld4 / 32;
   const float* W = F.host ? X.put(w, (size_t)R * nt) : w;
   float* ck_p = X.get<float>(ns * nck);
   float* ck_q = X.get<float>(qs * nck);
@@ -727,7 +776,7 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   float* tp = X.get<float>(ns);
   float* rr = X.get<float>(ns);
   float* Qt = X.get<float>(qs);
-  double* hacc = X.get<double>(ns);
+  double* hacc = X.get<double>((size_t)n * nseg);
   double* C = X.get<double>(n);
   double* gC = X.get<double>(n);
   double* vol = X.put(hm->cell_vol);
@@ -744,11 +793,18 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   if (cudaMemsetAsync(p, 0, ns * sizeof(float), st) ||
       cudaMemsetAsync(q, 0, qs * sizeof(float), st) ||
       cudaMemsetAsync(Qt, 0, qs * sizeof(float), st) ||
-      cudaMemsetAsync(hacc, 0, ns * sizeof(double), st))
+      cudaMemsetAsync(hacc, 0, (size_t)n * nseg * sizeof(double), st))
     return MG_ERR_CUDA;
   int64_t launches = 0;
-  // forward, keeping (p_l, q_{l-1/2}) at l = 0, K, 2K, ...
+  // forward, keeping (p_l, q_{l-1/2}) at l = 0, K, 2K, ... (or every p_l)
+  if (keep && cudaMemsetAsync(seg, 0, ns * sizeof(float), st)) return MG_ERR_CUDA;
   for (int l = 0; l < nt; ++l) {
+    if (keep) {   // p_l in seg slot l, p_{l+1} written to slot l + 1
+      F.step_q(seg + ns * l, q);
+      F.step_p(q, seg + ns * l, trd, l, seg + ns * (l + 1));
+      launches += 2;
+      continue;
+    }
     if (l % K == 0) {
       if (cudaMemcpyAsync(ck_p + ns * (l / K), p, ns * sizeof(float), cudaMemcpyDeviceToDevice,
                           st) ||
@@ -765,11 +821,12 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   const float fdt = (float)dt;
   for (int c = nck - 1; c >= 0; --c) {
     const int l0 = c * K, l1 = std::min(nt, l0 + K);
-    if (cudaMemcpyAsync(p, ck_p + ns * c, ns * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
-        cudaMemcpyAsync(q, ck_q + qs * c, qs * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
-        cudaMemcpyAsync(seg, p, ns * sizeof(float), cudaMemcpyDeviceToDevice, st))
+    if (!keep &&
+        (cudaMemcpyAsync(p, ck_p + ns * c, ns * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
+         cudaMemcpyAsync(q, ck_q + qs * c, qs * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
+         cudaMemcpyAsync(seg, p, ns * sizeof(float), cudaMemcpyDeviceToDevice, st)))
       return MG_ERR_CUDA;
-    for (int l = l0; l < l1; ++l) {
+    for (int l = l0; l < l1 && !keep; ++l) {
       F.step_q(p, q);
       F.step_p(q, p, trd, l);
       if (cudaMemcpyAsync(seg + ns * (l + 1 - l0), p, ns * sizeof(float),
@@ -782,21 +839,21 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
       const float4* p0 = reinterpret_cast<const float4*>(seg + ns * (l - l0));
       const int first = l == nt - 1;
       if (F.d == 2) {
-        k_flux_adj_p<2><<<gp, 256, 0, st>>>(n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+        launch_pdl(k_flux_adj_p<2>, gp, st, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
                                              reinterpret_cast<const float4*>(Qt),
                                              reinterpret_cast<float4*>(tp),
                                              reinterpret_cast<float4*>(rr), p1, p0, hacc, F.rp,
                                              F.rs, F.rt, W, nt, l, first, fdt);
-        k_flux_adj_q<2><<<gq, 256, 0, st>>>(m, F.ld4, F.cells, F.grad, F.damp,
+        launch_pdl(k_flux_adj_q<2>, gq, st, m, F.ld4, F.cells, F.grad, F.damp,
                                              reinterpret_cast<const float4*>(rr),
                                              reinterpret_cast<float4*>(Qt), fdt);
       } else {
-        k_flux_adj_p<3><<<gp, 256, 0, st>>>(n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+        launch_pdl(k_flux_adj_p<3>, gp, st, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
                                              reinterpret_cast<const float4*>(Qt),
                                              reinterpret_cast<float4*>(tp),
                                              reinterpret_cast<float4*>(rr), p1, p0, hacc, F.rp,
                                              F.rs, F.rt, W, nt, l, first, fdt);
-        k_flux_adj_q<3><<<gq, 256, 0, st>>>(m, F.ld4, F.cells, F.grad, F.damp,
+        launch_pdl(k_flux_adj_q<3>, gq, st, m, F.ld4, F.cells, F.grad, F.damp,
                                              reinterpret_cast<const float4*>(rr),
                                              reinterpret_cast<float4*>(Qt), fdt);
       }
@@ -806,7 +863,7 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   // gradient: C-sensitivity per node, per finest cell, restricted to the level
   const unsigned gn = (unsigned)((n + 255) / 256), gm = (unsigned)((m + 255) / 256);
   k_flux_mass<<<gn, 256, 0, st>>>(F.c, F.eps_d, C);
-  k_flux_hsum<<<gn, 256, 0, st>>>(n, F.ld, hacc, C, gC);
+  k_flux_hsum<<<gn, 256, 0, st>>>(n, nseg, hacc, C, gC);
   k_flux_cell_grad<<<gm, 256, 0, st>>>(m, F.k1, F.cells, vol, gC, gf);
   if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
   MG_FX(launch_restrict(nc, lp_d, li_d, gf, go, st));

@@ -132,6 +132,10 @@ def test_square_layer_jacobians_match_oracle(mg, with_sigma):
     g7 = mg.jacobian_T_apply_pml(mesh, level, _dev(eps), sh, _dev(s), dt, Wd, _dev(xi),
                                  _dev(zeta), ckpt_every=7).cpu().numpy()
     assert np.array_equal(g7, g)
+    # one segment: the forward keeps every state and nothing is recomputed
+    gk = mg.jacobian_T_apply_pml(mesh, level, _dev(eps), sh, _dev(s), dt, Wd, _dev(xi),
+                                 _dev(zeta), ckpt_every=len(s)).cpu().numpy()
+    assert np.array_equal(gk, g)
     gh = mg.jacobian_T_apply_pml(mesh, level, eps, sh, s, dt, W, xi, zeta, ckpt_every=32)
     assert np.array_equal(gh, g)
     jh = mg.jacobian_apply_pml(mesh, level, eps, sh, s, dt, v, xi, zeta)
