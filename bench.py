@@ -100,6 +100,8 @@ def apply_tuning(mesh, spec):
         mesh.set_kernel_tuning(kind, t["batch"], t["tile_rows"], t["src_tile"])
         mesh.set_shot_groups(t.get("groups", 1), kind)
         mesh.set_gather_ring(t.get("ring", 0), kind)
+        if "stream" in t:
+            mesh.set_l1_streaming(t["stream"], kind)
         if kind == "forward":
             mesh.set_min_blocks(t.get("min_blocks", 0))
             mesh.set_row_sweep(t.get("sweep", 0))
@@ -224,7 +226,7 @@ TRAFFIC = {
 def shape_key(t):
     """The launch-shape fields of a kind's tuning that change its traffic."""
     return (t["batch"], t["tile_rows"], t.get("groups", 1), t.get("min_blocks", 0),
-            t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0)) + (
+            t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0), t.get("stream", 0)) + (
         (t["tma"],) if t.get("tma", 0) else ())
 
 

@@ -93,6 +93,8 @@ SIGNATURES = {
     "mg_mesh_set_row_sweep": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_get_row_sweep": (C.c_int, [C.c_void_p]),
     "mg_mesh_set_tma_tiles": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_l1_streaming": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mg_mesh_get_l1_streaming": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_mesh_get_tma_tiles": (C.c_int, [C.c_void_p]),
     "mg_mesh_checkpoint_generation": (C.c_int64, [C.c_void_p]),
     "mg_mesh_set_persistent": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_int]),

@@ -155,6 +155,13 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_gather_ring(self.handle, int(k), int(depth)),
                 "mg_mesh_set_gather_ring")
 
+    def set_l1_streaming(self, on: bool, kind=None):
+        """Once-read loads of the row kernels without L1 allocation
+        (mg_mesh_set_l1_streaming) for one kind or all (None)."""
+        k = -1 if kind is None else self.KINDS[kind]
+        L.check(self._lib.mg_mesh_set_l1_streaming(self.handle, int(k), int(bool(on))),
+                "mg_mesh_set_l1_streaming")
+
     def set_tma_tiles(self, rows: int):
         """Rows per tile of the bulk-copy tiled forward (mg_mesh_set_tma_tiles);
         0: off."""
@@ -224,6 +231,11 @@ class Mesh:
             d[name]["ring"] = int(ring[k])
         d["forward"]["sweep"] = int(self._lib.mg_mesh_get_row_sweep(self.handle))
         d["forward"]["tma"] = int(self._lib.mg_mesh_get_tma_tiles(self.handle))
+        l1 = np.zeros(3, dtype=np.int32)
+        L.check(self._lib.mg_mesh_get_l1_streaming(self.handle, C.c_void_p(l1.ctypes.data)),
+                "mg_mesh_get_l1_streaming")
+        for name, k in self.KINDS.items():
+            d[name]["stream"] = int(l1[k])
         return d
 
     def autotune(self, eps, shots, wavelet, dt, steps=128, level=1, allow_cfl=False,

@@ -120,7 +120,8 @@ struct mg_mesh {
     int ring = 0;         // row kernels: gather ring of 4 or 8 slots per lane, 0 = plain loads
     int sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
     int tma = 0;          // forward: rows per tile of the bulk-copy tiled kernel (0 = off)
-  } tune[3];
+    int stream = 0;       // row kernels: once-read loads bypass L1 allocation
+  } tune[3] = {Tuning{1, 0, 32, 1, 0, 0, 0, 0, 0, 1}, Tuning{}, Tuning{}};
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
   int wu = 0;
@@ -449,6 +450,7 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   b.min_blocks = M->tune[0].min_blocks;
   b.ring = M->tune[0].ring;
   b.sweep = M->tune[0].sweep;
+  b.stream = M->tune[0].stream;
   b.pdl = M->dep_launch;
   if (M->tune[0].tma) {
     const mg::DevTiles TT = tile_tables(M, M->tune[0].tma);
@@ -471,6 +473,7 @@ int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st)
   mg::TangentArgs b = a;
   b.f.batch = M->tune[1].batch;
   b.f.ring = M->tune[1].ring;
+  b.f.stream = M->tune[1].stream;
   b.f.pdl = M->dep_launch;
   return mg::launch_tangent(b, S_pad, st);
 }
@@ -481,6 +484,7 @@ int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st)
   mg::AdjointArgs b = a;
   b.batch = M->tune[2].batch;
   b.ring = M->tune[2].ring;
+  b.stream = M->tune[2].stream;
   b.pdl = M->dep_launch;
   return mg::launch_adjoint(b, S_pad, st);
 }
@@ -1028,6 +1032,20 @@ int mg_mesh_set_row_sweep(mg_mesh* M, int blocks) {
 
 int mg_mesh_get_row_sweep(const mg_mesh* M) { return M ? M->tune[0].sweep : MG_ERR_ARG; }
 
+int mg_mesh_set_l1_streaming(mg_mesh* M, int kind, int on) {
+  if (!M || kind < -1 || kind > 2 || (on != 0 && on != 1)) return MG_ERR_ARG;
+  drop_graphs(M);
+  for (int k = 0; k < 3; ++k)
+    if (kind == -1 || kind == k) M->tune[k].stream = on;
+  return MG_OK;
+}
+
+int mg_mesh_get_l1_streaming(const mg_mesh* M, int32_t* out) {
+  if (!M || !out) return MG_ERR_ARG;
+  for (int k = 0; k < 3; ++k) out[k] = M->tune[k].stream;
+  return MG_OK;
+}
+
 int mg_mesh_set_tma_tiles(mg_mesh* M, int rows) {
   if (!M || rows < 0 || rows > 1024 || rows % mg::kSliceH) return MG_ERR_ARG;
   drop_graphs(M);
@@ -1239,6 +1257,7 @@ int mg_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg_shots* 
     float* seg = P<float>(M->seg);
     a.f.batch = M->tune[1].batch;
     a.f.ring = M->tune[1].ring;
+    a.f.stream = M->tune[1].stream;
     a.f.pdl = M->dep_launch;
     a.f.hint = M->cache_hints;
     const int W = group_cols(M, 1, pp.S_pad), NG = pp.S_pad / W;
@@ -1386,6 +1405,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
   a.f.traces = trf;
   a.f.batch = M->tune[1].batch;
   a.f.ring = M->tune[1].ring;
+  a.f.stream = M->tune[1].stream;
   a.f.pdl = M->dep_launch;
   a.f.hint = keep ? M->cache_hints : 0;   // p_{l-1} is last read here only when kept
   a.tcoef = P<const float2>(M->tcoef);
@@ -1521,6 +1541,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.step_base = nullptr;
   aa.batch = M->tune[2].batch;
   aa.ring = M->tune[2].ring;
+  aa.stream = M->tune[2].stream;
   aa.G = G;
   aa.Gc = G + acc;
   aa.H = G + 2 * acc;
@@ -1702,8 +1723,11 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
   // would otherwise bias against the first candidates
   for (int i = 0; i < 4 && rc == MG_OK; ++i) rc = run(2);
   if (rc == MG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MG_ERR_CUDA;
-  auto time_of = [&](int kind, const mg_mesh::Tuning& c, float* out) -> int {
+  // the L1 policy is the caller's setting, not a candidate
+  const int l1[3] = {M->tune[0].stream, M->tune[1].stream, M->tune[2].stream};
+  auto time_of = [&](int kind, mg_mesh::Tuning c, float* out) -> int {
     drop_graphs(M);
+    c.stream = l1[kind];
     M->tune[kind] = c;
     int r = run(kind);  // warm-up: tile tables, buffers, graphs
     float cand = 1e30f;
@@ -1743,6 +1767,7 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
       if (ms[i] <= ms[order[0]] * 1.01f) { first = i; break; }
     float best = ms[first];
     mg_mesh::Tuning pick = shapes[first];
+    pick.stream = l1[kind];
     // groups act only inside graph chunks (forward, tangent: runs of at
     // least `chunk` steps) and graph segments (adjoint: even segments), so
     // they are timed only when the timed runs use them
@@ -1751,6 +1776,7 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
       for (int G : {2, 4, 8}) {
         mg_mesh::Tuning c = shapes[order[top]];
         c.groups = G;
+        c.stream = l1[kind];
         M->tune[kind] = c;
         if (group_cols(M, kind, S_pad) == S_pad) continue;
         float t = 0.0f;

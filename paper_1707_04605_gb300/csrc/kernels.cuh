@@ -49,6 +49,7 @@ struct StepArgs {
   int32_t hint = 0;         // row kernels: L2 evict-first on the last read of pm
   int32_t ring = 0;         // row kernels: gather ring of 4 or 8 slots per lane (0 = plain loads)
   int32_t sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
+  int32_t stream = 0;       // row kernels: once-read data loaded without L1 allocation
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -83,6 +84,7 @@ struct AdjointArgs {
   int32_t pdl = 0;          // as in StepArgs
   int32_t hint = 0;         // row kernel: L2 evict-first on the read of pk
   int32_t ring = 0;         // row kernel: gather ring depth as in StepArgs
+  int32_t stream = 0;       // row kernel: once-read loads without L1 allocation
   float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;

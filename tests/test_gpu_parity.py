@@ -369,8 +369,9 @@ def test_wide_batch_row_shapes_cover_every_shot(mg):
 
 @pytest.mark.parametrize("batch", [1, 2, 4])
 def test_register_capped_forward_gives_identical_results(mg, batch):
-    """mg_mesh_set_min_blocks(5) only changes register allocation, and
-    mg_mesh_set_row_sweep only which CTA advances which rows: same bits."""
+    """mg_mesh_set_min_blocks(5) only changes register allocation,
+    mg_mesh_set_row_sweep only which CTA advances which rows, and
+    mg_mesh_set_l1_streaming only cache policy: same bits."""
     w = configs.asteroid_2d(n_refine=1, S=100, nt=300)
     eps = _dev(w.eps)
     mesh = mg.mesh_from_workload(w)
@@ -389,12 +390,17 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     out = run()
     assert torch.equal(ref[0], out[0])
     assert torch.equal(ref[1], out[1])
-    # consecutive row blocks per CTA (a ragged last sweep included)
+    # consecutive row blocks per CTA (a ragged last sweep included), and
+    # once-read loads without L1 allocation
     for sweep in (3, 7):
         mesh.set_row_sweep(sweep)
         out = run()
         assert torch.equal(ref[0], out[0])
         assert torch.equal(ref[1], out[1])
+    mesh.set_l1_streaming(not mesh.tuning()["forward"]["stream"], "forward")
+    out = run()
+    assert torch.equal(ref[0], out[0])
+    assert torch.equal(ref[1], out[1])
 
 
 @pytest.mark.parametrize("S,batch,groups,chunk", [(100, 2, 1, 128), (100, 1, 2, 128),
@@ -736,3 +742,39 @@ def test_tma_tiled_forward_refuses_narrow_batches(mg):
     with pytest.raises(L.MgError) as e:
         mg.forward(mesh, _dev(w.eps), w.shots, _dev(w.wavelet(dt)), dt)
     assert e.value.code == L.MG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("S,batch", [(100, 2), (100, 1), (37, 4), (300, 2)])
+def test_l1_streaming_gives_identical_results(mg, S, batch):
+    """Once-read loads without L1 allocation change only cache policy: the
+    forward (kept history and checkpoints), the lockstep and fused
+    tangents, the tangent on kept states and both J^T w paths keep their
+    bits either way."""
+    w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(-1, batch, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    rng = np.random.default_rng(14)
+    W = _dev(rng.standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    v = _dev(rng.standard_normal(w.mesh.n_cells[1]))
+
+    def run():
+        y = mg.forward(mesh, eps, w.shots, s, dt, keep_states=True)
+        gk = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
+                                 reuse_checkpoints=True)
+        jvk = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, reuse_states=True)
+        jv = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
+        yf, jvf = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
+        gf = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
+                                 reuse_checkpoints=True)
+        g = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64)
+        return y, gk, jvk, jv, yf, jvf, gf, g
+
+    mesh.set_l1_streaming(False)
+    ref = run()
+    mesh.set_l1_streaming(True)
+    assert all(mesh.tuning()[k]["stream"] == 1 for k in ("forward", "tangent", "adjoint"))
+    for a, b in zip(ref, run()):
+        assert torch.equal(a, b)
