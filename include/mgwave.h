@@ -334,11 +334,11 @@ int mg_mesh_get_row_sweep(const mg_mesh* mesh);
  * 1 loads the data a step reads once (the row's own state values that are
  * not gathered, its coefficients and its stiffness entries) with
  * L1::no_allocate, so that L1 keeps the neighbour rows the gathers reuse;
- * 0 loads them normally.  Same results.  Default 1 for the forward kind
- * (measured on GB300, same box: ellipsoid_3d 558.5 -> 539.8 us per step,
- * asteroid_2d 20.7 -> 20.1 us), 0 for the tangent and adjoint kinds (their
- * asteroid_2d steps were 5-9% slower with it).  Drops the cached graphs.
- * Errors: MG_ERR_ARG for other values. */
+ * 0 (default) loads them normally.  Same results.  Measured slower on
+ * GB300 (three alternating runs on one box: ellipsoid_3d forward 535 ->
+ * 556 us per step, the uneven batch's forward 842 -> 910 ms, the asteroid_2d
+ * tangent and reverse steps 5-9%), so it stays off.  Drops the cached
+ * graphs.  Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_l1_streaming(mg_mesh* mesh, int kind, int on);
 /* That switch of the forward, tangent and adjoint kinds into out[3]. */
 int mg_mesh_get_l1_streaming(const mg_mesh* mesh, int32_t* out);

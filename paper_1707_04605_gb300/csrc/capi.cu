@@ -121,7 +121,7 @@ struct mg_mesh {
     int sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
     int tma = 0;          // forward: rows per tile of the bulk-copy tiled kernel (0 = off)
     int stream = 0;       // row kernels: once-read loads bypass L1 allocation
-  } tune[3] = {Tuning{1, 0, 32, 1, 0, 0, 0, 0, 0, 1}, Tuning{}, Tuning{}};
+  } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
   int wu = 0;

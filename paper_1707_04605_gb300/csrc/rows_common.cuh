@@ -44,10 +44,7 @@ __device__ __forceinline__ void grid_dep_sync() {
 // and without L1 allocation when `na` is set (L1 keeps the neighbour rows
 // the gathers reuse).  NC: read-only data of the launch (no store of this
 // launch aliases it); otherwise the load is a memory access the compiler
-// keeps in place (the same thread may overwrite the data later), which also
-// issues it before the row's gathers: measured on the 3D forward, the gain
-// comes from that placement (without the clobber the same switch was 4%
-// slower).
+// keeps in place (the same thread may overwrite the data later).
 template <bool NC>
 __device__ __forceinline__ float4 ld_once(const float* p, int hint, int na) {
   float4 v;
