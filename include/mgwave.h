@@ -233,7 +233,10 @@ int mg_jacobian_apply(mg_mesh* mesh, int level, const double* eps,
  * with MG_REUSE_CHECKPOINTS and ckpt_every = nt needs no forward at all.
  *   traces, jv  [rec_ptr[n_shots]][nt] FP32 outputs (device, or host with
  *               MG_HOST_PTRS); other arguments as mg_jacobian_apply.
- *   flags       MG_HOST_PTRS, MG_ALLOW_CFL, MG_NO_GRAPH, MG_KEEP_STATES;
+ *   flags       MG_HOST_PTRS, MG_ALLOW_CFL, MG_NO_GRAPH, MG_KEEP_STATES, and
+ *               MG_PERSISTENT with MG_KEEP_STATES (several steps per
+ *               cooperative launch, as mg_forward's; ends with a stream
+ *               synchronisation, MG_ERR_TIMEOUT if a barrier wait ran out);
  *               MG_KEEP_CHECKPOINTS, MG_REUSE_CHECKPOINTS and
  *               MG_SINGLE_SOURCE return MG_ERR_UNSUPPORTED.
  * Row kernels only (the tiled tangent kernel does not record p). */
@@ -247,7 +250,13 @@ int mg_forward_jacobian_apply(mg_mesh* mesh, int level, const double* eps,
  * adjoint (reverse-time leapfrog) with checkpoints every ckpt_every steps
  * and recomputation in between.
  *  w  data, [rec_ptr[n_shots]][nt] float32 trace weights
- *  g  data, [cells of level] float64 output */
+ *  g  data, [cells of level] float64 output
+ *  flags  MG_HOST_PTRS, MG_NO_GRAPH, MG_ALLOW_CFL, MG_REUSE_CHECKPOINTS;
+ *         MG_PERSISTENT when the reused checkpoints are a kept history
+ *         (ckpt_every = nt after MG_KEEP_STATES): the reverse steps run
+ *         several per cooperative launch, as mg_forward's (ends with a
+ *         stream synchronisation; MG_ERR_TIMEOUT if a barrier wait ran
+ *         out), else MG_ERR_UNSUPPORTED. */
 int mg_jacobian_T_apply(mg_mesh* mesh, int level, const double* eps,
                         const mg_shots* shots, const double* wavelet, double dt,
                         int nt, const float* w, double* g, int ckpt_every,

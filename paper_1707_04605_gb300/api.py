@@ -374,10 +374,12 @@ def jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
 
 
 def forward_jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=None, *,
-                           keep_states=False, allow_cfl=False, stream=None, flags=0):
+                           keep_states=False, allow_cfl=False, persistent=False, stream=None,
+                           flags=0):
     """(traces, J v) of one fused pass (mg_forward_jacobian_apply); with
     keep_states the forward history stays in the handle for
-    jacobian_T_apply(..., ckpt_every=nt, reuse_checkpoints=True)."""
+    jacobian_T_apply(..., ckpt_every=nt, reuse_checkpoints=True).
+    persistent (with keep_states) runs several steps per cooperative launch."""
     lib = L.load()
     sh = Shots.of(shots)
     nt = int(len(wavelet) if nt is None else nt)
@@ -388,6 +390,8 @@ def forward_jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=Non
     f = f0 | flags | (L.MG_ALLOW_CFL if allow_cfl else 0)
     if keep_states:
         f |= L.MG_KEEP_STATES
+    if persistent:
+        f |= L.MG_PERSISTENT
     rc = lib.mg_forward_jacobian_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw,
                                        float(dt), nt, pv, _ptr(y), _ptr(jv), st, f)
     L.check(rc, "mg_forward_jacobian_apply")
@@ -396,7 +400,7 @@ def forward_jacobian_apply(mesh: Mesh, level, eps, shots, wavelet, dt, v, nt=Non
 
 def jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, w, nt=None, *,
                      ckpt_every=256, reuse_checkpoints=False, allow_cfl=False,
-                     stream=None, flags=0):
+                     persistent=False, stream=None, flags=0):
     """J^T w: gradient [cells of level] float64 for trace weights w [n_traces, nt]."""
     lib = L.load()
     sh = Shots.of(shots)
@@ -405,6 +409,8 @@ def jacobian_T_apply(mesh: Mesh, level, eps, shots, wavelet, dt, w, nt=None, *,
     (w, pwt), = ex
     out = _alloc(dev, (mesh.n_cells_per_level[level],), "float64", eps)
     f = f0 | flags | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    if persistent:
+        f |= L.MG_PERSISTENT
     if reuse_checkpoints:
         f |= L.MG_REUSE_CHECKPOINTS
     rc = lib.mg_jacobian_T_apply(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),

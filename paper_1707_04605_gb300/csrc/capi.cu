@@ -552,6 +552,32 @@ std::string key_of(const char* kind, std::initializer_list<const void*> ptrs,
 
 bool graphs_on(mg_mesh* M, int flags) { return M->chunk >= 2 && !(flags & MG_NO_GRAPH); }
 
+// Barrier arguments of the handle's persistent launches (status word and
+// counter, cleared on the stream first).
+int persist_args(mg_mesh* M, cudaStream_t st, float* seg, size_t state, mg::PersistArgs& pa) {
+  int* status = err_word(M);
+  if (!status) return MG_ERR_OOM;
+  MG_CU(cudaMemsetAsync(status, 0, sizeof(int), st));
+  pa.count = reinterpret_cast<unsigned*>(status + 1);
+  pa.status = status;
+  pa.budget = M->persist_budget;
+  pa.extra = M->persist_extra;
+  pa.seg = seg;
+  pa.state = (int64_t)state;
+  return MG_OK;
+}
+
+// After persistent launches: wait for them, then MG_ERR_TIMEOUT (status
+// word cleared) if a barrier wait ran out.
+int persist_status(mg_mesh* M, cudaStream_t st) {
+  int word = 0;
+  MG_CU(cudaMemcpyAsync(&word, M->errbuf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MG_CU(cudaStreamSynchronize(st));
+  if (word == 0) return MG_OK;
+  MG_CU(cudaMemset(M->errbuf.p, 0, sizeof(int)));
+  return MG_ERR_TIMEOUT;
+}
+
 // Batched forward loop over steps [0, nt); optional traces and checkpoints.
 // Whole chunks of M->chunk steps run as one graph launch each.
 int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_every,
@@ -570,14 +596,8 @@ int run_forward(mg_mesh* M, const Prep& pp, int nt, float* traces, int ckpt_ever
   if (flags & MG_PERSISTENT) {
     // several steps per cooperative launch, ending at every checkpoint; the
     // status word is cleared first (a stale time-out would stop the barrier)
-    int* status = err_word(M);
-    if (!status) return MG_ERR_OOM;
-    MG_CU(cudaMemsetAsync(status, 0, sizeof(int), st));
     mg::PersistArgs pa{};
-    pa.count = reinterpret_cast<unsigned*>(status + 1);
-    pa.status = status;
-    pa.budget = M->persist_budget;
-    pa.extra = M->persist_extra;
+    MG_TRY(persist_args(M, st, nullptr, 0, pa));
     while (l < nt) {
       if (ckpt && l % ckpt_every == 0) {
         float* slot = ckpt + (size_t)(l / ckpt_every) * 2 * state;
@@ -1186,16 +1206,8 @@ int mg_forward(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
       ck = P<float>(M->ckpt);
     }
     MG_TRY(run_forward(M, pp, nt, tr, ckpt_every, ck, st, flags));
-    if (flags & MG_PERSISTENT) {
-      // the barrier waits are bounded: read (and clear) the status word
-      int word = 0;
-      MG_CU(cudaMemcpyAsync(&word, M->errbuf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-      MG_CU(cudaStreamSynchronize(st));
-      if (word != 0) {
-        MG_CU(cudaMemset(M->errbuf.p, 0, sizeof(int)));
-        return MG_ERR_TIMEOUT;
-      }
-    }
+    // the barrier waits are bounded: read (and clear) the status word
+    if (flags & MG_PERSISTENT) MG_TRY(persist_status(M, st));
     if (ck) {
       M->ck_valid = true;  M->ck_gen++;
       M->ck_every = ckpt_every;
@@ -1355,7 +1367,8 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
                               float* traces, float* jv, void* stream, int flags) {
   if (!M || !v || !jv || !traces) return MG_ERR_ARG;
   if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
-  if (flags & ~(kCommonFlags | MG_KEEP_STATES)) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(kCommonFlags | MG_KEEP_STATES | MG_PERSISTENT)) return MG_ERR_UNSUPPORTED;
+  if ((flags & MG_PERSISTENT) && !(flags & MG_KEEP_STATES)) return MG_ERR_UNSUPPORTED;
   DeviceGuard g(M->device);
   if (!g.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1446,7 +1459,30 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
     }
     return MG_OK;
   };
-  if (graph) {
+  if (flags & MG_PERSISTENT) {
+    // each shot group: cooperative launches of up to persist_steps steps
+    // with grid barriers between the steps, writing the kept history
+    mg::PersistArgs pa{};
+    MG_TRY(persist_args(M, st, seg, state, pa));
+    for (int g = 0; g < NG; ++g) {
+      mg::TangentArgs b = a;
+      b.f.step_base = nullptr;
+      b.f.col0 = g * W;
+      b.f.cols = W;
+      float *u = q, *z = qm;
+      for (int l = 0; l < nt;) {
+        pa.steps = std::min(nt - l, M->persist_steps);
+        b.f.step = l;
+        b.q = u;
+        b.qm = z;
+        MG_TRY(mg::launch_tangent_persist(b, pp.S_pad, pa, st));
+        M->launches += 1;
+        if (pa.steps % 2) std::swap(u, z);
+        l += pa.steps;
+      }
+    }
+    MG_TRY(persist_status(M, st));
+  } else if (graph) {
     const std::string key = key_of("fwdtan", {seg, p, pm, q, qm, tr, trf, a.f.wavelet, a.f.coef,
                                               a.tcoef, a.f.ev.src_ptr, base},
                                    {pp.S_pad, pp.S, pp.R, nt, n, W, keep ? 1 : 0});
@@ -1474,7 +1510,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
                         int ckpt_every, void* stream, int flags) {
   if (!M || !w || !g || ckpt_every < 1) return MG_ERR_ARG;
   if (level < 0 || level >= M->hm.n_levels) return MG_ERR_ARG;
-  if (flags & ~(kCommonFlags | MG_REUSE_CHECKPOINTS)) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(kCommonFlags | MG_REUSE_CHECKPOINTS | MG_PERSISTENT)) return MG_ERR_UNSUPPORTED;
   DeviceGuard guard(M->device);
   if (!guard.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1497,6 +1533,8 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   if ((flags & MG_REUSE_CHECKPOINTS) && !reuse) return MG_ERR_ARG;
   // every state of the forward kept (MG_KEEP_STATES): one segment, no recompute
   const bool states = reuse && M->seg_full && ckpt_every == nt;
+  // several reverse steps per cooperative launch: on the kept history only
+  if ((flags & MG_PERSISTENT) && !states) return MG_ERR_UNSUPPORTED;
   if (!states) M->seg_full = false;   // the segment buffer is rewritten below
   const int nck = (nt + ckpt_every - 1) / ckpt_every;
   if (!reuse) {
@@ -1560,6 +1598,30 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
       MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state, seg + state, (int64_t)state, st));
       MG_TRY(mg::launch_copy_f4(ck + (size_t)a * 2 * state + state, seg, (int64_t)state, st));
       M->launches += 2;
+    }
+    if (flags & MG_PERSISTENT) {   // kept history: one segment, l0 = 0, l1 = nt
+      mg::PersistArgs pa{};
+      MG_TRY(persist_args(M, st, seg, state, pa));
+      for (int g = 0; g < NGa; ++g) {
+        mg::AdjointArgs b = aa;
+        b.col0 = g * Wa;
+        b.cols = Wa;
+        float* x = mu;
+        float* y = mu1;
+        for (int k = l1; k > l0;) {
+          pa.steps = std::min(k - l0, M->persist_steps);
+          b.mu = x;
+          b.mu1 = y;
+          b.k = k;
+          MG_TRY(mg::launch_adjoint_persist(b, pp.S_pad, pa, st));
+          M->launches += 1;
+          if (pa.steps % 2) std::swap(x, y);
+          k -= pa.steps;
+        }
+      }
+      if ((l1 - l0) % 2) std::swap(mu, mu1);
+      MG_TRY(persist_status(M, st));
+      continue;
     }
     if (use_graph && l1 - l0 == ckpt_every) {
       // whole segment: recompute p_{l0+1..l1}, then reverse steps k = l1..l0+1,

@@ -154,10 +154,22 @@ struct PersistArgs {
   int* status;              // the handle's status word
   long long budget;         // SM clock cycles one barrier wait may take
   int32_t extra;            // arrivals awaited beyond the grid's CTAs
+  float* seg = nullptr;     // kept history (tangent, adjoint): slot j holds p_{j-1}
+  int64_t state = 0;        // floats per kept state
 };
 // a.pout must equal a.pm (in-place update).  MG_ERR_UNSUPPORTED when the
 // device cannot hold the launch's source tiles as co-resident CTAs.
 int launch_step_persist(const StepArgs& a, int S_pad, const PersistArgs& pa, cudaStream_t st);
+// The fused forward + tangent step writing the kept history, pa.steps steps
+// from a.f.step = l: p_l, p_{l-1}, p_{l+1} are slots l + 1, l, l + 2 of
+// pa.seg; a.q / a.qm (dp_l, dp_{l-1}) swap roles after every step.
+int launch_tangent_persist(const TangentArgs& a, int S_pad, const PersistArgs& pa,
+                           cudaStream_t st);
+// Reverse steps on the kept history, k = a.k, a.k - 1, ... (pa.steps of
+// them): p_k is slot k + 1 of pa.seg; a.mu / a.mu1 swap roles after every
+// step.
+int launch_adjoint_persist(const AdjointArgs& a, int S_pad, const PersistArgs& pa,
+                           cudaStream_t st);
 
 // The same with the neighbour gathers pipelined through a shared-memory
 // ring (kernels_ring.cu; called by the launchers above when ring > 0).

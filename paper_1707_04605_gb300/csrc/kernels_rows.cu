@@ -65,9 +65,142 @@ __global__ void __launch_bounds__(kThreads) k_step_persist(StepArgs a, PersistAr
   }
 }
 
+template <int LPR, int NV>
+__global__ void __launch_bounds__(kThreads) k_tangent_persist(TangentArgs a, PersistArgs pa) {
+  constexpr int RPB = kWarps * 32 / LPR;
+  const int nblk = (a.f.K.n + RPB - 1) / RPB;
+  const unsigned nctas = gridDim.x * gridDim.y;
+  const float* x = a.q;
+  float* y = a.qm;
+  TangentArgs b = a;
+  for (int j = 0; j < pa.steps; ++j) {
+    const int l = a.f.step + j;
+    b.f.p = pa.seg + (size_t)(l + 1) * pa.state;
+    b.f.pm = pa.seg + (size_t)l * pa.state;
+    b.f.pout = pa.seg + (size_t)(l + 2) * pa.state;
+    b.f.step = l;
+    b.q = x;
+    b.qm = y;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) tangent_rows_block<LPR, NV, 0>(b, blk);
+    if (j + 1 < pa.steps &&
+        !grid_barrier(pa.count, (unsigned)(j + 1) * (nctas + (unsigned)pa.extra), pa.status,
+                      pa.budget))
+      return;
+    float* t = const_cast<float*>(x);
+    x = y;
+    y = t;
+  }
+}
+
+template <int LPR, int NV>
+__global__ void __launch_bounds__(kThreads) k_adjoint_persist(AdjointArgs a, PersistArgs pa) {
+  constexpr int RPB = kWarps * 32 / LPR;
+  const int nblk = (a.K.n + RPB - 1) / RPB;
+  const unsigned nctas = gridDim.x * gridDim.y;
+  const float* x = a.mu;
+  float* y = a.mu1;
+  AdjointArgs b = a;
+  for (int j = 0; j < pa.steps; ++j) {
+    const int k = a.k - j;
+    b.mu = x;
+    b.mu1 = y;
+    b.pk = pa.seg + (size_t)(k + 1) * pa.state;
+    b.k = k;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) adjoint_rows_block<LPR, NV, 0>(b, blk);
+    if (j + 1 < pa.steps &&
+        !grid_barrier(pa.count, (unsigned)(j + 1) * (nctas + (unsigned)pa.extra), pa.status,
+                      pa.budget))
+      return;
+    float* t = const_cast<float*>(x);
+    x = y;
+    y = t;
+  }
+}
+
+// Cooperative launch of a persistent kernel: at most the kernel's occupancy
+// times the SM count CTAs (every CTA resident), the barrier counter zeroed
+// on the stream first.
+template <class A>
+int launch_coop(void (*kern)(A, PersistArgs), Shape sh, const A& a, const PersistArgs& pa,
+                cudaStream_t st) {
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  const long resident = (long)occ * nsm;
+  if (resident < (long)sh.grid.y) return MG_ERR_UNSUPPORTED;
+  sh.grid.x = (unsigned)std::min<long>(sh.grid.x, resident / sh.grid.y);
+  if (cudaMemsetAsync(pa.count, 0, sizeof(unsigned), st) != cudaSuccess) return MG_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = sh.grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kern, a, pa) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  return check_launch();
+}
+
+bool persist_ok(const PersistArgs& pa) {
+  return pa.steps >= 1 && pa.count && pa.status && pa.budget >= 1 && pa.extra >= 0;
+}
+
 }  // namespace
 
 int rows_tiles(int cols, int nv) { return (int)shape_of(1, cols, nv).grid.y; }
+
+#define MG_PERSIST_SWITCH(KERN, ARGS)                                                    \
+  switch (sh.lpr * 8 + sh.nv) {                                                        \
+    case 32 * 8 + 1: return launch_coop(KERN<32, 1>, sh, ARGS, pa, st);                \
+    case 32 * 8 + 2: return launch_coop(KERN<32, 2>, sh, ARGS, pa, st);                \
+    case 32 * 8 + 4: return launch_coop(KERN<32, 4>, sh, ARGS, pa, st);                \
+    case 16 * 8 + 1: return launch_coop(KERN<16, 1>, sh, ARGS, pa, st);                \
+    case 16 * 8 + 2: return launch_coop(KERN<16, 2>, sh, ARGS, pa, st);                \
+    case 16 * 8 + 4: return launch_coop(KERN<16, 4>, sh, ARGS, pa, st);                \
+    case 8 * 8 + 1: return launch_coop(KERN<8, 1>, sh, ARGS, pa, st);                  \
+    case 8 * 8 + 2: return launch_coop(KERN<8, 2>, sh, ARGS, pa, st);                  \
+    case 8 * 8 + 4: return launch_coop(KERN<8, 4>, sh, ARGS, pa, st);                  \
+    case 4 * 8 + 1: return launch_coop(KERN<4, 1>, sh, ARGS, pa, st);                  \
+    case 4 * 8 + 2: return launch_coop(KERN<4, 2>, sh, ARGS, pa, st);                  \
+    case 4 * 8 + 4: return launch_coop(KERN<4, 4>, sh, ARGS, pa, st);                  \
+    case 2 * 8 + 1: return launch_coop(KERN<2, 1>, sh, ARGS, pa, st);                  \
+    case 2 * 8 + 2: return launch_coop(KERN<2, 2>, sh, ARGS, pa, st);                  \
+    case 2 * 8 + 4: return launch_coop(KERN<2, 4>, sh, ARGS, pa, st);                  \
+    case 1 * 8 + 1: return launch_coop(KERN<1, 1>, sh, ARGS, pa, st);                  \
+    case 1 * 8 + 2: return launch_coop(KERN<1, 2>, sh, ARGS, pa, st);                  \
+    case 1 * 8 + 4: return launch_coop(KERN<1, 4>, sh, ARGS, pa, st);                  \
+    default: return MG_ERR_ARG;                                                        \
+  }
+
+int launch_tangent_persist(const TangentArgs& a, int S_pad, const PersistArgs& pa,
+                           cudaStream_t st) {
+  const int cols = a.f.cols ? a.f.cols : S_pad;
+  const Shape sh = shape_of(a.f.K.n, cols, a.f.batch);
+  if (!range_ok(sh, a.f.col0, cols, a.f.ld) || !persist_ok(pa) || !pa.seg || pa.state < 1 ||
+      a.f.step < 0)
+    return MG_ERR_ARG;
+  MG_PERSIST_SWITCH(k_tangent_persist, a)
+}
+
+int launch_adjoint_persist(const AdjointArgs& a, int S_pad, const PersistArgs& pa,
+                           cudaStream_t st) {
+  const int cols = a.cols ? a.cols : S_pad;
+  const Shape sh = shape_of(a.K.n, cols, a.batch);
+  if (!range_ok(sh, a.col0, cols, a.ld) || !persist_ok(pa) || !pa.seg || pa.state < 1 ||
+      a.k - pa.steps < 0)
+    return MG_ERR_ARG;
+  MG_PERSIST_SWITCH(k_adjoint_persist, a)
+}
+#undef MG_PERSIST_SWITCH
 
 int launch_step_persist(const StepArgs& a, int S_pad, const PersistArgs& pa, cudaStream_t st) {
   const int cols = a.cols ? a.cols : S_pad;

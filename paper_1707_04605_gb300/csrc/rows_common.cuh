@@ -446,11 +446,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   for (int b = b0; b < b1; ++b) step_rows_block<LPR, NV, R>(a, b);
 }
 
+// The forward + tangent step of row block `blk`.
 template <int LPR, int NV, int R>
-__global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
+__device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
+  const int row = (blk * kWarps + warp) * RPW + lane / LPR;
   const unsigned mask = __ballot_sync(0xffffffffu, row < a.f.K.n);
   if (row >= a.f.K.n) return;
   const int lr = lane % LPR;
@@ -500,6 +501,11 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
       if (a.f.traces) a.f.traces[at] = get_from<NV>(pn, j, d);   // forward traces too
     }
   }
+}
+
+template <int LPR, int NV, int R>
+__global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
+  tangent_rows_block<LPR, NV, R>(a, blockIdx.x);
 }
 
 // Tangent step when the forward states are kept: p_{l-1}, p_l, p_{l+1} of
@@ -562,11 +568,12 @@ __device__ __forceinline__ void kahan_step(float& s, float& c, float term) {
   s = t;
 }
 
+// The reverse step of row block `blk`.
 template <int LPR, int NV, int R>
-__global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
+__device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = (blockIdx.x * kWarps + warp) * RPW + lane / LPR;
+  const int row = (blk * kWarps + warp) * RPW + lane / LPR;
   const bool valid = row < a.K.n;
   const unsigned mask = __ballot_sync(0xffffffffu, valid);
   const int lr = lane % LPR;
@@ -632,6 +639,11 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
     a.H[gi] = h;
     a.Hc[gi] = hc;
   }
+}
+
+template <int LPR, int NV, int R>
+__global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
+  adjoint_rows_block<LPR, NV, R>(a, blockIdx.x);
 }
 
 // Launch shape for `cols` shot columns (a multiple of 4: a power of two up

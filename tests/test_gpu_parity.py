@@ -778,3 +778,39 @@ def test_l1_streaming_gives_identical_results(mg, S, batch):
     assert all(mesh.tuning()[k]["stream"] == 1 for k in ("forward", "tangent", "adjoint"))
     for a, b in zip(ref, run()):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("nt,groups,steps", [(300, 1, 64), (301, 2, 7), (300, 2, 128)])
+def test_persistent_fused_pass_and_reverse_steps_give_the_graph_bits(mg, nt, groups, steps):
+    """The fused forward + tangent pass writing the kept history and the
+    reverse steps on it, several steps per cooperative launch: the same
+    traces, J v and J^T w bits as their graph replays."""
+    w = configs.asteroid_2d(n_refine=1, S=100, nt=nt)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_shot_groups(groups)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    eps = _dev(w.eps)
+    rng = np.random.default_rng(15)
+    v = _dev(rng.standard_normal(w.mesh.n_cells[1]))
+    W = _dev(rng.standard_normal((w.shots.n_traces, nt)), torch.float32)
+
+    def run(persistent):
+        y, jv = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True,
+                                          persistent=persistent)
+        g = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=nt,
+                                reuse_checkpoints=True, persistent=persistent)
+        return y, jv, g
+
+    ref = run(False)
+    mesh.set_persistent(steps)
+    for a, b in zip(ref, run(True)):
+        assert torch.equal(a, b)
+    # a persistent J^T w needs the kept history
+    from paper_1707_04605_gb300 import _lib as L
+
+    mg.forward(mesh, eps, w.shots, s, dt, ckpt_every=64, keep_checkpoints=True)
+    with pytest.raises(L.MgError) as e:
+        mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64,
+                            reuse_checkpoints=True, persistent=True)
+    assert e.value.code == L.MG_ERR_UNSUPPORTED
