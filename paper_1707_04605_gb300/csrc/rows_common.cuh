@@ -386,8 +386,22 @@ __device__ __forceinline__ float get_from(const float4 (&v)[NV], int j, int d) {
 // MINB > 1 asks the compiler for at least MINB resident CTAs per SM (a
 // register cap): more warps in flight for the HBM-bound case, at the price
 // of a few spilled registers in the rare source/receiver epilogue.
+// A load the compiler keeps where it is written (after the row's gathers
+// in the late-load form below).
+__device__ __forceinline__ float4 ld_pinned(const float* p) {
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
 // The forward step of row block `blk` (kWarps * 32 / LPR consecutive rows).
-template <int LPR, int NV, int R>
+// LATE: the row's p_{l-1} and coefficients are loaded after its gathers, so
+// that they hold no registers across the gather loop (the register-capped
+// kernel then needs no spill slots in it).
+template <int LPR, int NV, int R, bool LATE = false>
 __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -400,12 +414,22 @@ __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
   Row r = row_of(a.K, row);
   r.na = a.stream;
   grid_dep_sync();
-  const float4 c = ld_coef(a.coef + row, a.stream);
   const size_t ro = (size_t)row * a.ld + base;
-  float4 old[NV], self[NV], acc[NV];
+  float4 c, old[NV], self[NV], acc[NV];
+  if constexpr (!LATE) {
+    c = ld_coef(a.coef + row, a.stream);
 #pragma unroll
-  for (int j = 0; j < NV; ++j) old[j] = ld_once<false>(a.pm + ro + 4 * LPR * j, a.hint, a.stream);
+    for (int j = 0; j < NV; ++j)
+      old[j] = ld_once<false>(a.pm + ro + 4 * LPR * j, a.hint, a.stream);
+  }
   gather1<LPR, NV, R>(r, a.p + base, row, lr, mask, a.ld, self, acc);
+  if constexpr (LATE) {
+    c = ld_pinned(reinterpret_cast<const float*>(a.coef + row));
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      old[j] = a.hint || a.stream ? ld_once<false>(a.pm + ro + 4 * LPR * j, a.hint, a.stream)
+                                  : ld_pinned(a.pm + ro + 4 * LPR * j);
+  }
   float4 out[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) out[j] = leap(c, self[j], old[j], acc[j]);
@@ -436,14 +460,15 @@ __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
 // are then still in the SM's L1.
 template <int LPR, int NV, int MINB, int R>
 __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
+  constexpr bool kLate = MINB > 1;   // the register-capped form loads late
   if (a.sweep <= 1) {
-    step_rows_block<LPR, NV, R>(a, blockIdx.x);
+    step_rows_block<LPR, NV, R, kLate>(a, blockIdx.x);
     return;
   }
   constexpr int RPB = kWarps * 32 / LPR;
   const int nblk = (a.K.n + RPB - 1) / RPB;
   const int b0 = blockIdx.x * a.sweep, b1 = min(b0 + a.sweep, nblk);
-  for (int b = b0; b < b1; ++b) step_rows_block<LPR, NV, R>(a, b);
+  for (int b = b0; b < b1; ++b) step_rows_block<LPR, NV, R, kLate>(a, b);
 }
 
 // The forward + tangent step of row block `blk`.
