@@ -102,6 +102,8 @@ def apply_tuning(mesh, spec):
         mesh.set_gather_ring(t.get("ring", 0), kind)
         if "stream" in t:
             mesh.set_l1_streaming(t["stream"], kind)
+        if kind == "tangent":
+            mesh.set_min_blocks(t.get("min_blocks", 0), "tangent")
         if kind == "forward":
             mesh.set_min_blocks(t.get("min_blocks", 0))
             mesh.set_row_sweep(t.get("sweep", 0))
@@ -571,19 +573,25 @@ def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
     chosen = {}
     for kind, fn in calls.items():
         best = None
-        for g in (1, 2, 4):
-            mesh.set_shot_groups(g, kind)
-            fn()                                   # records the graph
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            t = a.elapsed_time(b)
-            if best is None or t < best[1] * 0.99:
-                best = (g, t)
+        caps = (0, 5) if kind == "tangent" else (None,)   # the fused kernel's register cap
+        for cap in caps:
+            if cap is not None:
+                mesh.set_min_blocks(cap, "tangent")
+            for g in (1, 2, 4):
+                mesh.set_shot_groups(g, kind)
+                fn()                                   # records the graph
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                t = a.elapsed_time(b)
+                if best is None or t < best[1] * 0.99:
+                    best = (g, t, cap)
         mesh.set_shot_groups(best[0], kind)
+        if best[2] is not None:
+            mesh.set_min_blocks(best[2], "tangent")
         chosen[kind] = best[0]
         if kind == "tangent":
             calls["tangent"]()                     # kept history for the reverse steps

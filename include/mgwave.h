@@ -315,6 +315,14 @@ int mg_mesh_set_shot_groups(mg_mesh* mesh, int kind, int groups);
  * Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_min_blocks(mg_mesh* mesh, int min_blocks);
 
+/* The same register cap for a kernel kind: MG_KERNEL_FORWARD (as
+ * mg_mesh_set_min_blocks) or MG_KERNEL_TANGENT (the lockstep and fused
+ * forward + tangent row kernel).  The capped kernels load the row's own
+ * states and coefficients after its gathers, so that nothing is held across
+ * the gather loop and the cap needs no spill slots there.  Same results.
+ * Drops the cached graphs.  Errors: MG_ERR_ARG for other kinds or values. */
+int mg_mesh_set_kernel_min_blocks(mg_mesh* mesh, int kind, int min_blocks);
+
 /* Gather ring of the row kernels of a kernel kind (kind = -1: all kinds):
  * depth 4 or 8 makes every lane copy the float4s it needs of the neighbour
  * rows depth - 1 stiffness entries ahead into its own slots of a

@@ -88,6 +88,7 @@ SIGNATURES = {
     "mg_mesh_set_shot_groups": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_set_conductivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mg_mesh_set_min_blocks": (C.c_int, [C.c_void_p, C.c_int]),
+    "mg_mesh_set_kernel_min_blocks": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_set_gather_ring": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_get_gather_ring": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mg_mesh_set_row_sweep": (C.c_int, [C.c_void_p, C.c_int]),

@@ -182,8 +182,14 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_persistent(self.handle, int(steps), int(wait_cycles),
                                                  int(extra_arrivals)), "mg_mesh_set_persistent")
 
-    def set_min_blocks(self, min_blocks: int):
-        """Register cap of the forward row kernel (mg_mesh_set_min_blocks): 0 or 5."""
+    def set_min_blocks(self, min_blocks: int, kind: str = "forward"):
+        """Register cap of the forward or tangent row kernel
+        (mg_mesh_set_min_blocks / mg_mesh_set_kernel_min_blocks): 0 or 5."""
+        if kind != "forward":
+            L.check(self._lib.mg_mesh_set_kernel_min_blocks(self.handle, self.KINDS[kind],
+                                                            int(min_blocks)),
+                    "mg_mesh_set_kernel_min_blocks")
+            return
         L.check(self._lib.mg_mesh_set_min_blocks(self.handle, int(min_blocks)),
                 "mg_mesh_set_min_blocks")
 

@@ -474,6 +474,7 @@ int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st)
   b.f.batch = M->tune[1].batch;
   b.f.ring = M->tune[1].ring;
   b.f.stream = M->tune[1].stream;
+  b.f.min_blocks = M->tune[1].min_blocks;
   b.f.pdl = M->dep_launch;
   return mg::launch_tangent(b, S_pad, st);
 }
@@ -1100,6 +1101,13 @@ int mg_mesh_set_min_blocks(mg_mesh* M, int min_blocks) {
   return MG_OK;
 }
 
+int mg_mesh_set_kernel_min_blocks(mg_mesh* M, int kind, int min_blocks) {
+  if (!M || kind < 0 || kind > 1 || (min_blocks != 0 && min_blocks != 5)) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->tune[kind].min_blocks = min_blocks;
+  return MG_OK;
+}
+
 int mg_mesh_get_tuning(const mg_mesh* M, int32_t* out) {
   if (!M || !out) return MG_ERR_ARG;
   out[0] = M->chunk;
@@ -1419,6 +1427,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
   a.f.batch = M->tune[1].batch;
   a.f.ring = M->tune[1].ring;
   a.f.stream = M->tune[1].stream;
+  a.f.min_blocks = M->tune[1].min_blocks;
   a.f.pdl = M->dep_launch;
   a.f.hint = keep ? M->cache_hints : 0;   // p_{l-1} is last read here only when kept
   a.tcoef = P<const float2>(M->tcoef);
@@ -1775,7 +1784,7 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
       {1, 256, 16},        {2, 0, 32, 1, 5},    {4, 0, 32, 1, 5},    {1, 0, 32, 1, 0, 0, 4},
       {2, 0, 32, 1, 0, 0, 4}, {4, 0, 32, 1, 0, 0, 4}, {1, 0, 32, 1, 0, 0, 8},
       {2, 0, 32, 1, 0, 0, 8}, {4, 0, 32, 1, 0, 0, 8}, {1, 0, 32, 1, 0, 0, 0, 4},
-      {2, 0, 32, 1, 5, 0, 0, 4}, {4, 0, 32, 1, 5, 0, 0, 4}};
+      {2, 0, 32, 1, 5, 0, 0, 4}, {4, 0, 32, 1, 5, 0, 0, 4}, {1, 0, 32, 1, 5}};
   const int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
   cudaEvent_t e0, e1;
   MG_CU(cudaEventCreate(&e0));
@@ -1812,8 +1821,10 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
     float ms[n_shapes];
     for (int i = 0; i < n_shapes && rc == MG_OK; ++i) {
       ms[i] = 1e30f;
-      if ((shapes[i].min_blocks || shapes[i].bulk || shapes[i].sweep || shapes[i].tma) &&
-          kind != 0)
+      // register caps apply to the forward and the tangent, the other
+      // variants to the forward only
+      if (((shapes[i].bulk || shapes[i].sweep || shapes[i].tma) && kind != 0) ||
+          (shapes[i].min_blocks && kind == 2))
         continue;
       rc = time_of(kind, shapes[i], &ms[i]);
     }

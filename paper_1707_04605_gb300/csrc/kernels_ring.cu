@@ -38,10 +38,11 @@ int launch_tangent_ring(const TangentArgs& a, int S_pad, cudaStream_t st) {
   if (!range_ok(sh, a.f.col0, cols, a.f.ld)) return MG_ERR_ARG;
   if (int rc = ring_check(a.f.ring, 2, sh.nv)) return rc;
   cudaError_t err = cudaSuccess;
+  if (a.f.min_blocks != 0) return MG_ERR_ARG;
   if (a.f.ring == 4) {
-    MG_ROWS_SWITCH(k_tangent_rows, 4, 2, a.f.pdl, a)
+    MG_ROWS_SWITCH_M(k_tangent_rows, 1, 4, 2, a.f.pdl, a)
   } else {
-    MG_ROWS_SWITCH(k_tangent_rows, 8, 2, a.f.pdl, a)
+    MG_ROWS_SWITCH_M(k_tangent_rows, 1, 8, 2, a.f.pdl, a)
   }
   if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();

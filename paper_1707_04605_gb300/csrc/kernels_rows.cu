@@ -268,7 +268,13 @@ int launch_tangent(const TangentArgs& a, int S_pad, cudaStream_t st) {
   const Shape sh = shape_of(a.f.K.n, cols, a.f.batch);
   if (!range_ok(sh, a.f.col0, cols, a.f.ld)) return MG_ERR_ARG;
   cudaError_t err = cudaSuccess;
-  MG_ROWS_SWITCH(k_tangent_rows, 0, 2, a.f.pdl, a)
+  if (a.f.min_blocks == 5) {
+    MG_ROWS_SWITCH_M(k_tangent_rows, 5, 0, 2, a.f.pdl, a)
+  } else if (a.f.min_blocks == 0) {
+    MG_ROWS_SWITCH_M(k_tangent_rows, 1, 0, 2, a.f.pdl, a)
+  } else {
+    return MG_ERR_ARG;
+  }
   if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();
 }

@@ -397,6 +397,12 @@ __device__ __forceinline__ float4 ld_pinned(const float* p) {
   return v;
 }
 
+__device__ __forceinline__ float2 ld_pinned2(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+  return v;
+}
+
 // The forward step of row block `blk` (kWarps * 32 / LPR consecutive rows).
 // LATE: the row's p_{l-1} and coefficients are loaded after its gathers, so
 // that they hold no registers across the gather loop (the register-capped
@@ -471,8 +477,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   for (int b = b0; b < b1; ++b) step_rows_block<LPR, NV, R, kLate>(a, b);
 }
 
-// The forward + tangent step of row block `blk`.
-template <int LPR, int NV, int R>
+// The forward + tangent step of row block `blk`.  LATE as in
+// step_rows_block: the row's own states and coefficients are loaded after
+// its gathers.
+template <int LPR, int NV, int R, bool LATE = false>
 __device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -486,16 +494,31 @@ __device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk
   Row r = row_of(a.f.K, row);
   r.na = a.f.stream;
   grid_dep_sync();
-  const float4 c = ld_coef(a.f.coef + row, a.f.stream);
-  const float2 tc = ld_coef(a.tcoef + row, a.f.stream);
   const size_t ro = (size_t)row * ld + base;
-  float4 pold[NV], qold[NV], ps[NV], qs[NV], pacc[NV], qacc[NV];
+  float4 c, pold[NV], qold[NV], ps[NV], qs[NV], pacc[NV], qacc[NV];
+  float2 tc;
+  if constexpr (!LATE) {
+    c = ld_coef(a.f.coef + row, a.f.stream);
+    tc = ld_coef(a.tcoef + row, a.f.stream);
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    pold[j] = ld_once<false>(a.f.pm + ro + 4 * LPR * j, a.f.hint, a.f.stream);
-    qold[j] = ld_once<false>(a.qm + ro + 4 * LPR * j, 0, a.f.stream);
+    for (int j = 0; j < NV; ++j) {
+      pold[j] = ld_once<false>(a.f.pm + ro + 4 * LPR * j, a.f.hint, a.f.stream);
+      qold[j] = ld_once<false>(a.qm + ro + 4 * LPR * j, 0, a.f.stream);
+    }
   }
   gather2<LPR, NV, R>(r, a.f.p + base, a.q + base, row, lr, mask, ld, ps, qs, pacc, qacc);
+  if constexpr (LATE) {
+    c = ld_pinned(reinterpret_cast<const float*>(a.f.coef + row));
+    tc = ld_pinned2(a.tcoef + row);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      pold[j] = a.f.hint || a.f.stream ? ld_once<false>(a.f.pm + ro + 4 * LPR * j, a.f.hint,
+                                                        a.f.stream)
+                                       : ld_pinned(a.f.pm + ro + 4 * LPR * j);
+      qold[j] = a.f.stream ? ld_once<false>(a.qm + ro + 4 * LPR * j, 0, a.f.stream)
+                           : ld_pinned(a.qm + ro + 4 * LPR * j);
+    }
+  }
   float4 pn[NV], qn[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) pn[j] = leap(c, ps[j], pold[j], pacc[j]);
@@ -528,9 +551,10 @@ __device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk
   }
 }
 
-template <int LPR, int NV, int R>
-__global__ void __launch_bounds__(kThreads) k_tangent_rows(TangentArgs a) {
-  tangent_rows_block<LPR, NV, R>(a, blockIdx.x);
+// MINB > 1: the register cap of k_step_rows, with the late loads.
+template <int LPR, int NV, int MINB, int R>
+__global__ void __launch_bounds__(kThreads, MINB) k_tangent_rows(TangentArgs a) {
+  tangent_rows_block<LPR, NV, R, (MINB > 1)>(a, blockIdx.x);
 }
 
 // Tangent step when the forward states are kept: p_{l-1}, p_l, p_{l+1} of

@@ -401,6 +401,16 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     out = run()
     assert torch.equal(ref[0], out[0])
     assert torch.equal(ref[1], out[1])
+    # the tangent's register cap: the lockstep and fused passes keep their bits
+    v = _dev(np.random.default_rng(16).standard_normal(w.mesh.n_cells[1]))
+    jv = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
+    yf, jvf = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
+    mesh.set_min_blocks(5, "tangent")
+    assert mesh.tuning()["tangent"]["min_blocks"] == 5
+    assert torch.equal(mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v), jv)
+    yc, jvc = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
+    assert torch.equal(yc, yf) and torch.equal(jvc, jvf)
+    assert torch.equal(yc, ref[0])
 
 
 @pytest.mark.parametrize("S,batch,groups,chunk", [(100, 2, 1, 128), (100, 1, 2, 128),
