@@ -102,10 +102,8 @@ def apply_tuning(mesh, spec):
         mesh.set_gather_ring(t.get("ring", 0), kind)
         if "stream" in t:
             mesh.set_l1_streaming(t["stream"], kind)
-        if kind == "tangent":
-            mesh.set_min_blocks(t.get("min_blocks", 0), "tangent")
+        mesh.set_min_blocks(t.get("min_blocks", 0), kind)
         if kind == "forward":
-            mesh.set_min_blocks(t.get("min_blocks", 0))
             mesh.set_row_sweep(t.get("sweep", 0))
             mesh.set_tma_tiles(t.get("tma", 0))
 
@@ -554,11 +552,12 @@ def batch_leg(mg, torch, dev, nt=4000, ckpt=256):
 
 
 def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
-    """Shot groups per kind for the kept-history path (the states it streams
-    are larger than L2, unlike the checkpointed path the autotuner times):
-    the fused forward + tangent pass (keeping the history) and J^T w on it
-    are timed over the first nt_probe steps with 1, 2 and 4 groups; the
-    fastest stays."""
+    """Shot groups and register caps per kind for the kept-history path (the
+    states it streams are larger than L2, unlike the checkpointed path the
+    autotuner times): the fused forward + tangent pass (keeping the history)
+    and J^T w on it are timed over the first nt_probe steps with 1, 2 and 4
+    groups under each register cap of the kind's row kernel; the fastest
+    stays."""
     stream = torch.cuda.current_stream()
     nt_probe = min(nt_probe, len(wav_d))
     wav = wav_d[:nt_probe].contiguous()
@@ -573,10 +572,8 @@ def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
     chosen = {}
     for kind, fn in calls.items():
         best = None
-        caps = (0, 5) if kind == "tangent" else (None,)   # the fused kernel's register cap
-        for cap in caps:
-            if cap is not None:
-                mesh.set_min_blocks(cap, "tangent")
+        for cap in {"tangent": (0, 5), "adjoint": (0, 5, 6)}[kind]:
+            mesh.set_min_blocks(cap, kind)
             for g in (1, 2, 4):
                 mesh.set_shot_groups(g, kind)
                 fn()                                   # records the graph
@@ -590,8 +587,7 @@ def tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, level, nt_probe=1024):
                 if best is None or t < best[1] * 0.99:
                     best = (g, t, cap)
         mesh.set_shot_groups(best[0], kind)
-        if best[2] is not None:
-            mesh.set_min_blocks(best[2], "tangent")
+        mesh.set_min_blocks(best[2], kind)
         chosen[kind] = best[0]
         if kind == "tangent":
             calls["tangent"]()                     # kept history for the reverse steps

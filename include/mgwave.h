@@ -316,11 +316,13 @@ int mg_mesh_set_shot_groups(mg_mesh* mesh, int kind, int groups);
 int mg_mesh_set_min_blocks(mg_mesh* mesh, int min_blocks);
 
 /* The same register cap for a kernel kind: MG_KERNEL_FORWARD (as
- * mg_mesh_set_min_blocks) or MG_KERNEL_TANGENT (the lockstep and fused
- * forward + tangent row kernel).  The capped kernels load the row's own
- * states and coefficients after its gathers, so that nothing is held across
- * the gather loop and the cap needs no spill slots there.  Same results.
- * Drops the cached graphs.  Errors: MG_ERR_ARG for other kinds or values. */
+ * mg_mesh_set_min_blocks), MG_KERNEL_TANGENT (the lockstep and fused
+ * forward + tangent row kernel) or MG_KERNEL_ADJOINT (the reverse row
+ * kernel; 5 or 6 resident CTAs per SM).  The capped kernels load the row's
+ * own states and coefficients after its gathers, so that nothing is held
+ * across the gather loop and the cap needs fewer spill slots there.  Same
+ * results.  Drops the cached graphs.  Errors: MG_ERR_ARG for other kinds or
+ * values (6 for a kind other than the adjoint). */
 int mg_mesh_set_kernel_min_blocks(mg_mesh* mesh, int kind, int min_blocks);
 
 /* Gather ring of the row kernels of a kernel kind (kind = -1: all kinds):
@@ -333,8 +335,10 @@ int mg_mesh_set_kernel_min_blocks(mg_mesh* mesh, int kind, int min_blocks);
  * order: same results.  A launch shape whose ring exceeds a CTA's shared
  * memory (two gathered states of 4 float4 per lane at depth 8) fails with
  * MG_ERR_UNSUPPORTED.  Applies to the row kernels only (not to tiles or
- * the bulk-copy forward).  Drops the cached graphs.  Errors: MG_ERR_ARG
- * for other values. */
+ * the bulk-copy forward); ring kernels run without the register cap of
+ * mg_mesh_set_kernel_min_blocks (the ring keeps the gathered values in
+ * shared memory, not registers).  Drops the cached graphs.  Errors:
+ * MG_ERR_ARG for other values. */
 int mg_mesh_set_gather_ring(mg_mesh* mesh, int kind, int depth);
 
 /* Row sweep of the forward row kernel: blocks > 1 makes each CTA advance

@@ -183,8 +183,9 @@ class Mesh:
                                                  int(extra_arrivals)), "mg_mesh_set_persistent")
 
     def set_min_blocks(self, min_blocks: int, kind: str = "forward"):
-        """Register cap of the forward or tangent row kernel
-        (mg_mesh_set_min_blocks / mg_mesh_set_kernel_min_blocks): 0 or 5."""
+        """Register cap of the forward, tangent or adjoint row kernel
+        (mg_mesh_set_min_blocks / mg_mesh_set_kernel_min_blocks): 0 or 5,
+        or 6 for the adjoint."""
         if kind != "forward":
             L.check(self._lib.mg_mesh_set_kernel_min_blocks(self.handle, self.KINDS[kind],
                                                             int(min_blocks)),

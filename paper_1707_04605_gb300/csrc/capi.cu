@@ -486,6 +486,7 @@ int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st)
   b.batch = M->tune[2].batch;
   b.ring = M->tune[2].ring;
   b.stream = M->tune[2].stream;
+  b.min_blocks = M->tune[2].min_blocks;
   b.pdl = M->dep_launch;
   return mg::launch_adjoint(b, S_pad, st);
 }
@@ -1102,7 +1103,9 @@ int mg_mesh_set_min_blocks(mg_mesh* M, int min_blocks) {
 }
 
 int mg_mesh_set_kernel_min_blocks(mg_mesh* M, int kind, int min_blocks) {
-  if (!M || kind < 0 || kind > 1 || (min_blocks != 0 && min_blocks != 5)) return MG_ERR_ARG;
+  if (!M || kind < 0 || kind > 2 ||
+      (min_blocks != 0 && min_blocks != 5 && (min_blocks != 6 || kind != 2)))
+    return MG_ERR_ARG;
   drop_graphs(M);
   M->tune[kind].min_blocks = min_blocks;
   return MG_OK;
@@ -1589,6 +1592,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.batch = M->tune[2].batch;
   aa.ring = M->tune[2].ring;
   aa.stream = M->tune[2].stream;
+  aa.min_blocks = M->tune[2].min_blocks;
   aa.G = G;
   aa.Gc = G + acc;
   aa.H = G + 2 * acc;
@@ -1784,7 +1788,8 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
       {1, 256, 16},        {2, 0, 32, 1, 5},    {4, 0, 32, 1, 5},    {1, 0, 32, 1, 0, 0, 4},
       {2, 0, 32, 1, 0, 0, 4}, {4, 0, 32, 1, 0, 0, 4}, {1, 0, 32, 1, 0, 0, 8},
       {2, 0, 32, 1, 0, 0, 8}, {4, 0, 32, 1, 0, 0, 8}, {1, 0, 32, 1, 0, 0, 0, 4},
-      {2, 0, 32, 1, 5, 0, 0, 4}, {4, 0, 32, 1, 5, 0, 0, 4}, {1, 0, 32, 1, 5}};
+      {2, 0, 32, 1, 5, 0, 0, 4}, {4, 0, 32, 1, 5, 0, 0, 4}, {1, 0, 32, 1, 5},
+      {1, 0, 32, 1, 6},    {2, 0, 32, 1, 6},    {2, 0, 32, 1, 5}};
   const int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
   cudaEvent_t e0, e1;
   MG_CU(cudaEventCreate(&e0));
@@ -1821,10 +1826,10 @@ int mg_autotune(mg_mesh* M, const double* eps, const mg_shots* shots, const doub
     float ms[n_shapes];
     for (int i = 0; i < n_shapes && rc == MG_OK; ++i) {
       ms[i] = 1e30f;
-      // register caps apply to the forward and the tangent, the other
-      // variants to the forward only
+      // register caps: 5 CTAs per SM for every kind, 6 for the adjoint;
+      // the other variants apply to the forward only
       if (((shapes[i].bulk || shapes[i].sweep || shapes[i].tma) && kind != 0) ||
-          (shapes[i].min_blocks && kind == 2))
+          (shapes[i].min_blocks == 6 && kind != 2))
         continue;
       rc = time_of(kind, shapes[i], &ms[i]);
     }

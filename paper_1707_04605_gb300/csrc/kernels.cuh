@@ -85,6 +85,7 @@ struct AdjointArgs {
   int32_t hint = 0;         // row kernel: L2 evict-first on the read of pk
   int32_t ring = 0;         // row kernel: gather ring depth as in StepArgs
   int32_t stream = 0;       // row kernel: once-read loads without L1 allocation
+  int32_t min_blocks = 0;   // row kernel: 0, or 5 or 6 resident CTAs per SM (register cap)
   float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;

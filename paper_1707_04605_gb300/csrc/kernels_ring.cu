@@ -20,7 +20,7 @@ int launch_step_ring(const StepArgs& a, int S_pad, cudaStream_t st) {
   const int cols = a.cols ? a.cols : S_pad;
   Shape sh = shape_of(a.K.n, cols, a.batch);
   if (a.sweep > 1) sh.grid.x = (sh.grid.x + a.sweep - 1) / a.sweep;
-  if (!range_ok(sh, a.col0, cols, a.ld) || a.min_blocks != 0) return MG_ERR_ARG;
+  if (!range_ok(sh, a.col0, cols, a.ld)) return MG_ERR_ARG;
   if (int rc = ring_check(a.ring, 1, sh.nv)) return rc;
   cudaError_t err = cudaSuccess;
   if (a.ring == 4) {
@@ -38,7 +38,6 @@ int launch_tangent_ring(const TangentArgs& a, int S_pad, cudaStream_t st) {
   if (!range_ok(sh, a.f.col0, cols, a.f.ld)) return MG_ERR_ARG;
   if (int rc = ring_check(a.f.ring, 2, sh.nv)) return rc;
   cudaError_t err = cudaSuccess;
-  if (a.f.min_blocks != 0) return MG_ERR_ARG;
   if (a.f.ring == 4) {
     MG_ROWS_SWITCH_M(k_tangent_rows, 1, 4, 2, a.f.pdl, a)
   } else {
@@ -70,9 +69,9 @@ int launch_adjoint_ring(const AdjointArgs& a, int S_pad, cudaStream_t st) {
   if (int rc = ring_check(a.ring, 1, sh.nv)) return rc;
   cudaError_t err = cudaSuccess;
   if (a.ring == 4) {
-    MG_ROWS_SWITCH(k_adjoint_rows, 4, 1, a.pdl, a)
+    MG_ROWS_SWITCH_M(k_adjoint_rows, 1, 4, 1, a.pdl, a)
   } else {
-    MG_ROWS_SWITCH(k_adjoint_rows, 8, 1, a.pdl, a)
+    MG_ROWS_SWITCH_M(k_adjoint_rows, 1, 8, 1, a.pdl, a)
   }
   if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();

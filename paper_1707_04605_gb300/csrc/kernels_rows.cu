@@ -296,7 +296,15 @@ int launch_adjoint(const AdjointArgs& a, int S_pad, cudaStream_t st) {
   const Shape sh = shape_of(a.K.n, cols, a.batch);
   if (!range_ok(sh, a.col0, cols, a.ld)) return MG_ERR_ARG;
   cudaError_t err = cudaSuccess;
-  MG_ROWS_SWITCH(k_adjoint_rows, 0, 1, a.pdl, a)
+  if (a.min_blocks == 6) {
+    MG_ROWS_SWITCH_M(k_adjoint_rows, 6, 0, 1, a.pdl, a)
+  } else if (a.min_blocks == 5) {
+    MG_ROWS_SWITCH_M(k_adjoint_rows, 5, 0, 1, a.pdl, a)
+  } else if (a.min_blocks == 0) {
+    MG_ROWS_SWITCH_M(k_adjoint_rows, 1, 0, 1, a.pdl, a)
+  } else {
+    return MG_ERR_ARG;
+  }
   if (err != cudaSuccess) return MG_ERR_CUDA;
   return check_launch();
 }

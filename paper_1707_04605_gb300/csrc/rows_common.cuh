@@ -617,8 +617,8 @@ __device__ __forceinline__ void kahan_step(float& s, float& c, float term) {
   s = t;
 }
 
-// The reverse step of row block `blk`.
-template <int LPR, int NV, int R>
+// The reverse step of row block `blk`.  LATE as in step_rows_block.
+template <int LPR, int NV, int R, bool LATE = false>
 __device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk) {
   constexpr int RPW = 32 / LPR, TW = 4 * LPR * NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -646,15 +646,27 @@ __device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk
       cp_async4(mine + 3, a.Hc + gi);
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    const float4 c = ld_coef(a.coef + row, a.stream);
     const size_t ro = (size_t)row * a.ld + base;
-    float4 old[NV], pk[NV], self[NV], acc[NV];
+    float4 c, old[NV], pk[NV], self[NV], acc[NV];
+    if constexpr (!LATE) {
+      c = ld_coef(a.coef + row, a.stream);
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      old[j] = ld_once<false>(a.mu1 + ro + 4 * LPR * j, 0, a.stream);  // mu_{k+1}
-      pk[j] = ld_once<true>(a.pk + ro + 4 * LPR * j, a.hint, a.stream);
+      for (int j = 0; j < NV; ++j) {
+        old[j] = ld_once<false>(a.mu1 + ro + 4 * LPR * j, 0, a.stream);  // mu_{k+1}
+        pk[j] = ld_once<true>(a.pk + ro + 4 * LPR * j, a.hint, a.stream);
+      }
     }
     gather1<LPR, NV, R>(r, a.mu + base, row, lr, mask, a.ld, self, acc);
+    if constexpr (LATE) {
+      c = ld_pinned(reinterpret_cast<const float*>(a.coef + row));
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        old[j] = a.stream ? ld_once<false>(a.mu1 + ro + 4 * LPR * j, 0, a.stream)
+                          : ld_pinned(a.mu1 + ro + 4 * LPR * j);
+        pk[j] = a.hint || a.stream ? ld_once<true>(a.pk + ro + 4 * LPR * j, a.hint, a.stream)
+                                   : ld_pinned(a.pk + ro + 4 * LPR * j);
+      }
+    }
     float4 out[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) out[j] = leap(c, self[j], old[j], acc[j]);
@@ -690,9 +702,10 @@ __device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk
   }
 }
 
-template <int LPR, int NV, int R>
-__global__ void __launch_bounds__(kThreads) k_adjoint_rows(AdjointArgs a) {
-  adjoint_rows_block<LPR, NV, R>(a, blockIdx.x);
+// MINB > 1: a register cap (6 resident CTAs per SM), with the late loads.
+template <int LPR, int NV, int MINB, int R>
+__global__ void __launch_bounds__(kThreads, MINB) k_adjoint_rows(AdjointArgs a) {
+  adjoint_rows_block<LPR, NV, R, (MINB > 1)>(a, blockIdx.x);
 }
 
 // Launch shape for `cols` shot columns (a multiple of 4: a power of two up

@@ -411,6 +411,18 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     yc, jvc = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
     assert torch.equal(yc, yf) and torch.equal(jvc, jvf)
     assert torch.equal(yc, ref[0])
+    # the adjoint's register caps, from checkpoints and on the kept history
+    g_kept = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
+                                 reuse_checkpoints=True)
+    for cap in (5, 6):
+        mesh.set_min_blocks(cap, "adjoint")
+        assert mesh.tuning()["adjoint"]["min_blocks"] == cap
+        mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
+        assert torch.equal(mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
+                                               reuse_checkpoints=True), g_kept)
+        # a J^T from its own checkpoints replaces the kept history
+        assert torch.equal(mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W,
+                                               ckpt_every=64), ref[1])
 
 
 @pytest.mark.parametrize("S,batch,groups,chunk", [(100, 2, 1, 128), (100, 1, 2, 128),
