@@ -1,11 +1,11 @@
 // Uneven batches: several independent problems (own mesh handle, eps, shot
-// batch, wavelet and dt; common step count).  The instances are cut into
-// groups whose states fit half of L2; each group of several instances is
-// advanced by one kernel launch per leapfrog step over a work list of
-// (instance, row block, source tile) items, so small instances share the
-// GPU instead of leaving it idle, while every step still finds its states
-// in L2; an instance too large to share L2 runs the tuned single-instance
-// path.
+// batch, wavelet and dt; common step count).  The instances whose step
+// alone is bound by launch latency are packed into groups whose states fit
+// half of L2; each group of several instances is advanced by one kernel
+// launch per leapfrog step over a work list of (instance, row block, source
+// tile) items, so small instances share the GPU instead of leaving it idle,
+// while every step still finds its states in L2; every other instance runs
+// the tuned single-instance path.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -269,13 +269,20 @@ int check_batch(int n_inst, mg_mesh* const* meshes) {
   return MG_OK;
 }
 
-// L2-aware grouping.  Advancing every instance at every step touches the
-// states of all of them; when those exceed L2 every step streams from HBM,
-// while an instance run on its own may stay L2-resident.  So the batch is
-// cut, in the caller's order, into groups whose working set (`states`
-// padded states per instance) fits half of L2: a group of several
-// instances runs the batched kernels, an instance alone runs the tuned
-// single-instance path (its autotuned kernels and CUDA graphs).
+// Node-shot updates per step below which one instance's step is bound by
+// launch latency on its own: about 3.5 us per step of the single-instance
+// path at ~400 G node-shot updates/s.
+constexpr size_t kLatencyBoundWork = size_t(3) << 19;
+
+// Grouping.  An instance with a step of at least kLatencyBoundWork updates
+// runs alone on the tuned single-instance path (its autotuned kernels and
+// CUDA graphs): a batched launch cannot do its work faster, and advancing
+// it with others at every step would touch the states of all of them, which
+// then stream from HBM once they exceed L2.  The latency-bound instances
+// are packed, largest first, into groups whose working set (`states` padded
+// states per instance) fits half of L2 (first fit), and each group of
+// several runs the batched kernels.  Instances are independent, so the
+// order in which groups run does not change any result.
 std::vector<std::vector<int>> l2_groups(int n_inst, mg_mesh* const* meshes, const mg_shots* shots,
                                         int states) {
   int dev = 0, l2 = 0;
@@ -284,19 +291,32 @@ std::vector<std::vector<int>> l2_groups(int n_inst, mg_mesh* const* meshes, cons
     l2 = 64 << 20;
   const size_t budget = (size_t)l2 / 2;
   std::vector<std::vector<int>> groups;
-  size_t used = 0;
+  std::vector<size_t> used;                 // working set of each packed group
+  std::vector<std::pair<size_t, int>> small;   // (working set, instance)
   for (int i = 0; i < n_inst; ++i) {
     MeshView v;
     mesh_view(meshes[i], &v);
-    const size_t ws = (size_t)states * v.n * padded_shots(shots[i].n_shots) * sizeof(float);
-    if (groups.empty() || used + ws > budget || ws > budget) {
+    const size_t cols = padded_shots(shots[i].n_shots);
+    const size_t ws = (size_t)states * v.n * cols * sizeof(float);
+    if ((size_t)v.n * cols >= kLatencyBoundWork || ws > budget)
       groups.push_back({i});
-      used = ws;
-    } else {
-      groups.back().push_back(i);
-      used += ws;
+    else
+      small.push_back({ws, i});
+  }
+  std::stable_sort(small.begin(), small.end(),
+                   [](const std::pair<size_t, int>& x, const std::pair<size_t, int>& y) {
+                     return x.first > y.first;
+                   });
+  const size_t first_packed = groups.size();
+  for (const auto& [ws, i] : small) {
+    size_t g = first_packed;
+    while (g < groups.size() && used[g - first_packed] + ws > budget) ++g;
+    if (g == groups.size()) {
+      groups.push_back({});
+      used.push_back(0);
     }
-    if (ws > budget) used = budget + 1;   // an instance beyond the budget stays alone
+    groups[g].push_back(i);
+    used[g - first_packed] += ws;
   }
   return groups;
 }
@@ -391,7 +411,6 @@ extern "C" int mg_jacobian_T_apply_batch(int n_inst, mg_mesh* const* meshes, con
   if (!levels || !eps || !shots || !wavelets || !dts || !w || !g || nt < 1 || ckpt_every < 1)
     return MG_ERR_ARG;
   if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < n_inst; ++i)
     if (!w[i] || !g[i]) return MG_ERR_ARG;
   for (const auto& grp : l2_groups(n_inst, meshes, shots, 3)) {
