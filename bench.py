@@ -212,20 +212,20 @@ TRAFFIC = {
     # groups; sha1 of the kernel sources).  Captures (--cache-control none,
     # steady-state launches) summarised in profiles/launch_list_asteroid_2d_bench.md
     # and profiles/forward_ellipsoid_3d_s64.md.
-    # k_tangent_rows<16, 1, 0>, fused forward + tangent writing the kept
-    # history, two shot groups of 64 columns: 11.6 MB read + 24.6 MB written
-    # per launch, two launches per step
-    ("asteroid_2d fused", (1, 0, 2, 0, 0, 0, 0, 0), True): (72.4e6, "5cdb51dee7d12692c143c5803c563120f34469d3"),
-    # k_adjoint_rows<16, 2, 0>, reverse step on the kept history, one launch
-    # of 128 columns: 35.1 MB read + 18.4 MB written
-    ("asteroid_2d reverse", (2, 0, 1, 0, 0, 0, 0, 0), True): (53.5e6, "5cdb51dee7d12692c143c5803c563120f34469d3"),
-    # k_tangent_rows<16, 1, 0>, lockstep forward + tangent (J v of the
-    # checkpointed step), two shot groups: 11.0 MB read + 15.3 MB written
-    # per launch
-    ("asteroid_2d tangent", (1, 0, 2, 0, 0, 0, 0, 0), True): (52.6e6, "5cdb51dee7d12692c143c5803c563120f34469d3"),
-    # k_step_rows<8, 2, 5, 0>, register cap, 4 row blocks per CTA: 1237.9 MB
-    # read + 466.7 MB written per launch
-    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4, 0), False): (1.7046e9, "5cdb51dee7d12692c143c5803c563120f34469d3"),
+    # k_tangent_rows<16, 1, 5, 0>, fused forward + tangent writing the kept
+    # history, register cap, two shot groups of 64 columns: 10.5 MB read +
+    # 24.5 MB written per launch, two launches per step
+    ("asteroid_2d fused", (1, 0, 2, 5, 0, 0, 0, 0), True): (70.0e6, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
+    # k_adjoint_rows<16, 2, 5, 0>, reverse step on the kept history, register
+    # cap, one launch of 128 columns: 36.5 MB read + 20.9 MB written
+    ("asteroid_2d reverse", (2, 0, 1, 5, 0, 0, 0, 0), True): (57.5e6, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
+    # k_tangent_rows<16, 1, 5, 0>, lockstep forward + tangent (J v of the
+    # checkpointed step), register cap, two shot groups: 9.6 MB read +
+    # 15.3 MB written per launch
+    ("asteroid_2d tangent", (1, 0, 2, 5, 0, 0, 0, 0), True): (49.7e6, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
+    # k_step_rows<8, 2, 5, 0>, register cap, 4 row blocks per CTA: 1228.3 MB
+    # read + 465.8 MB written per launch
+    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4, 0), False): (1.6941e9, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
 }
 
 
