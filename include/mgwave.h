@@ -648,11 +648,14 @@ int mg_approx_jacobian(mg_mesh* mesh, int level, const double* eps, const mg_sho
  * conductivity the traces equal mg_forward's with the Neumann boundary.
  *   xi    [n_cells] FP64 >= 0 per finest cell (caller order), or NULL.
  *   zeta  [n_cells][dim] FP64 >= 0 per finest cell and direction, or NULL.
- *   traces, shots, wavelet, dt, nt, flags (MG_HOST_PTRS, MG_ALLOW_CFL) as
- *   mg_forward; dt is checked against the CFL bound of mg_cfl_dt (the
- *   explicit damping terms need dt zeta and dt (sigma + xi)/eps below 1 in
- *   addition, which the caller chooses).  Synchronous; one launch per flux
- *   and per node update.
+ *   traces, shots, wavelet, dt, nt, flags (MG_HOST_PTRS, MG_ALLOW_CFL,
+ *   MG_NO_GRAPH) as mg_forward; dt is checked against the CFL bound of
+ *   mg_cfl_dt (the explicit damping terms need dt zeta and dt (sigma + xi)/eps
+ *   below 1 in addition, which the caller chooses).  Synchronous; one launch
+ *   per flux and per node update, whole chunks of the handle's graph chunk
+ *   length replayed as one CUDA graph each (recorded once per call; step
+ *   index read from a device counter the graph advances) unless
+ *   MG_NO_GRAPH; the same results either way.
  * Errors: MG_ERR_ARG (null, negative zeta, degenerate cell), MG_ERR_CFL,
  * MG_ERR_UNSUPPORTED (other flags), MG_ERR_OOM, MG_ERR_CUDA. */
 int mg_forward_pml(mg_mesh* mesh, const double* eps, const mg_shots* shots, const double* wavelet,
@@ -688,6 +691,10 @@ int mg_jacobian_apply_pml(mg_mesh* mesh, int level, const double* eps, const mg_
  *   g        [cells of level] FP64 out;
  *   ckpt_every  checkpoint spacing >= 1 (memory: ceil(nt / ckpt_every)
  *            copies of p and q, and ckpt_every + 1 copies of p).
+ * Each segment's recomputed p states are written straight into their
+ * slots of the segment buffer; a full segment (recompute and reverse
+ * steps) replays as one CUDA graph, as do chunks of the reverse steps when
+ * one segment holds the whole run (unless MG_NO_GRAPH).
  * Other arguments and flags as mg_jacobian_apply_pml.  Synchronous. */
 int mg_jacobian_T_apply_pml(mg_mesh* mesh, int level, const double* eps,
                             const mg_shots* shots, const double* wavelet, double dt, int nt,

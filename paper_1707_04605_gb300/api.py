@@ -599,9 +599,10 @@ def approx_jacobian(mesh: Mesh, level, eps, shots, wavelet, dt, u=None, *, want_
 
 
 def forward_pml(mesh: Mesh, eps, shots, wavelet, dt, xi=None, zeta=None, nt=None, *,
-                allow_cfl=False, stream=None):
+                allow_cfl=False, stream=None, flags=0):
     """Traces [n_traces, nt] float32 of the first-order flux leapfrog with the
-    split-field layer xi [cells], zeta [cells, dim] (mg_forward_pml)."""
+    split-field layer xi [cells], zeta [cells, dim] (mg_forward_pml); flags
+    may add MG_NO_GRAPH."""
     lib = L.load()
     sh = Shots.of(shots)
     nt = int(len(wavelet) if nt is None else nt)
@@ -611,7 +612,7 @@ def forward_pml(mesh: Mesh, eps, shots, wavelet, dt, xi=None, zeta=None, nt=None
     pxi = next(it)[1] if xi is not None else None
     pzeta = next(it)[1] if zeta is not None else None
     out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
-    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0) | int(flags)
     rc = lib.mg_forward_pml(mesh.handle, pe, C.byref(sh.c), pw, float(dt), nt, pxi, pzeta,
                             _ptr(out), st, f)
     L.check(rc, "mg_forward_pml")
@@ -619,7 +620,7 @@ def forward_pml(mesh: Mesh, eps, shots, wavelet, dt, xi=None, zeta=None, nt=None
 
 
 def jacobian_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, v, xi=None, zeta=None,
-                       nt=None, *, allow_cfl=False, stream=None):
+                       nt=None, *, allow_cfl=False, stream=None, flags=0):
     """J v [n_traces, nt] float32 of forward_pml's traces for v on the cells of
     ``level`` (mg_jacobian_apply_pml)."""
     lib = L.load()
@@ -632,7 +633,7 @@ def jacobian_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, v, xi=None, z
     pxi = next(it)[1] if xi is not None else None
     pzeta = next(it)[1] if zeta is not None else None
     out = _alloc(dev, (sh.n_traces, nt), "float32", eps)
-    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0) | int(flags)
     rc = lib.mg_jacobian_apply_pml(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
                                    nt, pxi, pzeta, pv, _ptr(out), st, f)
     L.check(rc, "mg_jacobian_apply_pml")
@@ -640,7 +641,7 @@ def jacobian_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, v, xi=None, z
 
 
 def jacobian_T_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, w, xi=None, zeta=None,
-                         nt=None, *, ckpt_every=64, allow_cfl=False, stream=None):
+                         nt=None, *, ckpt_every=64, allow_cfl=False, stream=None, flags=0):
     """J^T w (float64 [cells of level]) of forward_pml's traces for the trace
     weights w [n_traces, nt] float32 (mg_jacobian_T_apply_pml)."""
     lib = L.load()
@@ -653,7 +654,7 @@ def jacobian_T_apply_pml(mesh: Mesh, level, eps, shots, wavelet, dt, w, xi=None,
     pxi = next(it)[1] if xi is not None else None
     pzeta = next(it)[1] if zeta is not None else None
     g = _alloc(dev, (mesh.n_cells_per_level[level],), "float64", eps)
-    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0)
+    f = f0 | (L.MG_ALLOW_CFL if allow_cfl else 0) | int(flags)
     rc = lib.mg_jacobian_T_apply_pml(mesh.handle, int(level), pe, C.byref(sh.c), pw, float(dt),
                                      nt, pxi, pzeta, pw_, _ptr(g), int(ckpt_every), st, f)
     L.check(rc, "mg_jacobian_T_apply_pml")

@@ -1880,6 +1880,7 @@ namespace mg {
 int padded_shots(int S) { return round_pad(S); }
 const HostMesh* host_mesh(const mg_mesh* M) { return M ? &M->hm : nullptr; }
 int mesh_device(const mg_mesh* M) { return M->device; }
+int mesh_graph_chunk(const mg_mesh* M) { return M->chunk; }
 void add_launches(mg_mesh* M, int64_t n) { M->launches += n; }
 
 int mesh_view(mg_mesh* M, MeshView* v) {

@@ -36,6 +36,7 @@ struct HostMesh;
 // launches made on its behalf by entry points outside capi.cu.
 const HostMesh* host_mesh(const mg_mesh* mesh);
 int mesh_device(const mg_mesh* mesh);
+int mesh_graph_chunk(const mg_mesh* mesh);   // steps per CUDA-graph chunk (0: off)
 void add_launches(mg_mesh* mesh, int64_t n);
 
 // One problem of a multi-instance batch, prepared on its own handle: device

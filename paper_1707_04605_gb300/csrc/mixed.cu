@@ -48,6 +48,27 @@ __device__ __forceinline__ void pdl_sync() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Step index of a launch: l, plus the device int *base when the launch is
+// a node of a CUDA graph replayed once per chunk of steps (the graph moves
+// the base at its end).  Read after pdl_sync.
+struct StepRef {
+  int l;
+  const int* base;
+};
+__device__ __forceinline__ int step_of(const StepRef& s) { return s.base ? s.l + *s.base : s.l; }
+
+// p states kept in slots of one buffer: p_l in slot l mod K (stride ns4
+// float4), so that a launch finds its states from its step index alone;
+// seg == nullptr: the launch's own state pointers.
+struct Slots {
+  float4* seg;
+  int64_t ns4;
+  int K;
+};
+__device__ __forceinline__ float4* slot_of(const Slots& s, int l) {
+  return s.seg + (int64_t)(l % s.K) * s.ns4;
+}
+
 // per node: {dt / C_i, R_i + S_i}
 __global__ void k_flux_coefs(CoefArgs c, const double* __restrict__ xi, double dt,
                              float2* __restrict__ out) {
@@ -67,8 +88,10 @@ __global__ void k_flux_coefs(CoefArgs c, const double* __restrict__ xi, double d
 template <int D>
 __global__ void k_flux_q(int64_t m, int ld4, const int32_t* __restrict__ cells,
                          const float* __restrict__ grad, const float* __restrict__ damp,
-                         const float4* __restrict__ p, float4* __restrict__ q, float dt) {
+                         const float4* __restrict__ p, float4* __restrict__ q, float dt,
+                         StepRef sr, Slots sl) {
   pdl_sync();
+  if (sl.seg) p = slot_of(sl, step_of(sr));
   const int64_t total = m * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -106,9 +129,16 @@ __global__ void k_flux_p(int64_t n, int64_t m, int ld4, const int64_t* __restric
                          const float4* p, float4* pout, const int32_t* __restrict__ src_ptr,
                          const int32_t* __restrict__ src_shot, const int32_t* __restrict__ rec_ptr,
                          const int32_t* __restrict__ rec_shot,
-                         const int32_t* __restrict__ rec_trace, float f, float* __restrict__ traces,
-                         int nt, int l) {
+                         const int32_t* __restrict__ rec_trace, const float* __restrict__ fl,
+                         float* __restrict__ traces, int nt, StepRef sr, Slots sl) {
   pdl_sync();
+  const int l = step_of(sr);
+  const float f = __ldg(fl + l);
+  if (sl.seg) {   // p_l in slot l, p_{l+1} into the next slot
+    pout = slot_of(sl, l);
+    p = pout;
+    pout += sl.ns4;
+  }
   const int64_t total = n * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -180,9 +210,12 @@ __global__ void k_flux_p_tan(int64_t n, int64_t m, int ld4, const int64_t* __res
                              const int32_t* __restrict__ src_shot,
                              const int32_t* __restrict__ rec_ptr,
                              const int32_t* __restrict__ rec_shot,
-                             const int32_t* __restrict__ rec_trace, float f,
-                             float* __restrict__ traces, int nt, int l) {
+                             const int32_t* __restrict__ rec_trace,
+                             const float* __restrict__ fl, float* __restrict__ traces, int nt,
+                             StepRef sr) {
   pdl_sync();
+  const int l = step_of(sr);
+  const float f = __ldg(fl + l);
   const int64_t total = n * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -240,7 +273,8 @@ __global__ void k_flux_p_tan(int64_t n, int64_t m, int ld4, const int64_t* __res
   }
 }
 
-// Adjoint node kernel of reverse step l.  a = adjoint of p_{l+1}: what step
+// Adjoint node kernel of reverse step l (p_l in slot l mod K of sl, p_{l+1}
+// in the next slot).  a = adjoint of p_{l+1}: what step
 // l+1 sent back (tp + dt sum_k B^(k)T Qt^(k); zero when l = nt-1) plus the
 // weights of the row's receivers at sample l.  Sums a (p_{l+1} - p_l) over
 // the node's shots in FP32 (the threads of a node are consecutive lanes:
@@ -253,13 +287,16 @@ template <int D>
 __global__ void k_flux_adj_p(int64_t n, int64_t m, int ld4, const int64_t* __restrict__ nc_ptr,
                              const int32_t* __restrict__ nc_cell, const float* __restrict__ w,
                              const float2* __restrict__ coef, const float4* __restrict__ Qt,
-                             float4* __restrict__ tp, float4* __restrict__ rr,
-                             const float4* __restrict__ p1, const float4* __restrict__ p0,
+                             float4* __restrict__ tp, float4* __restrict__ rr, Slots sl,
                              double* __restrict__ hacc, const int32_t* __restrict__ rec_ptr,
                              const int32_t* __restrict__ rec_shot,
                              const int32_t* __restrict__ rec_trace,
-                             const float* __restrict__ W, int nt, int l, int first, float dt) {
+                             const float* __restrict__ W, int nt, StepRef sr, float dt) {
   pdl_sync();
+  const int l = step_of(sr);
+  const bool first = l == nt - 1;
+  const float4* __restrict__ p0 = slot_of(sl, l);   // p_l; p_{l+1} in the next slot
+  const float4* __restrict__ p1 = p0 + sl.ns4;
   const int64_t total = n * ld4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -440,34 +477,78 @@ struct Flux {
   int32_t* cells = nullptr;
   float *grad = nullptr, *w = nullptr, *damp = nullptr;
   int32_t *sp = nullptr, *ss = nullptr, *rp = nullptr, *rs = nullptr, *rt = nullptr;
-  std::vector<float> fl;
+  float* fl = nullptr;      // f_l (FP32) per step, device
   float2* coef = nullptr;
 
-  void step_q(float* p, float* q) const {
+  // flux update from p (or, with sl.seg, from the slot of step sr)
+  void step_q(float* p, float* q, cudaStream_t s, StepRef sr = {0, nullptr},
+              Slots sl = {nullptr, 0, 1}) const {
     const int g = grid_for(m * ld4);
     if (d == 2)
-      launch_pdl(k_flux_q<2>, g, st, m, ld4, cells, grad, damp,
-                                      reinterpret_cast<const float4*>(p),
-                                      reinterpret_cast<float4*>(q), (float)dt);
+      launch_pdl(k_flux_q<2>, g, s, m, ld4, cells, grad, damp,
+                 reinterpret_cast<const float4*>(p), reinterpret_cast<float4*>(q), (float)dt, sr,
+                 sl);
     else
-      launch_pdl(k_flux_q<3>, g, st, m, ld4, cells, grad, damp,
-                                      reinterpret_cast<const float4*>(p),
-                                      reinterpret_cast<float4*>(q), (float)dt);
+      launch_pdl(k_flux_q<3>, g, s, m, ld4, cells, grad, damp,
+                 reinterpret_cast<const float4*>(p), reinterpret_cast<float4*>(q), (float)dt, sr,
+                 sl);
   }
-  // p_{l+1} into pout (nullptr: in place over p)
-  void step_p(const float* q, float* p, float* traces, int l, float* pout = nullptr) const {
+  // node update of step sr: p_{l+1} into pout (nullptr: in place over p),
+  // or with sl.seg from the step's slot into the next one
+  void step_p(const float* q, float* p, float* traces, StepRef sr, cudaStream_t s,
+              float* pout = nullptr, Slots sl = {nullptr, 0, 1}) const {
     const int g = grid_for(n * ld4);
     float4* po = reinterpret_cast<float4*>(pout ? pout : p);
     if (d == 2)
-      launch_pdl(k_flux_p<2>, g, st, n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
-                                      reinterpret_cast<const float4*>(q),
-                                      reinterpret_cast<const float4*>(p), po, sp, ss, rp, rs, rt,
-                                      fl[l], traces, nt, l);
+      launch_pdl(k_flux_p<2>, g, s, n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
+                 reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(p), po, sp,
+                 ss, rp, rs, rt, fl, traces, nt, sr, sl);
     else
-      launch_pdl(k_flux_p<3>, g, st, n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
-                                      reinterpret_cast<const float4*>(q),
-                                      reinterpret_cast<const float4*>(p), po, sp, ss, rp, rs, rt,
-                                      fl[l], traces, nt, l);
+      launch_pdl(k_flux_p<3>, g, s, n, m, ld4, c.nc_ptr, c.nc_cell, w, coef,
+                 reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(p), po, sp,
+                 ss, rp, rs, rt, fl, traces, nt, sr, sl);
+  }
+};
+
+// One captured chunk of steps, replayed with cudaGraphLaunch on the
+// caller's stream.  Recorded on a private stream (the caller's may be the
+// legacy default stream, which cannot be captured); destroyed with the
+// call, after the stream it ran on has drained.
+struct Chunk {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t used = nullptr;
+  Chunk() = default;
+  Chunk(const Chunk&) = delete;
+  Chunk& operator=(const Chunk&) = delete;
+  ~Chunk() {
+    if (!exec) return;
+    if (used) cudaStreamSynchronize(used);
+    cudaGraphExecDestroy(exec);
+  }
+  template <class Body>
+  int record(Body&& body) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MG_ERR_CUDA;
+    int rc = MG_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = MG_ERR_CUDA;
+    } else {
+      rc = body(cs);
+      if (cudaStreamEndCapture(cs, &g) != cudaSuccess && rc == MG_OK) rc = MG_ERR_CUDA;
+    }
+    if (rc == MG_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+      exec = nullptr;
+      rc = MG_ERR_CUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc != MG_OK) cudaGetLastError();
+    return rc;
+  }
+  int launch(cudaStream_t st) {
+    used = st;
+    return cudaGraphLaunch(exec, st) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
   }
 };
 
@@ -586,11 +667,11 @@ int flux_setup(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
   else if (cudaMemcpy(wav_h.data(), wavelet, nt * sizeof(double), cudaMemcpyDeviceToHost) !=
            cudaSuccess)
     return MG_ERR_CUDA;
-  F.fl.resize(nt);
+  std::vector<float> fl_h(nt);
   double acc = 0.0;
   for (int l = 0; l < nt; ++l) {
     acc += dt * wav_h[l];
-    F.fl[l] = (float)acc;
+    fl_h[l] = (float)acc;
   }
 
   if (mesh_view(M, &F.V) != MG_OK) return MG_ERR_ARG;
@@ -616,9 +697,10 @@ int flux_setup(mg_mesh* M, const double* eps, const mg_shots* shots, const doubl
   F.rp = X.put(rp);
   F.rs = X.put(rs);
   F.rt = X.put(rt);
+  F.fl = X.put(fl_h);
   F.coef = X.get<float2>(n);
   if (!F.cells || !F.grad || !F.w || !F.damp || !F.sp || !F.ss || !F.rp || !F.rs || !F.rt ||
-      !F.coef)
+      !F.fl || !F.coef)
     return MG_ERR_OOM;
   F.c = F.V.coef_base;
   F.c.eps = F.eps_d;
@@ -641,6 +723,13 @@ struct DeviceScope {
     if (rc_ != MG_OK) return rc_; \
   } while (0)
 
+// Steps per CUDA-graph chunk for a call (0: plain launches): the handle's
+// chunk length, unless MG_NO_GRAPH.
+int chunk_len(const mg_mesh* M, int flags) {
+  const int c = mesh_graph_chunk(M);
+  return (flags & MG_NO_GRAPH) || c < 2 ? 0 : c;
+}
+
 }  // namespace
 }  // namespace mg
 
@@ -649,7 +738,7 @@ extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* sho
                               const double* zeta, float* traces, void* stream, int flags) {
   using namespace mg;
   if (!M || !eps || !shots || !wavelet || !traces || nt < 1 || !(dt > 0.0)) return MG_ERR_ARG;
-  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL | MG_NO_GRAPH)) return MG_ERR_UNSUPPORTED;
   DeviceScope scope(mesh_device(M));
   if (!scope.ok) return MG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -660,13 +749,28 @@ extern "C" int mg_forward_pml(mg_mesh* M, const double* eps, const mg_shots* sho
   float* p = X.get<float>((size_t)n * F.ld);
   float* q = X.get<float>((size_t)F.d * m * F.ld);
   float* tr = F.host ? X.get<float>((size_t)R * nt) : traces;
-  if (!p || !q || !tr) return MG_ERR_OOM;
+  int* base = X.get<int>(1);
+  if (!p || !q || !tr || !base) return MG_ERR_OOM;
   if (cudaMemsetAsync(p, 0, (size_t)n * F.ld * sizeof(float), st) ||
       cudaMemsetAsync(q, 0, (size_t)F.d * m * F.ld * sizeof(float), st))
     return MG_ERR_CUDA;
-  for (int l = 0; l < nt; ++l) {
-    F.step_q(p, q);
-    F.step_p(q, p, tr, l);
+  const int C = chunk_len(M, flags);
+  int l = 0;
+  Chunk ch;
+  if (C && nt >= C) {   // whole chunks: one graph launch each
+    MG_FX(launch_set_int(base, 0, st));
+    MG_FX(ch.record([&](cudaStream_t cs) {
+      for (int j = 0; j < C; ++j) {
+        F.step_q(p, q, cs);
+        F.step_p(q, p, tr, {j, base}, cs);
+      }
+      return launch_add_int(base, C, cs);
+    }));
+    for (; l + C <= nt; l += C) MG_FX(ch.launch(st));
+  }
+  for (; l < nt; ++l) {
+    F.step_q(p, q, st);
+    F.step_p(q, p, tr, {l, nullptr}, st);
   }
   if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
   add_launches(M, 1 + 2 * (int64_t)nt);
@@ -682,7 +786,7 @@ extern "C" int mg_jacobian_apply_pml(mg_mesh* M, int level, const double* eps,
                                      const double* v, float* jv, void* stream, int flags) {
   using namespace mg;
   if (!M || !eps || !shots || !wavelet || !v || !jv || nt < 1 || !(dt > 0.0)) return MG_ERR_ARG;
-  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL | MG_NO_GRAPH)) return MG_ERR_UNSUPPORTED;
   const HostMesh* hm = host_mesh(M);
   if (level < 0 || level >= hm->n_levels) return MG_ERR_ARG;
   DeviceScope scope(mesh_device(M));
@@ -704,7 +808,8 @@ extern "C" int mg_jacobian_apply_pml(mg_mesh* M, int level, const double* eps,
   float* q = X.get<float>(qs);
   float* dq = X.get<float>(qs);
   float* tr = F.host ? X.get<float>((size_t)R * nt) : jv;
-  if (!v_d || !anc || !dv || !C || !dC || !ratio || !p || !dp || !q || !dq || !tr)
+  int* base = X.get<int>(1);
+  if (!v_d || !anc || !dv || !C || !dC || !ratio || !p || !dp || !q || !dq || !tr || !base)
     return MG_ERR_OOM;
   MG_FX(launch_prolong(m, anc, v_d, nullptr, dv, st));
   const unsigned gn = (unsigned)((n + 255) / 256);
@@ -717,22 +822,32 @@ extern "C" int mg_jacobian_apply_pml(mg_mesh* M, int level, const double* eps,
       cudaMemsetAsync(dq, 0, qs * sizeof(float), st))
     return MG_ERR_CUDA;
   const int gp = grid_for(n * F.ld4);
-  for (int l = 0; l < nt; ++l) {
-    F.step_q(p, q);
-    F.step_q(dp, dq);
+  auto step = [&](StepRef sr, cudaStream_t s) {
+    F.step_q(p, q, s);
+    F.step_q(dp, dq, s);
     if (F.d == 2)
-      launch_pdl(k_flux_p_tan<2>, gp, st,
-          n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef, ratio,
-          reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
-          reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp, F.rs,
-          F.rt, F.fl[l], tr, nt, l);
+      launch_pdl(k_flux_p_tan<2>, gp, s, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+                 ratio, reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
+                 reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp,
+                 F.rs, F.rt, F.fl, tr, nt, sr);
     else
-      launch_pdl(k_flux_p_tan<3>, gp, st,
-          n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef, ratio,
-          reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
-          reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp, F.rs,
-          F.rt, F.fl[l], tr, nt, l);
+      launch_pdl(k_flux_p_tan<3>, gp, s, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+                 ratio, reinterpret_cast<const float4*>(q), reinterpret_cast<const float4*>(dq),
+                 reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(dp), F.sp, F.ss, F.rp,
+                 F.rs, F.rt, F.fl, tr, nt, sr);
+  };
+  const int CL = chunk_len(M, flags);
+  int l = 0;
+  Chunk ch;
+  if (CL && nt >= CL) {   // whole chunks: one graph launch each
+    MG_FX(launch_set_int(base, 0, st));
+    MG_FX(ch.record([&](cudaStream_t cs) {
+      for (int j = 0; j < CL; ++j) step({j, base}, cs);
+      return launch_add_int(base, CL, cs);
+    }));
+    for (; l + CL <= nt; l += CL) MG_FX(ch.launch(st));
   }
+  for (; l < nt; ++l) step({l, nullptr}, st);
   if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
   add_launches(M, 5 + 3 * (int64_t)nt);
   if (F.host && cudaMemcpyAsync(jv, tr, (size_t)R * nt * sizeof(float), cudaMemcpyDeviceToHost,
@@ -749,7 +864,7 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   using namespace mg;
   if (!M || !eps || !shots || !wavelet || !w || !g || nt < 1 || !(dt > 0.0) || ckpt_every < 1)
     return MG_ERR_ARG;
-  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL)) return MG_ERR_UNSUPPORTED;
+  if (flags & ~(MG_HOST_PTRS | MG_ALLOW_CFL | MG_NO_GRAPH)) return MG_ERR_UNSUPPORTED;
   const HostMesh* hm = host_mesh(M);
   if (level < 0 || level >= hm->n_levels) return MG_ERR_ARG;
   DeviceScope scope(mesh_device(M));
@@ -769,9 +884,9 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   const float* W = F.host ? X.put(w, (size_t)R * nt) : w;
   float* ck_p = X.get<float>(ns * nck);
   float* ck_q = X.get<float>(qs * nck);
-  float* p = X.get<float>(ns);
-  float* q = X.get<float>(qs);
   float* seg = X.get<float>(ns * (K + 1));
+  float* p = keep ? seg : X.get<float>(ns);   // the forward's state (keep: unused)
+  float* q = X.get<float>(qs);
   float* trd = X.get<float>((size_t)R * nt);
   float* tp = X.get<float>(ns);
   float* rr = X.get<float>(ns);
@@ -787,8 +902,9 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
   int64_t* lp_d = X.put(lp);
   int32_t* li_d = X.put(li);
   double* go = F.host ? X.get<double>(nc) : g;
+  int* base = X.get<int>(1);
   if (!W || !ck_p || !ck_q || !p || !q || !seg || !trd || !tp || !rr || !Qt || !hacc || !C ||
-      !gC || !vol || !gf || !lp_d || !li_d || !go)
+      !gC || !vol || !gf || !lp_d || !li_d || !go || !base)
     return MG_ERR_OOM;
   if (cudaMemsetAsync(p, 0, ns * sizeof(float), st) ||
       cudaMemsetAsync(q, 0, qs * sizeof(float), st) ||
@@ -796,68 +912,128 @@ extern "C" int mg_jacobian_T_apply_pml(mg_mesh* M, int level, const double* eps,
       cudaMemsetAsync(hacc, 0, (size_t)n * nseg * sizeof(double), st))
     return MG_ERR_CUDA;
   int64_t launches = 0;
+  const int CL = chunk_len(M, flags);
+  // p_l in slot l of seg (keep: the whole run, slots 0..nt) or in slot
+  // l - l0 of the segment [l0, l0 + K) being reversed
+  const Slots sl{reinterpret_cast<float4*>(seg), (int64_t)ns / 4, keep ? nt + 1 : K};
   // forward, keeping (p_l, q_{l-1/2}) at l = 0, K, 2K, ... (or every p_l)
   if (keep && cudaMemsetAsync(seg, 0, ns * sizeof(float), st)) return MG_ERR_CUDA;
-  for (int l = 0; l < nt; ++l) {
-    if (keep) {   // p_l in seg slot l, p_{l+1} written to slot l + 1
-      F.step_q(seg + ns * l, q);
-      F.step_p(q, seg + ns * l, trd, l, seg + ns * (l + 1));
-      launches += 2;
-      continue;
+  auto fwd_slots = [&](StepRef sr, cudaStream_t s) {   // p_l in its slot, p_{l+1} the next
+    F.step_q(seg, q, s, sr, sl);
+    F.step_p(q, seg, trd, sr, s, nullptr, sl);
+  };
+  auto fwd = [&](StepRef sr, cudaStream_t s) {
+    if (keep) {
+      fwd_slots(sr, s);
+    } else {
+      F.step_q(p, q, s);
+      F.step_p(q, p, trd, sr, s);
     }
-    if (l % K == 0) {
-      if (cudaMemcpyAsync(ck_p + ns * (l / K), p, ns * sizeof(float), cudaMemcpyDeviceToDevice,
-                          st) ||
-          cudaMemcpyAsync(ck_q + qs * (l / K), q, qs * sizeof(float), cudaMemcpyDeviceToDevice,
-                          st))
+  };
+  // graph chunks: keep, CL steps; else one checkpoint interval of K steps
+  const int LF = keep ? CL : (CL ? K : 0);
+  int l = 0;
+  Chunk chf;
+  if (LF >= 2 && nt >= LF) {
+    MG_FX(launch_set_int(base, 0, st));
+    MG_FX(chf.record([&](cudaStream_t cs) {
+      for (int j = 0; j < LF; ++j) fwd({j, base}, cs);
+      return launch_add_int(base, LF, cs);
+    }));
+    for (; l + LF <= nt; l += LF) {
+      if (!keep &&
+          (cudaMemcpyAsync(ck_p + ns * (l / K), p, ns * sizeof(float), cudaMemcpyDeviceToDevice,
+                           st) ||
+           cudaMemcpyAsync(ck_q + qs * (l / K), q, qs * sizeof(float), cudaMemcpyDeviceToDevice,
+                           st)))
         return MG_ERR_CUDA;
+      MG_FX(chf.launch(st));
+      launches += 2 * LF;
     }
-    F.step_q(p, q);
-    F.step_p(q, p, trd, l);
+  }
+  for (; l < nt; ++l) {
+    if (!keep && l % K == 0 &&
+        (cudaMemcpyAsync(ck_p + ns * (l / K), p, ns * sizeof(float), cudaMemcpyDeviceToDevice,
+                         st) ||
+         cudaMemcpyAsync(ck_q + qs * (l / K), q, qs * sizeof(float), cudaMemcpyDeviceToDevice,
+                         st)))
+      return MG_ERR_CUDA;
+    fwd({l, nullptr}, st);
     launches += 2;
   }
-  // reverse, segment by segment
+  // reverse step l: p_l, p_{l+1} from their slots
   const int gp = grid_for(n * F.ld4), gq = grid_for(m * F.ld4);
   const float fdt = (float)dt;
-  for (int c = nck - 1; c >= 0; --c) {
-    const int l0 = c * K, l1 = std::min(nt, l0 + K);
-    if (!keep &&
-        (cudaMemcpyAsync(p, ck_p + ns * c, ns * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
-         cudaMemcpyAsync(q, ck_q + qs * c, qs * sizeof(float), cudaMemcpyDeviceToDevice, st) ||
-         cudaMemcpyAsync(seg, p, ns * sizeof(float), cudaMemcpyDeviceToDevice, st)))
-      return MG_ERR_CUDA;
-    for (int l = l0; l < l1 && !keep; ++l) {
-      F.step_q(p, q);
-      F.step_p(q, p, trd, l);
-      if (cudaMemcpyAsync(seg + ns * (l + 1 - l0), p, ns * sizeof(float),
-                          cudaMemcpyDeviceToDevice, st))
-        return MG_ERR_CUDA;
+  auto rev = [&](StepRef sr, cudaStream_t s) {
+    if (F.d == 2) {
+      launch_pdl(k_flux_adj_p<2>, gp, s, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+                 reinterpret_cast<const float4*>(Qt), reinterpret_cast<float4*>(tp),
+                 reinterpret_cast<float4*>(rr), sl, hacc, F.rp, F.rs, F.rt, W, nt, sr, fdt);
+      launch_pdl(k_flux_adj_q<2>, gq, s, m, F.ld4, F.cells, F.grad, F.damp,
+                 reinterpret_cast<const float4*>(rr), reinterpret_cast<float4*>(Qt), fdt);
+    } else {
+      launch_pdl(k_flux_adj_p<3>, gp, s, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
+                 reinterpret_cast<const float4*>(Qt), reinterpret_cast<float4*>(tp),
+                 reinterpret_cast<float4*>(rr), sl, hacc, F.rp, F.rs, F.rt, W, nt, sr, fdt);
+      launch_pdl(k_flux_adj_q<3>, gq, s, m, F.ld4, F.cells, F.grad, F.damp,
+                 reinterpret_cast<const float4*>(rr), reinterpret_cast<float4*>(Qt), fdt);
+    }
+  };
+  // segment [l0, l0 + len) with p_{l0} in slot 0 and q_{l0-1/2} in q: its
+  // forward steps into slots 1..len (q in place), then the reverse steps
+  // l0 + len - 1 .. l0; s0 is step l0
+  auto segment = [&](int len, StepRef s0, cudaStream_t s) {
+    for (int j = 0; j < len; ++j) fwd_slots({s0.l + j, s0.base}, s);
+    for (int j = len - 1; j >= 0; --j) rev({s0.l + j, s0.base}, s);
+  };
+  Chunk chr;
+  if (keep) {   // reverse steps nt-1 .. 0 in chunks of CL (base: the chunk's first step)
+    int k = nt;   // steps below k remain
+    if (CL >= 2 && nt >= CL) {
+      MG_FX(launch_set_int(base, nt - 1, st));
+      MG_FX(chr.record([&](cudaStream_t cs) {
+        for (int j = 0; j < CL; ++j) rev({-j, base}, cs);
+        return launch_add_int(base, -CL, cs);
+      }));
+      for (; k >= CL; k -= CL) {
+        MG_FX(chr.launch(st));
+        launches += 2 * CL;
+      }
+    }
+    for (int r = k - 1; r >= 0; --r) {
+      rev({r, nullptr}, st);
       launches += 2;
     }
-    for (int l = l1 - 1; l >= l0; --l) {
-      const float4* p1 = reinterpret_cast<const float4*>(seg + ns * (l + 1 - l0));
-      const float4* p0 = reinterpret_cast<const float4*>(seg + ns * (l - l0));
-      const int first = l == nt - 1;
-      if (F.d == 2) {
-        launch_pdl(k_flux_adj_p<2>, gp, st, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
-                                             reinterpret_cast<const float4*>(Qt),
-                                             reinterpret_cast<float4*>(tp),
-                                             reinterpret_cast<float4*>(rr), p1, p0, hacc, F.rp,
-                                             F.rs, F.rt, W, nt, l, first, fdt);
-        launch_pdl(k_flux_adj_q<2>, gq, st, m, F.ld4, F.cells, F.grad, F.damp,
-                                             reinterpret_cast<const float4*>(rr),
-                                             reinterpret_cast<float4*>(Qt), fdt);
-      } else {
-        launch_pdl(k_flux_adj_p<3>, gp, st, n, m, F.ld4, F.c.nc_ptr, F.c.nc_cell, F.w, F.coef,
-                                             reinterpret_cast<const float4*>(Qt),
-                                             reinterpret_cast<float4*>(tp),
-                                             reinterpret_cast<float4*>(rr), p1, p0, hacc, F.rp,
-                                             F.rs, F.rt, W, nt, l, first, fdt);
-        launch_pdl(k_flux_adj_q<3>, gq, st, m, F.ld4, F.cells, F.grad, F.damp,
-                                             reinterpret_cast<const float4*>(rr),
-                                             reinterpret_cast<float4*>(Qt), fdt);
+  } else {
+    const int nfull = nt / K;
+    auto load = [&](int c) {   // checkpoint c into slot 0 and q
+      return cudaMemcpyAsync(seg, ck_p + ns * c, ns * sizeof(float), cudaMemcpyDeviceToDevice,
+                             st) == cudaSuccess &&
+             cudaMemcpyAsync(q, ck_q + qs * c, qs * sizeof(float), cudaMemcpyDeviceToDevice,
+                             st) == cudaSuccess;
+    };
+    if (nt % K) {   // the last, shorter segment: plain launches
+      if (!load(nfull)) return MG_ERR_CUDA;
+      segment(nt - nfull * K, {nfull * K, nullptr}, st);
+      launches += 4 * (int64_t)(nt - nfull * K);
+    }
+    if (CL && K >= 2 && nfull >= 1) {   // full segments: one graph launch each
+      MG_FX(launch_set_int(base, (nfull - 1) * K, st));
+      MG_FX(chr.record([&](cudaStream_t cs) {
+        segment(K, {0, base}, cs);
+        return launch_add_int(base, -K, cs);
+      }));
+      for (int c = nfull - 1; c >= 0; --c) {
+        if (!load(c)) return MG_ERR_CUDA;
+        MG_FX(chr.launch(st));
+        launches += 4 * (int64_t)K;
       }
-      launches += 2;
+    } else {
+      for (int c = nfull - 1; c >= 0; --c) {
+        if (!load(c)) return MG_ERR_CUDA;
+        segment(K, {c * K, nullptr}, st);
+        launches += 4 * (int64_t)K;
+      }
     }
   }
   // gradient: C-sensitivity per node, per finest cell, restricted to the level

@@ -185,3 +185,37 @@ def test_jacobians_without_layer_equal_second_order_jacobians(mg):
     g1 = mg.jacobian_T_apply_pml(mesh, 1, _dev(eps), sh, _dev(s), dt, W).cpu().numpy()
     g2 = mg.jacobian_T_apply(mesh, 1, _dev(eps), sh, _dev(s), dt, W).cpu().numpy()
     assert rel_l2(g1, g2) < JAC_TOL
+
+
+def test_graph_chunks_give_the_same_bits(mg):
+    """The PML drivers replay whole chunks of steps as CUDA graphs (the step
+    index and the state slots read from a device base the graph moves):
+    forward, J v and J^T w (checkpoint spacings with a shorter last
+    segment, and the single kept segment) carry the bits of plain launches
+    (MG_NO_GRAPH), with chunks that leave remainders."""
+    import torch
+    from paper_1707_04605_gb300 import _lib as L
+
+    m, eps, dt, s, sh = _square_case()
+    xi, zeta = mixed.square_layer(m.coords, m.cells, 0.7, 1.0, 5.0)
+    w = configs.Workload("square_pml", m, eps, sh, 1.0, len(s), bc="neumann")
+    mesh = mg.mesh_from_workload(w)
+    rng = np.random.default_rng(21)
+    v = _dev(rng.standard_normal(m.n_cells[1]))
+    W = torch.as_tensor(rng.standard_normal((sh.n_traces, len(s))).astype(np.float32),
+                        device="cuda:0")
+    args = (_dev(eps), sh, _dev(s), dt)
+    lay = (_dev(xi), _dev(zeta))
+
+    def run(flags, ck):
+        return (mg.forward_pml(mesh, *args, *lay, flags=flags),
+                mg.jacobian_apply_pml(mesh, 1, *args, v, *lay, flags=flags),
+                mg.jacobian_T_apply_pml(mesh, 1, *args, W, *lay, ckpt_every=ck, flags=flags))
+
+    for chunk in (128, 16):
+        mesh.set_tuning(chunk=chunk)
+        for ck in (32, 7, len(s)):
+            ref = run(L.MG_NO_GRAPH, ck)
+            out = run(0, ck)
+            for a, b in zip(ref, out):
+                assert torch.equal(a, b), (chunk, ck)
