@@ -499,9 +499,11 @@ def pml_leg(mg, torch, mesh, w, eps_d, wav_d, dt, nt=1000, ckpt=1000):
             "algorithmic_bytes_per_forward_step": bytes_fwd,
             "forward_GB_per_s": bytes_fwd / (us["forward"] * 1e-6) / 1e9,
             "adjoint_vs_forward": secs["adjoint"] / secs["forward"],
-            "note": f"two launches per step (flux and node updates); the adjoint includes its "
-                    f"forward, which keeps every state (checkpoint spacing {ckpt} >= {nt} "
-                    f"steps: one segment, no recompute)"}
+            "graphs": mesh.tuning()["chunk"] >= 2,
+            "note": f"two launches per step (flux and node updates), whole chunks of "
+                    f"{mesh.tuning()['chunk']} steps replayed as CUDA graphs; the adjoint "
+                    f"includes its forward, which keeps every state (checkpoint spacing {ckpt} "
+                    f">= {nt} steps: one segment, no recompute)"}
 
 
 def batch_leg(mg, torch, dev, nt=4000, ckpt=256):
