@@ -103,6 +103,7 @@ def apply_tuning(mesh, spec):
         if "stream" in t:
             mesh.set_l1_streaming(t["stream"], kind)
         mesh.set_min_blocks(t.get("min_blocks", 0), kind)
+        mesh.set_late_prefetch(t.get("prefetch", 0), kind)
         if kind == "forward":
             mesh.set_row_sweep(t.get("sweep", 0))
             mesh.set_tma_tiles(t.get("tma", 0))
@@ -233,7 +234,8 @@ def shape_key(t):
     """The launch-shape fields of a kind's tuning that change its traffic."""
     return (t["batch"], t["tile_rows"], t.get("groups", 1), t.get("min_blocks", 0),
             t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0), t.get("stream", 0)) + (
-        (t["tma"],) if t.get("tma", 0) else ())
+        (t["tma"],) if t.get("tma", 0) else ()) + (
+        ("prefetch", t["prefetch"]) if t.get("prefetch", 0) else ())
 
 
 def sources_sha1():
@@ -302,33 +304,48 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
             best = ms if best is None else min(best, ms)
         return best
 
+    uniform = False
     if args is not None and args.tuning:
-        apply_tuning(mesh, {"forward": json.loads(args.tuning)})
+        t = json.loads(args.tuning)
+        apply_tuning(mesh, {"forward": t})
+        uniform = bool(t.get("uniform", 0))
+        mesh.set_uniform_ell(uniform)
     elif args is not None and (args.tile_rows != -1 or args.src_tile != -1 or args.lane_vec != -1):
         mesh.set_kernel_tuning("forward", args.lane_vec, args.tile_rows, args.src_tile)
         if args.min_blocks != -1:
             mesh.set_min_blocks(args.min_blocks)
     else:
         mesh.autotune(eps, w.shots, wav, dt, steps=32, level=1)
-        # register cap and row sweep of the chosen row shape, each timed as
-        # the best of three whole runs (the 32-step autotune windows do not
-        # always separate them)
+        # register cap, row sweep, prefetch of the late-loaded rows (and of
+        # the next swept block) and the uniformly strided stiffness for the
+        # chosen row shape, each timed as the best of three whole runs (the
+        # 32-step autotune windows do not always separate them)
         if mesh.tuning()["forward"]["tile_rows"] == 0 and mesh.tuning()["forward"]["tma"] == 0:
             best = None
-            for cap in (0, 5):
-                for sweep in (0, 4):
+            for uni in (False, True):
+                try:
+                    mesh.set_uniform_ell(uni)
+                except Exception:           # refused: padding would double K
+                    continue
+                for cap, sweep, pf in ((0, 0, 0), (0, 4, 0), (5, 0, 0), (5, 4, 0), (5, 4, 2),
+                                       (5, 4, 3)):
                     mesh.set_min_blocks(cap)
                     mesh.set_row_sweep(sweep)
+                    mesh.set_late_prefetch(pf, "forward")
                     mg.forward(mesh, eps, w.shots, wav, dt)
                     torch.cuda.synchronize()
                     ms = run_ms()
-                    if best is None or ms < best[2] * 0.99:
-                        best = (cap, sweep, ms)
-            mesh.set_min_blocks(best[0])
-            mesh.set_row_sweep(best[1])
+                    if best is None or ms < best[4] * 0.99:
+                        best = (uni, cap, sweep, pf, ms)
+            uniform = best[0]
+            mesh.set_uniform_ell(uniform)
+            mesh.set_min_blocks(best[1])
+            mesh.set_row_sweep(best[2])
+            mesh.set_late_prefetch(best[3], "forward")
     if args is not None and args.dep_launch != -1:
         mesh.set_dependent_launch(args.dep_launch)
     tuning = mesh.tuning()
+    tuning["forward"]["uniform"] = int(uniform)
     mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
     torch.cuda.synchronize()
     if args is not None and args.profile:
@@ -341,7 +358,7 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
     S_pad = 64
     bytes_step = 12.0 * n * S_pad + 8.0 * info["nnz"] + 16.0 * n
     peak, kind = peaks()
-    traffic = traffic_for("ellipsoid_3d forward", tuning["forward"])
+    traffic = traffic_for("ellipsoid_3d forward", tuning["forward"], uniform)
     mesh.close()
     return {"workload": f"ellipsoid_3d: {n} nodes, {w.mesh.cells.shape[0]} tets, {S} "
                         f"backscatter shots, {nt} of its 6000 steps timed (forward only; the "

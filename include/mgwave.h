@@ -351,6 +351,20 @@ int mg_mesh_set_row_sweep(mg_mesh* mesh, int blocks);
 /* The forward row sweep (>= 0), or MG_ERR_ARG for a null handle. */
 int mg_mesh_get_row_sweep(const mg_mesh* mesh);
 
+/* Prefetch of the late-loaded rows of the register-capped row kernels
+ * (mg_mesh_set_kernel_min_blocks) of a kernel kind (kind = -1: all kinds):
+ * level 1 (L1) or 2 (L2) makes each lane prefetch the lines of its row's
+ * own states and coefficients (p_{l-1}, and dp_{l-1} for the tangent;
+ * mu_{k+1} and p_k for the adjoint) before the gathers, so the loads after
+ * the gathers find them on chip without holding registers across the
+ * gather loop; 0: none.  Uncapped kernels are not affected.  Same results.
+ * Drops the cached graphs.  Errors: MG_ERR_ARG for other values. */
+int mg_mesh_set_late_prefetch(mg_mesh* mesh, int kind, int level);
+
+/* The prefetch levels of the forward, tangent and adjoint kinds into
+ * out[3].  Errors: MG_ERR_ARG for NULL arguments. */
+int mg_mesh_get_late_prefetch(const mg_mesh* mesh, int32_t* out);
+
 /* L1 policy of the row kernels of a kernel kind (kind = -1: all kinds):
  * 1 loads the data a step reads once (the row's own state values that are
  * not gathered, its coefficients and its stiffness entries) with

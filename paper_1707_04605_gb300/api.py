@@ -168,6 +168,14 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_tma_tiles(self.handle, int(rows)),
                 "mg_mesh_set_tma_tiles")
 
+    def set_late_prefetch(self, level: int, kind: str = None):
+        """Prefetch (0 none, 1 L1, 2 L2) of the rows the register-capped row
+        kernels load after their gathers (mg_mesh_set_late_prefetch); kind
+        None sets all kinds."""
+        k = -1 if kind is None else self.KINDS[kind]
+        L.check(self._lib.mg_mesh_set_late_prefetch(self.handle, k, int(level)),
+                "mg_mesh_set_late_prefetch")
+
     def set_row_sweep(self, blocks: int):
         """Consecutive row blocks per CTA of the forward row kernel
         (mg_mesh_set_row_sweep); 0 or 1: one."""
@@ -237,6 +245,10 @@ class Mesh:
         for name, k in self.KINDS.items():
             d[name]["ring"] = int(ring[k])
         d["forward"]["sweep"] = int(self._lib.mg_mesh_get_row_sweep(self.handle))
+        pf = (C.c_int32 * 3)()
+        L.check(self._lib.mg_mesh_get_late_prefetch(self.handle, pf), "mg_mesh_get_late_prefetch")
+        for k, kind in enumerate(("forward", "tangent", "adjoint")):
+            d[kind]["prefetch"] = int(pf[k])
         d["forward"]["tma"] = int(self._lib.mg_mesh_get_tma_tiles(self.handle))
         l1 = np.zeros(3, dtype=np.int32)
         L.check(self._lib.mg_mesh_get_l1_streaming(self.handle, C.c_void_p(l1.ctypes.data)),

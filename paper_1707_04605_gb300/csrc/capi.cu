@@ -121,6 +121,7 @@ struct mg_mesh {
     int sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
     int tma = 0;          // forward: rows per tile of the bulk-copy tiled kernel (0 = off)
     int stream = 0;       // row kernels: once-read loads bypass L1 allocation
+    int prefetch = 0;     // capped row kernels: prefetch of late-loaded rows (1 L1, 2 L2)
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
@@ -451,6 +452,7 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   b.ring = M->tune[0].ring;
   b.sweep = M->tune[0].sweep;
   b.stream = M->tune[0].stream;
+  b.prefetch = M->tune[0].prefetch;
   b.pdl = M->dep_launch;
   if (M->tune[0].tma) {
     const mg::DevTiles TT = tile_tables(M, M->tune[0].tma);
@@ -474,6 +476,7 @@ int do_tangent(mg_mesh* M, const mg::TangentArgs& a, int S_pad, cudaStream_t st)
   b.f.batch = M->tune[1].batch;
   b.f.ring = M->tune[1].ring;
   b.f.stream = M->tune[1].stream;
+  b.f.prefetch = M->tune[1].prefetch;
   b.f.min_blocks = M->tune[1].min_blocks;
   b.f.pdl = M->dep_launch;
   return mg::launch_tangent(b, S_pad, st);
@@ -486,6 +489,7 @@ int do_adjoint(mg_mesh* M, const mg::AdjointArgs& a, int S_pad, cudaStream_t st)
   b.batch = M->tune[2].batch;
   b.ring = M->tune[2].ring;
   b.stream = M->tune[2].stream;
+  b.prefetch = M->tune[2].prefetch;
   b.min_blocks = M->tune[2].min_blocks;
   b.pdl = M->dep_launch;
   return mg::launch_adjoint(b, S_pad, st);
@@ -1054,6 +1058,21 @@ int mg_mesh_set_row_sweep(mg_mesh* M, int blocks) {
 
 int mg_mesh_get_row_sweep(const mg_mesh* M) { return M ? M->tune[0].sweep : MG_ERR_ARG; }
 
+int mg_mesh_set_late_prefetch(mg_mesh* M, int kind, int level) {
+  if (!M || kind < -1 || kind > 2 || level < 0 || level > 3 || (level == 3 && kind != 0))
+    return MG_ERR_ARG;
+  drop_graphs(M);
+  for (int k = 0; k < 3; ++k)
+    if (kind == -1 || kind == k) M->tune[k].prefetch = level;
+  return MG_OK;
+}
+
+int mg_mesh_get_late_prefetch(const mg_mesh* M, int32_t* out) {
+  if (!M || !out) return MG_ERR_ARG;
+  for (int k = 0; k < 3; ++k) out[k] = M->tune[k].prefetch;
+  return MG_OK;
+}
+
 int mg_mesh_set_l1_streaming(mg_mesh* M, int kind, int on) {
   if (!M || kind < -1 || kind > 2 || (on != 0 && on != 1)) return MG_ERR_ARG;
   drop_graphs(M);
@@ -1430,6 +1449,7 @@ int mg_forward_jacobian_apply(mg_mesh* M, int level, const double* eps, const mg
   a.f.batch = M->tune[1].batch;
   a.f.ring = M->tune[1].ring;
   a.f.stream = M->tune[1].stream;
+  a.f.prefetch = M->tune[1].prefetch;
   a.f.min_blocks = M->tune[1].min_blocks;
   a.f.pdl = M->dep_launch;
   a.f.hint = keep ? M->cache_hints : 0;   // p_{l-1} is last read here only when kept
@@ -1592,6 +1612,7 @@ int mg_jacobian_T_apply(mg_mesh* M, int level, const double* eps, const mg_shots
   aa.batch = M->tune[2].batch;
   aa.ring = M->tune[2].ring;
   aa.stream = M->tune[2].stream;
+  aa.prefetch = M->tune[2].prefetch;
   aa.min_blocks = M->tune[2].min_blocks;
   aa.G = G;
   aa.Gc = G + acc;

@@ -50,6 +50,7 @@ struct StepArgs {
   int32_t ring = 0;         // row kernels: gather ring of 4 or 8 slots per lane (0 = plain loads)
   int32_t sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
   int32_t stream = 0;       // row kernels: once-read data loaded without L1 allocation
+  int32_t prefetch = 0;     // capped row kernels: prefetch of the late-loaded rows (0, 1 L1, 2 L2)
 };
 
 // Tangent step: forward and tangent states advance together.
@@ -86,6 +87,7 @@ struct AdjointArgs {
   int32_t ring = 0;         // row kernel: gather ring depth as in StepArgs
   int32_t stream = 0;       // row kernel: once-read loads without L1 allocation
   int32_t min_blocks = 0;   // row kernel: 0, or 5 or 6 resident CTAs per SM (register cap)
+  int32_t prefetch = 0;     // as in StepArgs
   float* G;                 // [tiles][n] sums; row kernels: set = absolute source tile
   float* Gc;                // compensations
   float* H;

@@ -397,6 +397,16 @@ __device__ __forceinline__ float4 ld_pinned(const float* p) {
   return v;
 }
 
+// Prefetch of the line holding p into L1 (level 1) or L2 (level 2): the
+// late loads of a capped kernel then find their rows on chip without
+// holding registers across the gathers.
+__device__ __forceinline__ void prefetch_to(const void* p, int level) {
+  if (level == 1)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+  else
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float2 ld_pinned2(const float2* p) {
   float2 v;
   asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
@@ -422,6 +432,14 @@ __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
   grid_dep_sync();
   const size_t ro = (size_t)row * a.ld + base;
   float4 c, old[NV], self[NV], acc[NV];
+  if constexpr (LATE) {
+    if (a.prefetch) {
+      const int lv = a.prefetch == 1 ? 1 : 2;
+      prefetch_to(a.coef + row, lv);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) prefetch_to(a.pm + ro + 4 * LPR * j, lv);
+    }
+  }
   if constexpr (!LATE) {
     c = ld_coef(a.coef + row, a.stream);
 #pragma unroll
@@ -464,6 +482,32 @@ __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
 // One row block per CTA, or (a.sweep > 1) a.sweep consecutive row blocks
 // per CTA, swept in order: the neighbour rows a block shares with the next
 // are then still in the SM's L1.
+// Prefetch level 3 of a swept CTA: before advancing block `blk`, each
+// thread prefetches into L2 what its row of block blk + 1 reads first: its
+// p_l and p_{l-1} segments, its coefficients and (uniformly strided
+// stiffness) its first two chunks of entries.  Addresses only: no load, no
+// register held.
+template <int LPR, int NV>
+__device__ __forceinline__ void prefetch_next_block(const StepArgs& a, int blk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = ((blk + 1) * kWarps + warp) * (32 / LPR) + lane / LPR;
+  if (row >= a.K.n) return;
+  const int lr = lane % LPR;
+  const size_t ro = (size_t)row * a.ld + a.col0 + blockIdx.y * 4 * LPR * NV + 4 * lr;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    prefetch_to(a.p + ro + 4 * LPR * j, 2);
+    prefetch_to(a.pm + ro + 4 * LPR * j, 2);
+  }
+  if (lr == 0) prefetch_to(a.coef + row, 2);
+  if (a.K.ellu) {
+    const int s = row / kSliceH;
+    const int2* e = a.K.ellu + (size_t)s * a.K.wu * kSliceH + (row - s * kSliceH);
+    if (lr < a.K.wu) prefetch_to(e + (size_t)lr * kSliceH, 2);
+    if (lr + LPR < a.K.wu) prefetch_to(e + (size_t)(lr + LPR) * kSliceH, 2);
+  }
+}
+
 template <int LPR, int NV, int MINB, int R>
 __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   constexpr bool kLate = MINB > 1;   // the register-capped form loads late
@@ -474,7 +518,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
   constexpr int RPB = kWarps * 32 / LPR;
   const int nblk = (a.K.n + RPB - 1) / RPB;
   const int b0 = blockIdx.x * a.sweep, b1 = min(b0 + a.sweep, nblk);
-  for (int b = b0; b < b1; ++b) step_rows_block<LPR, NV, R, kLate>(a, b);
+  for (int b = b0; b < b1; ++b) {
+    if constexpr (kLate)
+      if (a.prefetch == 3 && b + 1 < b1) prefetch_next_block<LPR, NV>(a, b);
+    step_rows_block<LPR, NV, R, kLate>(a, b);
+  }
 }
 
 // The forward + tangent step of row block `blk`.  LATE as in
@@ -497,6 +545,17 @@ __device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk
   const size_t ro = (size_t)row * ld + base;
   float4 c, pold[NV], qold[NV], ps[NV], qs[NV], pacc[NV], qacc[NV];
   float2 tc;
+  if constexpr (LATE) {
+    if (a.f.prefetch) {
+      prefetch_to(a.f.coef + row, a.f.prefetch);
+      prefetch_to(a.tcoef + row, a.f.prefetch);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        prefetch_to(a.f.pm + ro + 4 * LPR * j, a.f.prefetch);
+        prefetch_to(a.qm + ro + 4 * LPR * j, a.f.prefetch);
+      }
+    }
+  }
   if constexpr (!LATE) {
     c = ld_coef(a.f.coef + row, a.f.stream);
     tc = ld_coef(a.tcoef + row, a.f.stream);
@@ -648,6 +707,16 @@ __device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk
     }
     const size_t ro = (size_t)row * a.ld + base;
     float4 c, old[NV], pk[NV], self[NV], acc[NV];
+    if constexpr (LATE) {
+      if (a.prefetch) {
+        prefetch_to(a.coef + row, a.prefetch);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+          prefetch_to(a.mu1 + ro + 4 * LPR * j, a.prefetch);
+          prefetch_to(a.pk + ro + 4 * LPR * j, a.prefetch);
+        }
+      }
+    }
     if constexpr (!LATE) {
       c = ld_coef(a.coef + row, a.stream);
 #pragma unroll

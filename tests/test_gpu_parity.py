@@ -401,6 +401,18 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     out = run()
     assert torch.equal(ref[0], out[0])
     assert torch.equal(ref[1], out[1])
+    mesh.set_l1_streaming(False, "forward")
+    # prefetch of the late-loaded rows (L1, L2, and the next swept block's
+    # rows and entries), with the sliced and the uniformly strided stiffness
+    for uniform in (False, True):
+        mesh.set_uniform_ell(uniform)
+        for pf in (1, 2, 3):
+            mesh.set_late_prefetch(pf, "forward")
+            assert mesh.tuning()["forward"]["prefetch"] == pf
+            out = run()
+            assert torch.equal(ref[0], out[0])
+            assert torch.equal(ref[1], out[1])
+    mesh.set_late_prefetch(0, "forward")
     # the tangent's register cap: the lockstep and fused passes keep their bits
     v = _dev(np.random.default_rng(16).standard_normal(w.mesh.n_cells[1]))
     jv = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
@@ -414,8 +426,12 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
     # the adjoint's register caps, from checkpoints and on the kept history
     g_kept = mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
                                  reuse_checkpoints=True)
+    mesh.set_late_prefetch(2, "tangent")
+    yc, jvc = mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
+    assert torch.equal(yc, yf) and torch.equal(jvc, jvf)
     for cap in (5, 6):
         mesh.set_min_blocks(cap, "adjoint")
+        mesh.set_late_prefetch(cap - 4, "adjoint")   # L1, then L2
         assert mesh.tuning()["adjoint"]["min_blocks"] == cap
         mg.forward_jacobian_apply(mesh, 1, eps, w.shots, s, dt, v, keep_states=True)
         assert torch.equal(mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=w.nt,
