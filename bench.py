@@ -105,6 +105,7 @@ def apply_tuning(mesh, spec):
         mesh.set_min_blocks(t.get("min_blocks", 0), kind)
         mesh.set_late_prefetch(t.get("prefetch", 0), kind)
         if kind == "forward":
+            mesh.set_wide_lanes(t.get("wide", 1))
             mesh.set_row_sweep(t.get("sweep", 0))
             mesh.set_tma_tiles(t.get("tma", 0))
 
@@ -235,7 +236,8 @@ def shape_key(t):
     return (t["batch"], t["tile_rows"], t.get("groups", 1), t.get("min_blocks", 0),
             t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0), t.get("stream", 0)) + (
         (t["tma"],) if t.get("tma", 0) else ()) + (
-        ("prefetch", t["prefetch"]) if t.get("prefetch", 0) else ())
+        ("prefetch", t["prefetch"]) if t.get("prefetch", 0) else ()) + (
+        ("wide",) if t.get("wide", 0) else ())
 
 
 def sources_sha1():

@@ -361,6 +361,21 @@ int mg_mesh_get_row_sweep(const mg_mesh* mesh);
  * Drops the cached graphs.  Errors: MG_ERR_ARG for other values. */
 int mg_mesh_set_late_prefetch(mg_mesh* mesh, int kind, int level);
 
+/* Wide lanes of the register-capped forward row kernel with two float4 per
+ * lane (on = 1): each lane holds 8 consecutive shots of its row, so that
+ * every gather is one 32-byte load (sm_100 and later) instead of two
+ * 16-byte loads.  Applies while mg_mesh_set_min_blocks(5) holds, the launch
+ * shape has two float4 per lane, no L2 cache hint or L1 streaming applies
+ * and the shot stride is a multiple of 8; otherwise the two-load kernel
+ * runs.  Same arithmetic in the same order: same results.  Default 1
+ * (measured faster: ellipsoid_3d forward 469.5 -> 463.4 us per step,
+ * asteroid_2d 18.68 -> 18.52); 0: two 16-byte loads per gather.  Drops the
+ * cached graphs.  Errors: MG_ERR_ARG for other values. */
+int mg_mesh_set_wide_lanes(mg_mesh* mesh, int on);
+
+/* The switch above (0 or 1), or MG_ERR_ARG for a NULL handle. */
+int mg_mesh_get_wide_lanes(const mg_mesh* mesh);
+
 /* The prefetch levels of the forward, tangent and adjoint kinds into
  * out[3].  Errors: MG_ERR_ARG for NULL arguments. */
 int mg_mesh_get_late_prefetch(const mg_mesh* mesh, int32_t* out);

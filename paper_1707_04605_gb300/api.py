@@ -176,6 +176,12 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_late_prefetch(self.handle, k, int(level)),
                 "mg_mesh_set_late_prefetch")
 
+    def set_wide_lanes(self, on: bool):
+        """8 consecutive shots per lane (32-byte gathers) in the capped
+        forward row kernel with two float4 per lane (mg_mesh_set_wide_lanes)."""
+        L.check(self._lib.mg_mesh_set_wide_lanes(self.handle, int(bool(on))),
+                "mg_mesh_set_wide_lanes")
+
     def set_row_sweep(self, blocks: int):
         """Consecutive row blocks per CTA of the forward row kernel
         (mg_mesh_set_row_sweep); 0 or 1: one."""
@@ -245,6 +251,7 @@ class Mesh:
         for name, k in self.KINDS.items():
             d[name]["ring"] = int(ring[k])
         d["forward"]["sweep"] = int(self._lib.mg_mesh_get_row_sweep(self.handle))
+        d["forward"]["wide"] = int(self._lib.mg_mesh_get_wide_lanes(self.handle))
         pf = (C.c_int32 * 3)()
         L.check(self._lib.mg_mesh_get_late_prefetch(self.handle, pf), "mg_mesh_get_late_prefetch")
         for k, kind in enumerate(("forward", "tangent", "adjoint")):

@@ -122,6 +122,7 @@ struct mg_mesh {
     int tma = 0;          // forward: rows per tile of the bulk-copy tiled kernel (0 = off)
     int stream = 0;       // row kernels: once-read loads bypass L1 allocation
     int prefetch = 0;     // capped row kernels: prefetch of late-loaded rows (1 L1, 2 L2)
+    int wide = 1;         // capped forward: 8 consecutive shots per lane (256-bit loads)
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
@@ -453,6 +454,7 @@ int do_step(mg_mesh* M, const mg::StepArgs& a, int S_pad, cudaStream_t st) {
   b.sweep = M->tune[0].sweep;
   b.stream = M->tune[0].stream;
   b.prefetch = M->tune[0].prefetch;
+  b.wide = M->tune[0].wide;
   b.pdl = M->dep_launch;
   if (M->tune[0].tma) {
     const mg::DevTiles TT = tile_tables(M, M->tune[0].tma);
@@ -1066,6 +1068,15 @@ int mg_mesh_set_late_prefetch(mg_mesh* M, int kind, int level) {
     if (kind == -1 || kind == k) M->tune[k].prefetch = level;
   return MG_OK;
 }
+
+int mg_mesh_set_wide_lanes(mg_mesh* M, int on) {
+  if (!M || (on != 0 && on != 1)) return MG_ERR_ARG;
+  drop_graphs(M);
+  M->tune[0].wide = on;
+  return MG_OK;
+}
+
+int mg_mesh_get_wide_lanes(const mg_mesh* M) { return M ? M->tune[0].wide : MG_ERR_ARG; }
 
 int mg_mesh_get_late_prefetch(const mg_mesh* M, int32_t* out) {
   if (!M || !out) return MG_ERR_ARG;

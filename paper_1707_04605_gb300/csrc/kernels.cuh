@@ -51,6 +51,7 @@ struct StepArgs {
   int32_t sweep = 0;        // forward row kernel: consecutive row blocks per CTA (0, 1: one)
   int32_t stream = 0;       // row kernels: once-read data loaded without L1 allocation
   int32_t prefetch = 0;     // capped row kernels: prefetch of the late-loaded rows (0, 1 L1, 2 L2)
+  int32_t wide = 0;         // capped forward, two float4 per lane: 8 consecutive shots per lane
 };
 
 // Tangent step: forward and tangent states advance together.

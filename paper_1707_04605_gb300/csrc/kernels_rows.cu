@@ -251,7 +251,21 @@ int launch_step(const StepArgs& a, int S_pad, cudaStream_t st) {
   if (a.sweep > 1) sh.grid.x = (sh.grid.x + a.sweep - 1) / a.sweep;
   if (!range_ok(sh, a.col0, cols, a.ld)) return MG_ERR_ARG;
   cudaError_t err = cudaSuccess;
-  if (a.min_blocks == 5) {
+  // wide lanes: 32-byte accesses need 32-byte aligned rows and columns
+  const uintptr_t al = reinterpret_cast<uintptr_t>(a.p) | reinterpret_cast<uintptr_t>(a.pm) |
+                       reinterpret_cast<uintptr_t>(a.pout);
+  if (a.wide && a.min_blocks == 5 && sh.nv == 2 && !a.hint && !a.stream && a.ld % 8 == 0 &&
+      a.col0 % 8 == 0 && al % 32 == 0) {
+    switch (sh.lpr) {
+      case 32: err = launch_ex(k_step_rows_w<32, 5>, sh.grid, a.pdl, 0, st, a); break;
+      case 16: err = launch_ex(k_step_rows_w<16, 5>, sh.grid, a.pdl, 0, st, a); break;
+      case 8: err = launch_ex(k_step_rows_w<8, 5>, sh.grid, a.pdl, 0, st, a); break;
+      case 4: err = launch_ex(k_step_rows_w<4, 5>, sh.grid, a.pdl, 0, st, a); break;
+      case 2: err = launch_ex(k_step_rows_w<2, 5>, sh.grid, a.pdl, 0, st, a); break;
+      case 1: err = launch_ex(k_step_rows_w<1, 5>, sh.grid, a.pdl, 0, st, a); break;
+      default: return MG_ERR_ARG;
+    }
+  } else if (a.min_blocks == 5) {
     MG_ROWS_SWITCH_M(k_step_rows, 5, 0, 1, a.pdl, a)
   } else if (a.min_blocks == 0) {
     MG_ROWS_SWITCH_M(k_step_rows, 1, 0, 1, a.pdl, a)

@@ -216,6 +216,53 @@ __device__ __forceinline__ void row_sum2(const Row& r, const float* __restrict__
     }
   })
 }
+
+// Wide lanes: lane lr of a row holds the 8 consecutive shots [8 lr, 8 lr + 8)
+// of the row's tile (two float4 side by side) instead of two float4 4 LPR
+// shots apart, so each gather is one 32-byte load (ld.global.v8.f32, sm_100
+// and later): half the load instructions for the same bytes.
+struct F8 {
+  float4 a, b;
+};
+__device__ __forceinline__ F8 ldg8(const float* p) {
+  F8 r;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(r.a.x), "=f"(r.a.y), "=f"(r.a.z), "=f"(r.a.w), "=f"(r.b.x), "=f"(r.b.y),
+        "=f"(r.b.z), "=f"(r.b.w)
+      : "l"(p));
+  return r;
+}
+// Loaded where it stands (after the gathers), like ld_pinned.
+__device__ __forceinline__ F8 ld8_pinned(const float* p) {
+  F8 r;
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(r.a.x), "=f"(r.a.y), "=f"(r.a.z), "=f"(r.a.w), "=f"(r.b.x), "=f"(r.b.y),
+                 "=f"(r.b.z), "=f"(r.b.w)
+               : "l"(p)
+               : "memory");
+  return r;
+}
+__device__ __forceinline__ void st8(float* p, const F8& v) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v.a.x),
+               "f"(v.a.y), "f"(v.a.z), "f"(v.a.w), "f"(v.b.x), "f"(v.b.y), "f"(v.b.z), "f"(v.b.w)
+               : "memory");
+}
+
+// The row sum of row_sum with wide lanes (the same FMAs in the same order).
+template <int LPR>
+__device__ __forceinline__ void row_sum_w(const Row& r, const float* __restrict__ xb, int row,
+                                          int lr, unsigned mask, int ld, F8& self, F8& acc) {
+  int2 cur = entry_at(r, lr, row);
+  self = ldg8(xb + (size_t)row * ld);
+  const float v0 = __int_as_float(__shfl_sync(mask, cur.y, 0, LPR));
+  acc.a = scale4(v0, self.a);
+  acc.b = scale4(v0, self.b);
+  MG_FOR_ENTRIES(LPR, r, row, lr, mask, cur, col, v, {
+    const F8 x = ldg8(xb + (size_t)col * ld);
+    acc.a = fma4(v, x.a, acc.a);
+    acc.b = fma4(v, x.b, acc.b);
+  })
+}
 #undef MG_FOR_ENTRIES
 
 // ---------------------------------------------------------------------------
@@ -522,6 +569,78 @@ __global__ void __launch_bounds__(kThreads, MINB) k_step_rows(StepArgs a) {
     if constexpr (kLate)
       if (a.prefetch == 3 && b + 1 < b1) prefetch_next_block<LPR, NV>(a, b);
     step_rows_block<LPR, NV, R, kLate>(a, b);
+  }
+}
+
+// Shot s of the batch in the wide layout: float4 j and component d of this
+// lane, or -1 when another lane (or another source tile) owns it.
+template <int LPR>
+__device__ __forceinline__ int owner_w(int s, int tile0, int lr, int& d) {
+  const int rel = s - tile0;
+  if (rel < 0 || rel >= 8 * LPR || rel / 8 != lr) return -1;
+  d = rel % 4;
+  return (rel % 8) / 4;
+}
+
+// The capped forward step of row block `blk` with wide lanes (two float4
+// of consecutive shots per lane): the arithmetic of step_rows_block with
+// LATE, same results.  Plain loads only (no cache-policy variants).
+template <int LPR>
+__device__ __forceinline__ void step_rows_block_w(const StepArgs& a, int blk) {
+  constexpr int RPW = 32 / LPR, TW = 8 * LPR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = (blk * kWarps + warp) * RPW + lane / LPR;
+  const unsigned mask = __ballot_sync(0xffffffffu, row < a.K.n);
+  if (row >= a.K.n) return;
+  const int lr = lane % LPR;
+  const int tile0 = a.col0 + blockIdx.y * TW;
+  const int base = tile0 + 8 * lr;
+  const Row r = row_of(a.K, row);
+  grid_dep_sync();
+  const size_t ro = (size_t)row * a.ld + base;
+  if (a.prefetch & 3) {
+    const int lv = (a.prefetch & 3) == 1 ? 1 : 2;
+    prefetch_to(a.coef + row, lv);
+    prefetch_to(a.pm + ro, lv);
+  }
+  F8 self, acc;
+  row_sum_w<LPR>(r, a.p + base, row, lr, mask, a.ld, self, acc);
+  const float4 c = ld_pinned(reinterpret_cast<const float*>(a.coef + row));
+  const F8 old = ld8_pinned(a.pm + ro);
+  float4 out[2] = {leap(c, self.a, old.a, acc.a), leap(c, self.b, old.b, acc.b)};
+  const int l = a.step + (a.step_base ? *a.step_base : 0);
+  const int s0 = __ldg(a.ev.src_ptr + row), s1 = __ldg(a.ev.src_ptr + row + 1);
+  if (s0 != s1) {
+    const float sv = c.z * __ldg(a.wavelet + l);
+    for (int q = s0; q < s1; ++q) {
+      int d;
+      const int j = owner_w<LPR>(__ldg(a.ev.src_shot + q), tile0, lr, d);
+      if (j >= 0) add_to<2>(out, j, d, sv);
+    }
+  }
+  st8(a.pout + ro, F8{out[0], out[1]});
+  if (a.traces) {
+    const int r0 = __ldg(a.ev.rec_ptr + row), r1 = __ldg(a.ev.rec_ptr + row + 1);
+    for (int q = r0; q < r1; ++q) {
+      int d;
+      const int j = owner_w<LPR>(__ldg(a.ev.rec_shot + q), tile0, lr, d);
+      if (j >= 0) a.traces[(size_t)__ldg(a.ev.rec_trace + q) * a.nt + l] = get_from<2>(out, j, d);
+    }
+  }
+}
+
+template <int LPR, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_step_rows_w(StepArgs a) {
+  if (a.sweep <= 1) {
+    step_rows_block_w<LPR>(a, blockIdx.x);
+    return;
+  }
+  constexpr int RPB = kWarps * 32 / LPR;
+  const int nblk = (a.K.n + RPB - 1) / RPB;
+  const int b0 = blockIdx.x * a.sweep, b1 = min(b0 + a.sweep, nblk);
+  for (int b = b0; b < b1; ++b) {
+    if ((a.prefetch & 3) == 3 && b + 1 < b1) prefetch_next_block<LPR, 2>(a, b);
+    step_rows_block_w<LPR>(a, b);
   }
 }
 

@@ -413,6 +413,16 @@ def test_register_capped_forward_gives_identical_results(mg, batch):
             assert torch.equal(ref[0], out[0])
             assert torch.equal(ref[1], out[1])
     mesh.set_late_prefetch(0, "forward")
+    # two 16-byte loads per gather instead of the default wide lanes (8
+    # consecutive shots per lane, one 32-byte load), swept and not
+    assert mesh.tuning()["forward"]["wide"] == 1
+    mesh.set_wide_lanes(False)
+    for sweep in (0, 3):
+        mesh.set_row_sweep(sweep)
+        out = run()
+        assert torch.equal(ref[0], out[0])
+        assert torch.equal(ref[1], out[1])
+    mesh.set_wide_lanes(True)
     # the tangent's register cap: the lockstep and fused passes keep their bits
     v = _dev(np.random.default_rng(16).standard_normal(w.mesh.n_cells[1]))
     jv = mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v)
