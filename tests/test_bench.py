@@ -21,8 +21,10 @@ def test_roofline_fractions(bench):
     assert math.isclose(r["dram_frac"], 0.25)
     assert math.isclose(r["traffic_ratio"], 0.5)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    r = bench.roofline("k", 2e9, 1e-3, None, 4000.0, "of measured", "x", "y")
+    r = bench.roofline("k", 2e9, 1e-3, None, 4000.0, "of measured", "x", "y",
+                       bound=bench.L2_BOUND)
     assert r["traffic"] is None and r["dram_frac"] is None and r["traffic_ratio"] is None
+    assert r["bound"] == bench.L2_BOUND and r["denominator"] == "hbm"
 
 
 def test_shape_key_tells_launch_shapes_apart(bench):
