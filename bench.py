@@ -216,18 +216,20 @@ TRAFFIC = {
     # and profiles/forward_ellipsoid_3d_s64.md.
     # k_tangent_rows<16, 1, 5, 0>, fused forward + tangent writing the kept
     # history, register cap, two shot groups of 64 columns: 10.5 MB read +
-    # 24.5 MB written per launch, two launches per step
-    ("asteroid_2d fused", (1, 0, 2, 5, 0, 0, 0, 0), True): (70.0e6, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
+    # 24.4 MB written per launch, two launches per step
+    ("asteroid_2d fused", (1, 0, 2, 5, 0, 0, 0, 0), True): (69.9e6, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
     # k_adjoint_rows<16, 2, 5, 0>, reverse step on the kept history, register
-    # cap, one launch of 128 columns: 36.5 MB read + 20.9 MB written
-    ("asteroid_2d reverse", (2, 0, 1, 5, 0, 0, 0, 0), True): (57.5e6, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
+    # cap, one launch of 128 columns: 36.8 MB read + 21.1 MB written
+    ("asteroid_2d reverse", (2, 0, 1, 5, 0, 0, 0, 0), True): (57.9e6, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
     # k_tangent_rows<16, 1, 5, 0>, lockstep forward + tangent (J v of the
-    # checkpointed step), register cap, two shot groups: 9.6 MB read +
-    # 15.3 MB written per launch
-    ("asteroid_2d tangent", (1, 0, 2, 5, 0, 0, 0, 0), True): (49.7e6, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
-    # k_step_rows<8, 2, 5, 0>, register cap, 4 row blocks per CTA: 1228.3 MB
-    # read + 465.8 MB written per launch
-    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4, 0), False): (1.6941e9, "39b1a6a1254c945c54786d1d8a2d77c1b5a41483"),
+    # checkpointed step), register cap, two shot groups: 9.4 MB read +
+    # 15.1 MB written per launch
+    ("asteroid_2d tangent", (1, 0, 2, 5, 0, 0, 0, 0), True): (49.0e6, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
+    # k_step_rows_w<8, 5>, wide lanes, register cap, 4 row blocks per CTA,
+    # prefetch level 3, uniformly strided stiffness: 1244.8 MB read + 465.7 MB
+    # written per launch
+    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4, 0, "prefetch", 3, "wide"), True):
+        (1.7105e9, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
 }
 
 
