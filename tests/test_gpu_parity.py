@@ -370,8 +370,10 @@ def test_wide_batch_row_shapes_cover_every_shot(mg):
 @pytest.mark.parametrize("batch", [1, 2, 4])
 def test_register_capped_forward_gives_identical_results(mg, batch):
     """mg_mesh_set_min_blocks(5) only changes register allocation,
-    mg_mesh_set_row_sweep only which CTA advances which rows, and
-    mg_mesh_set_l1_streaming only cache policy: same bits."""
+    mg_mesh_set_row_sweep only which CTA advances which rows,
+    mg_mesh_set_l1_streaming and mg_mesh_set_late_prefetch only cache
+    policy, mg_mesh_set_wide_lanes only which lane holds which shots: same
+    bits."""
     w = configs.asteroid_2d(n_refine=1, S=100, nt=300)
     eps = _dev(w.eps)
     mesh = mg.mesh_from_workload(w)
@@ -862,3 +864,29 @@ def test_persistent_fused_pass_and_reverse_steps_give_the_graph_bits(mg, nt, gro
         mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64,
                             reuse_checkpoints=True, persistent=True)
     assert e.value.code == L.MG_ERR_UNSUPPORTED
+
+
+def test_tuning_setters_reject_values_they_do_not_take(mg):
+    """Register caps, prefetch levels and wide lanes outside their ranges
+    are refused with MG_ERR_ARG and leave the tuning unchanged."""
+    from paper_1707_04605_gb300 import _lib as L
+
+    w = configs.tiny_2d()
+    mesh = mg.mesh_from_workload(w)
+    lib = L.load()
+    before = mesh.tuning()
+    K = mesh.KINDS
+    for rc in (lib.mg_mesh_set_kernel_min_blocks(mesh.handle, K["forward"], 6),
+               lib.mg_mesh_set_kernel_min_blocks(mesh.handle, K["tangent"], 6),
+               lib.mg_mesh_set_kernel_min_blocks(mesh.handle, K["adjoint"], 7),
+               lib.mg_mesh_set_kernel_min_blocks(mesh.handle, 3, 5),
+               lib.mg_mesh_set_late_prefetch(mesh.handle, K["tangent"], 3),
+               lib.mg_mesh_set_late_prefetch(mesh.handle, -1, 3),
+               lib.mg_mesh_set_late_prefetch(mesh.handle, K["forward"], 4),
+               lib.mg_mesh_set_wide_lanes(mesh.handle, 2),
+               lib.mg_mesh_set_wide_lanes(None, 1)):
+        assert rc == L.MG_ERR_ARG
+    assert mesh.tuning() == before
+    assert lib.mg_mesh_set_late_prefetch(mesh.handle, K["forward"], 3) == L.MG_OK
+    assert lib.mg_mesh_set_kernel_min_blocks(mesh.handle, K["adjoint"], 6) == L.MG_OK
+    mesh.close()
