@@ -79,6 +79,9 @@ def parse():
                          "(instead of timing 1, 2, 4)")
     ap.add_argument("--uniform-ell", type=int, default=-1,
                     help="uniformly strided stiffness copy for the row kernels (0 or 1)")
+    ap.add_argument("--chunked-ell", type=int, default=-1,
+                    help="chunk-major stiffness copy: -1 for the lanes per row of the "
+                         "dominant kernel, 0 off, or a chunk (2..32)")
     ap.add_argument("--cache-hints", type=int, default=-1,
                     help="kept history: L2 evict-first on the last reads (0 or 1)")
     ap.add_argument("--hbm-only", action="store_true",
@@ -239,7 +242,8 @@ def shape_key(t):
             t.get("bulk", 0), t.get("ring", 0), t.get("sweep", 0), t.get("stream", 0)) + (
         (t["tma"],) if t.get("tma", 0) else ()) + (
         ("prefetch", t["prefetch"]) if t.get("prefetch", 0) else ()) + (
-        ("wide",) if t.get("wide", 0) else ())
+        ("wide",) if t.get("wide", 0) else ()) + (
+        ("ellc", t["ellc"]) if t.get("ellc", 0) else ())
 
 
 def sources_sha1():
@@ -252,6 +256,43 @@ def sources_sha1():
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def lanes_per_row(cols, nv):
+    """Lanes per row of a row-kernel launch over `cols` shot columns with
+    `nv` float4 per lane (the library's rule for its launch shapes)."""
+    while True:
+        lpr = min(32, cols // (4 * nv))
+        if nv == 1 or (lpr >= 1 and lpr & (lpr - 1) == 0 and cols % (4 * nv * lpr) == 0):
+            return lpr
+        nv >>= 1
+
+
+def set_chunked(mesh, tuning, cols, arg, kind):
+    """Chunk-major stiffness entries for the lanes per row of `kind`'s row
+    kernel (arg -1), of `arg` lanes (> 0) or none (0); records in every
+    kind's tuning the chunk its launches use (ellc, 0 when they use the
+    column layout)."""
+    t = tuning[kind]
+    chunk = arg
+    if arg == -1:
+        chunk = 0
+        if t["tile_rows"] == 0:
+            lpr = lanes_per_row(cols // t.get("groups", 1), t["batch"])
+            chunk = lpr if lpr >= 2 and lpr & (lpr - 1) == 0 else 0
+    mesh.set_chunked_ell(chunk)
+    mark_chunk(tuning, cols, chunk)
+    return chunk
+
+
+def mark_chunk(tuning, cols, chunk):
+    """Records in each kind's tuning (a dict of Mesh.tuning()'s shape, or
+    one kind's dict) the entry chunk its row-kernel launches use."""
+    kinds = [tuning[k] for k in ("forward", "tangent", "adjoint") if k in tuning] \
+        if "forward" in tuning else [tuning]
+    for tk in kinds:
+        lpr = lanes_per_row(cols // tk.get("groups", 1), tk["batch"])
+        tk["ellc"] = chunk if chunk and tk["tile_rows"] == 0 and lpr == chunk else 0
 
 
 def traffic_for(kernel, tuning, uniform=False):
@@ -358,6 +399,11 @@ def hbm_leg(mg, torch, dev, nt=300, args=None):
         mesh.set_dependent_launch(args.dep_launch)
     tuning = mesh.tuning()
     tuning["forward"]["uniform"] = int(uniform)
+    # chunk-major stiffness entries for the forward's lanes per row
+    ch_arg = -1 if args is None else args.chunked_ell
+    if args is not None and args.tuning and ch_arg == -1:
+        ch_arg = int(json.loads(args.tuning).get("ellc", -1))
+    set_chunked(mesh, tuning, 64, ch_arg, "forward")
     mg.forward(mesh, eps, w.shots, wav, dt)            # warm-up (graphs, buffers)
     torch.cuda.synchronize()
     if args is not None and args.profile:
@@ -846,6 +892,10 @@ def main():
     elif keep_states and not args.no_autotune:
         kept_groups = tune_kept(mg, torch, mesh, w, eps_d, wav_d, dt, v_d, LEVEL)
     tuning_kept = mesh.tuning()
+    # chunk-major stiffness entries for the lanes per row of the kernel that
+    # dominates the step (the tangent of the fused pass or of J v)
+    chunk = set_chunked(mesh, tuning_kept, S_pad, args.chunked_ell, "tangent")
+    mark_chunk(tuning, S_pad, chunk)
     adjoint_mode = (f"every forward state kept in HBM ({states_bytes / 1e9:.1f} GB): J^T w "
                     "without recompute, J v in the forward pass" if keep_states else
                     f"checkpoints every {CKPT} steps, recompute per segment")
@@ -1082,7 +1132,8 @@ def main():
         "config": {"workload": describe(w, layout), "nodes": n, "shots": S, "nt": nt,
                    "parallelism": f"shots: one 128-shot batch per GPU x {ws}",
                    "tuning": tuning_kept, "adjoint": adjoint_mode, "kept_groups": kept_groups,
-                   "stiffness": "uniformly strided ELL" if uniform else "sliced ELL",
+                   "stiffness": ("uniformly strided ELL" if uniform else "sliced ELL") + (
+                       f", chunk-major copy for {chunk} lanes per row" if chunk else ""),
                    "l2": "flushed between timed steps (256 MB write)"},
         "phases_ms": phases,
         "forward_updates_per_s": fwd_rate,

@@ -376,6 +376,18 @@ int mg_mesh_set_wide_lanes(mg_mesh* mesh, int on);
 /* The switch above (0 or 1), or MG_ERR_ARG for a NULL handle. */
 int mg_mesh_get_wide_lanes(const mg_mesh* mesh);
 
+/* Chunk-major copy of the stiffness entries for the wide-lane forward with
+ * `chunk` lanes per row (2, 4, 8, 16 or 32; 0: off): entry k of row r of
+ * slice s at s * stride + ((k / chunk) * 32 + r) * chunk + k % chunk, so a
+ * warp's load of one chunk of entries for its rows reads consecutive
+ * entries instead of one 32-entry column per lane.  Built on the device
+ * from the handle's entries (host time and ceil(w_max / chunk) * 32 * chunk
+ * * 8 bytes per slice of device memory); used by the wide-lane forward when
+ * its launch shape has `chunk` lanes per row, ignored otherwise.  Same
+ * results.  Drops the cached graphs.  Errors: MG_ERR_ARG for other values,
+ * MG_ERR_OOM, MG_ERR_CUDA. */
+int mg_mesh_set_chunked_ell(mg_mesh* mesh, int chunk);
+
 /* The prefetch levels of the forward, tangent and adjoint kinds into
  * out[3].  Errors: MG_ERR_ARG for NULL arguments. */
 int mg_mesh_get_late_prefetch(const mg_mesh* mesh, int32_t* out);

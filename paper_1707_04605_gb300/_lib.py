@@ -96,6 +96,7 @@ SIGNATURES = {
     "mg_mesh_set_late_prefetch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mg_mesh_set_wide_lanes": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_get_wide_lanes": (C.c_int, [C.c_void_p]),
+    "mg_mesh_set_chunked_ell": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_get_late_prefetch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mg_mesh_set_tma_tiles": (C.c_int, [C.c_void_p, C.c_int]),
     "mg_mesh_set_l1_streaming": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),

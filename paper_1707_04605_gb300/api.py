@@ -182,6 +182,12 @@ class Mesh:
         L.check(self._lib.mg_mesh_set_wide_lanes(self.handle, int(bool(on))),
                 "mg_mesh_set_wide_lanes")
 
+    def set_chunked_ell(self, chunk: int):
+        """Chunk-major copy of the stiffness entries for the wide-lane forward
+        with `chunk` lanes per row (mg_mesh_set_chunked_ell); 0: off."""
+        L.check(self._lib.mg_mesh_set_chunked_ell(self.handle, int(chunk)),
+                "mg_mesh_set_chunked_ell")
+
     def set_row_sweep(self, blocks: int):
         """Consecutive row blocks per CTA of the forward row kernel
         (mg_mesh_set_row_sweep); 0 or 1: one."""

@@ -126,6 +126,10 @@ struct mg_mesh {
   } tune[3];
   int dep_launch = 1;                     // row kernels launched as programmatic dependents
   Buf ellu;                               // ELL with every slice padded to wu columns
+  Buf ellc;                               // chunk-major ELL for cchunk lanes per row
+  int cchunk = 0;                         // its chunk (0: none)
+  int64_t cstride = 0;                    // entries per slice in it
+  bool chunked_ell = false;
   int wu = 0;
   bool uniform_ell = false;
   int cache_hints = 1;                    // kept history: L2 evict-first on last reads
@@ -164,6 +168,11 @@ mg::DevEll dev_ell(mg_mesh* M) {
   if (M->uniform_ell && M->ellu.p) {
     K.ellu = P<const int2>(M->ellu);
     K.wu = M->wu;
+  }
+  if (M->chunked_ell && M->ellc.p) {
+    K.ellc = P<const int2>(M->ellc);
+    K.cchunk = M->cchunk;
+    K.cstride = M->cstride;
   }
   return K;
 }
@@ -835,7 +844,8 @@ void mg_mesh_destroy(mg_mesh* M) {
   DeviceGuard g(M->device);
   Buf* all[] = {&M->ell, &M->slice_off, &M->slice_w, &M->nc_ptr, &M->nc_cell, &M->nc_w,
                 &M->nf_ptr, &M->nf_cell, &M->nf_w, &M->is_bnd, &M->row_abs, &M->cells,
-                &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas, &M->ellu};
+                &M->vol, &M->cf_ptr, &M->cf_facet, &M->bnd, &M->bnd_meas, &M->ellu,
+                &M->ellc};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto* v : {&M->anc, &M->lvl_ptr, &M->lvl_idx})
@@ -1014,6 +1024,52 @@ int mg_mesh_set_uniform_ell(mg_mesh* M, int on) {
     M->wu = w;
   }
   M->uniform_ell = true;
+  return MG_OK;
+}
+
+int mg_mesh_set_chunked_ell(mg_mesh* M, int chunk) {
+  if (!M || (chunk != 0 && chunk != 2 && chunk != 4 && chunk != 8 && chunk != 16 && chunk != 32))
+    return MG_ERR_ARG;
+  drop_graphs(M);
+  if (!chunk) {
+    M->chunked_ell = false;
+    return MG_OK;
+  }
+  if (!M->ellc.p || M->cchunk != chunk) {
+    const mg::HostMesh& h = M->hm;
+    int w = 0;
+    for (int32_t x : h.slice_w) w = std::max(w, (int)x);
+    const size_t stored = h.slice_off.empty() ? 0 : (size_t)h.slice_off.back();
+    if (stored == 0) return MG_ERR_UNSUPPORTED;
+    const int64_t nch = (w + chunk - 1) / chunk;
+    const int64_t stride = nch * mg::kSliceH * chunk;
+    const size_t total = (size_t)h.n_slices * stride;
+    DeviceGuard g(M->device);
+    if (!g.ok) return MG_ERR_CUDA;
+    // the host copy of the entries is released after upload: read them back
+    std::vector<mg::EllEntry> ell(stored);
+    if (cudaMemcpy(ell.data(), M->ell.p, stored * sizeof(mg::EllEntry),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return MG_ERR_CUDA;
+    // slots past a slice's width are never read: zero-filled
+    std::vector<int32_t> c(2 * total, 0);
+    for (int64_t s = 0; s < h.n_slices; ++s)
+      for (int k = 0; k < h.slice_w[s]; ++k)
+        for (int r = 0; r < mg::kSliceH; ++r) {
+          const size_t o = (size_t)s * stride + ((size_t)(k / chunk) * mg::kSliceH + r) * chunk +
+                           k % chunk;
+          std::memcpy(&c[2 * o], &ell[h.slice_off[s] + (size_t)k * mg::kSliceH + r],
+                      sizeof(mg::EllEntry));
+        }
+    if (M->ellc.p) {
+      cudaFree(M->ellc.p);
+      M->ellc = Buf{};
+    }
+    MG_TRY(upload(M->ellc, c));
+    M->cchunk = chunk;
+    M->cstride = stride;
+  }
+  M->chunked_ell = true;
   return MG_OK;
 }
 

@@ -15,6 +15,12 @@ struct DevEll {
   int32_t n;                // rows
   const int2* ellu = nullptr;  // row kernels: the same entries with every slice
   int32_t wu = 0;              // padded to wu columns (slice s at s * wu * 32)
+  // wide-lane forward with `cchunk` lanes per row: the same entries chunk
+  // by chunk, entry k of row rl of slice s at
+  // s * cstride + ((k / cchunk) * 32 + rl) * cchunk + k % cchunk
+  const int2* ellc = nullptr;
+  int32_t cchunk = 0;
+  int64_t cstride = 0;
 };
 
 // Per-row event lists built from a shot batch: sources and receivers.

@@ -85,6 +85,7 @@ struct Row {
   const int2* e;  // entry 0 of the row (stride kSliceH)
   int w;          // entries of the row's slice, diagonal first
   int na = 0;     // load the entries without allocating them in L1
+  int cs = 0;     // chunk-major entries: log2 of the chunk (LPR), 0 = by column
 };
 
 // Read-only per-row data (coefficients, stiffness entries) loaded once per
@@ -129,10 +130,30 @@ __device__ __forceinline__ Row row_of(const DevEll& K, int row) {
   return r;
 }
 
+static_assert(kSliceH == 32, "chunk-major entry addressing assumes 32-row slices");
+
 // Entry k of the row (padding {row, 0} past the slice width).
 __device__ __forceinline__ int2 entry_at(const Row& r, int k, int row) {
   if (k >= r.w) return make_int2(row, 0);
-  return r.na ? ldg_stream2(r.e + (size_t)k * kSliceH) : __ldg(r.e + (size_t)k * kSliceH);
+  const size_t o = r.cs ? ((size_t)(k >> r.cs) << (r.cs + 5)) + (k & ((1 << r.cs) - 1))
+                        : (size_t)k * kSliceH;
+  return r.na ? ldg_stream2(r.e + o) : __ldg(r.e + o);
+}
+
+// The row of a kernel with LPR lanes per row: the chunk-major copy of the
+// entries when it is laid out for LPR (a warp's chunk loads are then
+// RPW * LPR consecutive entries), else row_of.
+template <int LPR>
+__device__ __forceinline__ Row row_of_c(const DevEll& K, int row) {
+  if (K.ellc && K.cchunk == LPR && LPR >= 2) {
+    const int slice = row / kSliceH;
+    Row r;
+    r.e = K.ellc + (size_t)slice * K.cstride + (size_t)(row - slice * kSliceH) * LPR;
+    r.w = __ldg(K.slice_w + slice);
+    r.cs = __ffs(LPR) - 1;
+    return r;
+  }
+  return row_of(K, row);
 }
 
 // The entries of a row are read LPR at a time: each of the row's LPR lanes
@@ -474,7 +495,7 @@ __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
   const int lr = lane % LPR;
   const int tile0 = a.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
-  Row r = row_of(a.K, row);
+  Row r = row_of_c<LPR>(a.K, row);
   r.na = a.stream;
   grid_dep_sync();
   const size_t ro = (size_t)row * a.ld + base;
@@ -547,7 +568,12 @@ __device__ __forceinline__ void prefetch_next_block(const StepArgs& a, int blk) 
     prefetch_to(a.pm + ro + 4 * LPR * j, 2);
   }
   if (lr == 0) prefetch_to(a.coef + row, 2);
-  if (a.K.ellu) {
+  if (a.K.ellc && a.K.cchunk == LPR) {   // the first two chunks of the row's entries
+    const int s = row / kSliceH;
+    const int2* e = a.K.ellc + (size_t)s * a.K.cstride + (size_t)(row - s * kSliceH) * LPR + lr;
+    prefetch_to(e, 2);
+    if (a.K.cstride > (int64_t)kSliceH * LPR) prefetch_to(e + (size_t)kSliceH * LPR, 2);
+  } else if (a.K.ellu) {
     const int s = row / kSliceH;
     const int2* e = a.K.ellu + (size_t)s * a.K.wu * kSliceH + (row - s * kSliceH);
     if (lr < a.K.wu) prefetch_to(e + (size_t)lr * kSliceH, 2);
@@ -595,7 +621,7 @@ __device__ __forceinline__ void step_rows_block_w(const StepArgs& a, int blk) {
   const int lr = lane % LPR;
   const int tile0 = a.col0 + blockIdx.y * TW;
   const int base = tile0 + 8 * lr;
-  const Row r = row_of(a.K, row);
+  const Row r = row_of_c<LPR>(a.K, row);
   grid_dep_sync();
   const size_t ro = (size_t)row * a.ld + base;
   if (a.prefetch & 3) {
@@ -658,7 +684,7 @@ __device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk
   const int tile0 = a.f.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
   const int ld = a.f.ld;
-  Row r = row_of(a.f.K, row);
+  Row r = row_of_c<LPR>(a.f.K, row);
   r.na = a.f.stream;
   grid_dep_sync();
   const size_t ro = (size_t)row * ld + base;
@@ -750,7 +776,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_kept_rows(TangentArgs a) {
   const int tile0 = a.f.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
   const int ld = a.f.ld;
-  Row r = row_of(a.f.K, row);
+  Row r = row_of_c<LPR>(a.f.K, row);
   r.na = a.f.stream;
   grid_dep_sync();
   const float4 c = ld_coef(a.f.coef + row, a.f.stream);
@@ -813,7 +839,7 @@ __device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk
   __shared__ float acc_s[kWarps * 32][4];
   float* mine = acc_s[warp * RPW + lane / LPR];
   if (valid) {
-    Row r = row_of(a.K, row);
+    Row r = row_of_c<LPR>(a.K, row);
     r.na = a.stream;
     grid_dep_sync();
     if (lr == 0) {

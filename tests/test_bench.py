@@ -86,3 +86,18 @@ def test_oracle_sample_on_two_processes(bench, monkeypatch):
     assert all(u == units for _, u in res)
     assert math.isclose(val, 2 * units / max(t for t, _ in res))
     assert "2 shots of 128" in ora.sample_text()
+
+
+def test_lanes_per_row_and_entry_chunks(bench):
+    """The bench's copy of the launch-shape rule (lanes per row) and the
+    chunk each kind's launches use once the chunk-major entries are built."""
+    assert bench.lanes_per_row(128, 2) == 16 and bench.lanes_per_row(64, 1) == 16
+    assert bench.lanes_per_row(64, 2) == 8 and bench.lanes_per_row(256, 4) == 16
+    assert bench.lanes_per_row(100, 2) == 25          # falls back to one float4 per lane
+    t = {"forward": {"batch": 2, "tile_rows": 0, "groups": 1},
+         "tangent": {"batch": 1, "tile_rows": 0, "groups": 2},
+         "adjoint": {"batch": 2, "tile_rows": 64, "groups": 1}}
+    bench.mark_chunk(t, 128, 16)
+    assert [t[k]["ellc"] for k in ("forward", "tangent", "adjoint")] == [16, 16, 0]
+    k = {"batch": 2, "tile_rows": 0, "groups": 1, "min_blocks": 5}
+    assert bench.shape_key(dict(k, ellc=16)) != bench.shape_key(k)

@@ -884,9 +884,47 @@ def test_tuning_setters_reject_values_they_do_not_take(mg):
                lib.mg_mesh_set_late_prefetch(mesh.handle, -1, 3),
                lib.mg_mesh_set_late_prefetch(mesh.handle, K["forward"], 4),
                lib.mg_mesh_set_wide_lanes(mesh.handle, 2),
-               lib.mg_mesh_set_wide_lanes(None, 1)):
+               lib.mg_mesh_set_wide_lanes(None, 1),
+               lib.mg_mesh_set_chunked_ell(mesh.handle, 3),
+               lib.mg_mesh_set_chunked_ell(mesh.handle, 64)):
         assert rc == L.MG_ERR_ARG
     assert mesh.tuning() == before
     assert lib.mg_mesh_set_late_prefetch(mesh.handle, K["forward"], 3) == L.MG_OK
     assert lib.mg_mesh_set_kernel_min_blocks(mesh.handle, K["adjoint"], 6) == L.MG_OK
+    mesh.close()
+
+
+@pytest.mark.parametrize("S", [64, 37, 200])
+def test_wide_lanes_and_chunked_entries_give_identical_results(mg, S):
+    """The capped forward with two float4 per lane: wide lanes (8
+    consecutive shots per lane, 32-byte gathers) and the chunk-major copy of
+    the entries (for each lane count a launch may use), with and without the
+    row sweep, the next-block prefetch and the uniformly strided copy, carry
+    the bits of the uncapped two-load kernel; J^T w through its recomputed
+    forward as well.  Shot counts whose stride is not a multiple of 8 run the
+    two-load kernel."""
+    w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
+    eps = _dev(w.eps)
+    mesh = mg.mesh_from_workload(w)
+    mesh.set_tuning(-1, 2, 0, 32)
+    dt = oracle_dt(w)
+    s = _dev(w.wavelet(dt))
+    W = _dev(np.random.default_rng(5).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+
+    def run():
+        return (mg.forward(mesh, eps, w.shots, s, dt),
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+
+    ref = run()
+    mesh.set_min_blocks(5)
+    assert mesh.tuning()["forward"]["wide"] == 1
+    for chunk in (0, 2, 4, 8, 16, 32):
+        mesh.set_chunked_ell(chunk)
+        for uniform, sweep, pf in ((False, 0, 0), (True, 3, 3), (False, 5, 3)):
+            mesh.set_uniform_ell(uniform)
+            mesh.set_row_sweep(sweep)
+            mesh.set_late_prefetch(pf, "forward")
+            out = run()
+            assert torch.equal(ref[0], out[0]), (chunk, uniform, sweep, pf)
+            assert torch.equal(ref[1], out[1]), (chunk, uniform, sweep, pf)
     mesh.close()
