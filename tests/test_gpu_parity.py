@@ -900,8 +900,9 @@ def test_wide_lanes_and_chunked_entries_give_identical_results(mg, S):
     consecutive shots per lane, 32-byte gathers) and the chunk-major copy of
     the entries (for each lane count a launch may use), with and without the
     row sweep, the next-block prefetch and the uniformly strided copy, carry
-    the bits of the uncapped two-load kernel; J^T w through its recomputed
-    forward as well.  Shot counts whose stride is not a multiple of 8 run the
+    the bits of the uncapped two-load kernel; J^T w (its recomputed forward
+    and reverse steps) and J v (the tangent kernel) read the chunk-major
+    entries too and keep theirs.  Shot counts whose stride is not a multiple of 8 run the
     two-load kernel."""
     w = configs.asteroid_2d(n_refine=1, S=S, nt=300)
     eps = _dev(w.eps)
@@ -910,10 +911,12 @@ def test_wide_lanes_and_chunked_entries_give_identical_results(mg, S):
     dt = oracle_dt(w)
     s = _dev(w.wavelet(dt))
     W = _dev(np.random.default_rng(5).standard_normal((w.shots.n_traces, w.nt)), torch.float32)
+    v = _dev(np.random.default_rng(6).standard_normal(w.mesh.n_cells[1]))
 
     def run():
         return (mg.forward(mesh, eps, w.shots, s, dt),
-                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64))
+                mg.jacobian_T_apply(mesh, 1, eps, w.shots, s, dt, W, ckpt_every=64),
+                mg.jacobian_apply(mesh, 1, eps, w.shots, s, dt, v))
 
     ref = run()
     mesh.set_min_blocks(5)
@@ -925,6 +928,6 @@ def test_wide_lanes_and_chunked_entries_give_identical_results(mg, S):
             mesh.set_row_sweep(sweep)
             mesh.set_late_prefetch(pf, "forward")
             out = run()
-            assert torch.equal(ref[0], out[0]), (chunk, uniform, sweep, pf)
-            assert torch.equal(ref[1], out[1]), (chunk, uniform, sweep, pf)
+            for a, b in zip(ref, out):
+                assert torch.equal(a, b), (chunk, uniform, sweep, pf)
     mesh.close()
