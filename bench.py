@@ -279,7 +279,7 @@ def set_chunked(mesh, tuning, cols, arg, kind):
         chunk = 0
         if t["tile_rows"] == 0:
             lpr = lanes_per_row(cols // t.get("groups", 1), t["batch"])
-            chunk = lpr if lpr >= 2 and lpr & (lpr - 1) == 0 else 0
+            chunk = lpr if 2 <= lpr <= 16 and lpr & (lpr - 1) == 0 else 0
     mesh.set_chunked_ell(chunk)
     mark_chunk(tuning, cols, chunk)
     return chunk

@@ -377,7 +377,7 @@ int mg_mesh_set_wide_lanes(mg_mesh* mesh, int on);
 int mg_mesh_get_wide_lanes(const mg_mesh* mesh);
 
 /* Chunk-major copy of the stiffness entries for the wide-lane forward with
- * `chunk` lanes per row (2, 4, 8, 16 or 32; 0: off): entry k of row r of
+ * `chunk` lanes per row (2, 4, 8 or 16; 0: off): entry k of row r of
  * slice s at s * stride + ((k / chunk) * 32 + r) * chunk + k % chunk, so a
  * warp's load of one chunk of entries for its rows reads consecutive
  * entries instead of one 32-entry column per lane.  Built on the device

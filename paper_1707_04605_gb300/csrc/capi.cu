@@ -1028,7 +1028,7 @@ int mg_mesh_set_uniform_ell(mg_mesh* M, int on) {
 }
 
 int mg_mesh_set_chunked_ell(mg_mesh* M, int chunk) {
-  if (!M || (chunk != 0 && chunk != 2 && chunk != 4 && chunk != 8 && chunk != 16 && chunk != 32))
+  if (!M || (chunk != 0 && chunk != 2 && chunk != 4 && chunk != 8 && chunk != 16))
     return MG_ERR_ARG;
   drop_graphs(M);
   if (!chunk) {

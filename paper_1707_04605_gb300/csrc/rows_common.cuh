@@ -85,7 +85,6 @@ struct Row {
   const int2* e;  // entry 0 of the row (stride kSliceH)
   int w;          // entries of the row's slice, diagonal first
   int na = 0;     // load the entries without allocating them in L1
-  int cs = 0;     // chunk-major entries: log2 of the chunk (LPR), 0 = by column
 };
 
 // Read-only per-row data (coefficients, stiffness entries) loaded once per
@@ -118,42 +117,33 @@ __device__ __forceinline__ float2 ld_coef(const float2* p, int na) {
   return na ? ldg_stream2f(p) : __ldg(p);
 }
 
-// With the uniformly strided copy (K.ellu) the row's first entry address is
-// arithmetic, so the entry loads need not wait for the slice offset.
-__device__ __forceinline__ Row row_of(const DevEll& K, int row) {
-  const int slice = row / kSliceH;
+// The row as lane lr of its LPR lanes sees it: e points at the lane's entry
+// of the row's first chunk of LPR entries; the chunk starting at entry k0
+// lies 32 k0 entries further in both layouts.  By column (sliced or, with
+// K.ellu, uniformly strided: then the address is arithmetic and the entry
+// loads need not wait for the slice offset) entry k of slice row r is at
+// 32 k + r; in the chunk-major copy laid out for LPR lanes per row it is at
+// (k / LPR * 32 + r) * LPR + k % LPR (LPR 2 to 16).
+template <int LPR>
+__device__ __forceinline__ Row row_of_c(const DevEll& K, int row, int lr) {
+  const int slice = row / kSliceH, rl = row - slice * kSliceH;
   Row r;
-  const int2* base = K.ellu ? K.ellu + (size_t)slice * K.wu * kSliceH
-                            : K.ell + __ldg(K.slice_off + slice);
-  r.e = base + (row - slice * kSliceH);
+  if (LPR >= 2 && LPR <= 16 && K.cchunk == LPR) {
+    r.e = K.ellc + (size_t)slice * K.cstride + (size_t)rl * LPR + lr;
+  } else {
+    const int2* base = K.ellu ? K.ellu + (size_t)slice * K.wu * kSliceH
+                              : K.ell + __ldg(K.slice_off + slice);
+    r.e = base + rl + (size_t)lr * kSliceH;
+  }
   r.w = __ldg(K.slice_w + slice);
   return r;
 }
 
-static_assert(kSliceH == 32, "chunk-major entry addressing assumes 32-row slices");
-
-// Entry k of the row (padding {row, 0} past the slice width).
-__device__ __forceinline__ int2 entry_at(const Row& r, int k, int row) {
-  if (k >= r.w) return make_int2(row, 0);
-  const size_t o = r.cs ? ((size_t)(k >> r.cs) << (r.cs + 5)) + (k & ((1 << r.cs) - 1))
-                        : (size_t)k * kSliceH;
-  return r.na ? ldg_stream2(r.e + o) : __ldg(r.e + o);
-}
-
-// The row of a kernel with LPR lanes per row: the chunk-major copy of the
-// entries when it is laid out for LPR (a warp's chunk loads are then
-// RPW * LPR consecutive entries), else row_of.
-template <int LPR>
-__device__ __forceinline__ Row row_of_c(const DevEll& K, int row) {
-  if (K.ellc && K.cchunk == LPR && LPR >= 2) {
-    const int slice = row / kSliceH;
-    Row r;
-    r.e = K.ellc + (size_t)slice * K.cstride + (size_t)(row - slice * kSliceH) * LPR;
-    r.w = __ldg(K.slice_w + slice);
-    r.cs = __ffs(LPR) - 1;
-    return r;
-  }
-  return row_of(K, row);
+// Lane lr's entry of the chunk starting at entry k0 (a multiple of LPR);
+// padding {row, 0} past the slice width.
+__device__ __forceinline__ int2 entry_at(const Row& r, int k0, int lr, int row) {
+  if (k0 + lr >= r.w) return make_int2(row, 0);
+  return r.na ? ldg_stream2(r.e + (size_t)k0 * kSliceH) : __ldg(r.e + (size_t)k0 * kSliceH);
 }
 
 // The entries of a row are read LPR at a time: each of the row's LPR lanes
@@ -168,10 +158,10 @@ __device__ __forceinline__ Row row_of_c(const DevEll& K, int row) {
 //
 // MG_FOR_ENTRIES(LPR, r, row, lr, mask, cur, COL, V, BODY...) runs BODY with
 // COL, V bound to entries 1 .. w-1 in order; `cur` must hold entry lr of the
-// first chunk (entry_at(r, lr, row)) on entry.
+// first chunk (entry_at(r, 0, lr, row)) on entry.
 #define MG_FOR_ENTRIES(LPR, r, row, lr, mask, cur, COL, V, ...)                     \
   for (int k0_ = 0; k0_ < (r).w; k0_ += (LPR)) {                                    \
-    const int2 nxt_ = entry_at((r), k0_ + (LPR) + (lr), (row));                     \
+    const int2 nxt_ = entry_at((r), k0_ + (LPR), (lr), (row));                     \
     const int kn_ = min((LPR), (r).w - k0_);                                        \
     _Pragma("unroll 1") for (int k_ = k0_ == 0 ? 1 : 0; k_ < kn_; ++k_) {           \
       const int COL = __shfl_sync((mask), (cur).x, k_, (LPR));                       \
@@ -186,7 +176,7 @@ template <int LPR, int NV>
 __device__ __forceinline__ void row_sum(const Row& r, const float* __restrict__ xb, int row,
                                         int lr, unsigned mask, int ld, float4 (&self)[NV],
                                         float4 (&acc)[NV]) {
-  int2 cur = entry_at(r, lr, row);
+  int2 cur = entry_at(r, 0, lr, row);
   const float* xr = xb + (size_t)row * ld;
 #pragma unroll
   for (int j = 0; j < NV; ++j) self[j] = __ldg(reinterpret_cast<const float4*>(xr + 4 * LPR * j));
@@ -209,7 +199,7 @@ __device__ __forceinline__ void row_sum2(const Row& r, const float* __restrict__
                                          unsigned mask, int ld, float4 (&ps)[NV],
                                          float4 (&qs)[NV], float4 (&pacc)[NV],
                                          float4 (&qacc)[NV]) {
-  int2 cur = entry_at(r, lr, row);
+  int2 cur = entry_at(r, 0, lr, row);
   const size_t ro = (size_t)row * ld;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
@@ -273,7 +263,7 @@ __device__ __forceinline__ void st8(float* p, const F8& v) {
 template <int LPR>
 __device__ __forceinline__ void row_sum_w(const Row& r, const float* __restrict__ xb, int row,
                                           int lr, unsigned mask, int ld, F8& self, F8& acc) {
-  int2 cur = entry_at(r, lr, row);
+  int2 cur = entry_at(r, 0, lr, row);
   self = ldg8(xb + (size_t)row * ld);
   const float v0 = __int_as_float(__shfl_sync(mask, cur.y, 0, LPR));
   acc.a = scale4(v0, self.a);
@@ -332,8 +322,8 @@ __device__ __forceinline__ void ring_sum(const Row& r, const float* __restrict__
   float* rv = reinterpret_cast<float*>(ring_smem + (size_t)R * NX * kThreads);
   const int tid = threadIdx.x;
   const float* xs[2] = {x0, x1};
-  int2 cur = entry_at(r, lr, row);        // issue side: entries [ib, ib + LPR)
-  int2 nxt = entry_at(r, LPR + lr, row);  // and the next chunk, in flight
+  int2 cur = entry_at(r, 0, lr, row);        // issue side: entries [ib, ib + LPR)
+  int2 nxt = entry_at(r, LPR, lr, row);  // and the next chunk, in flight
   int ib = 0;
   const float v0 = __int_as_float(__shfl_sync(mask, cur.y, 0, LPR));
   const size_t ro = (size_t)row * ld;
@@ -351,7 +341,7 @@ __device__ __forceinline__ void ring_sum(const Row& r, const float* __restrict__
       if (i >= ib + LPR) {
         cur = nxt;
         ib += LPR;
-        nxt = entry_at(r, ib + LPR + lr, row);
+        nxt = entry_at(r, ib + LPR, lr, row);
       }
       const int col = __shfl_sync(mask, cur.x, i - ib, LPR);
       const float v = __int_as_float(__shfl_sync(mask, cur.y, i - ib, LPR));
@@ -495,7 +485,7 @@ __device__ __forceinline__ void step_rows_block(const StepArgs& a, int blk) {
   const int lr = lane % LPR;
   const int tile0 = a.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
-  Row r = row_of_c<LPR>(a.K, row);
+  Row r = row_of_c<LPR>(a.K, row, lr);
   r.na = a.stream;
   grid_dep_sync();
   const size_t ro = (size_t)row * a.ld + base;
@@ -568,7 +558,7 @@ __device__ __forceinline__ void prefetch_next_block(const StepArgs& a, int blk) 
     prefetch_to(a.pm + ro + 4 * LPR * j, 2);
   }
   if (lr == 0) prefetch_to(a.coef + row, 2);
-  if (a.K.ellc && a.K.cchunk == LPR) {   // the first two chunks of the row's entries
+  if (LPR >= 2 && LPR <= 16 && a.K.cchunk == LPR) {   // the first two chunks of the row's entries
     const int s = row / kSliceH;
     const int2* e = a.K.ellc + (size_t)s * a.K.cstride + (size_t)(row - s * kSliceH) * LPR + lr;
     prefetch_to(e, 2);
@@ -621,7 +611,7 @@ __device__ __forceinline__ void step_rows_block_w(const StepArgs& a, int blk) {
   const int lr = lane % LPR;
   const int tile0 = a.col0 + blockIdx.y * TW;
   const int base = tile0 + 8 * lr;
-  const Row r = row_of_c<LPR>(a.K, row);
+  const Row r = row_of_c<LPR>(a.K, row, lr);
   grid_dep_sync();
   const size_t ro = (size_t)row * a.ld + base;
   if (a.prefetch & 3) {
@@ -684,7 +674,7 @@ __device__ __forceinline__ void tangent_rows_block(const TangentArgs& a, int blk
   const int tile0 = a.f.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
   const int ld = a.f.ld;
-  Row r = row_of_c<LPR>(a.f.K, row);
+  Row r = row_of_c<LPR>(a.f.K, row, lr);
   r.na = a.f.stream;
   grid_dep_sync();
   const size_t ro = (size_t)row * ld + base;
@@ -776,7 +766,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_kept_rows(TangentArgs a) {
   const int tile0 = a.f.col0 + blockIdx.y * TW;
   const int base = tile0 + 4 * lr;
   const int ld = a.f.ld;
-  Row r = row_of_c<LPR>(a.f.K, row);
+  Row r = row_of_c<LPR>(a.f.K, row, lr);
   r.na = a.f.stream;
   grid_dep_sync();
   const float4 c = ld_coef(a.f.coef + row, a.f.stream);
@@ -839,7 +829,7 @@ __device__ __forceinline__ void adjoint_rows_block(const AdjointArgs& a, int blk
   __shared__ float acc_s[kWarps * 32][4];
   float* mine = acc_s[warp * RPW + lane / LPR];
   if (valid) {
-    Row r = row_of_c<LPR>(a.K, row);
+    Row r = row_of_c<LPR>(a.K, row, lr);
     r.na = a.stream;
     grid_dep_sync();
     if (lr == 0) {

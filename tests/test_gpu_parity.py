@@ -886,7 +886,7 @@ def test_tuning_setters_reject_values_they_do_not_take(mg):
                lib.mg_mesh_set_wide_lanes(mesh.handle, 2),
                lib.mg_mesh_set_wide_lanes(None, 1),
                lib.mg_mesh_set_chunked_ell(mesh.handle, 3),
-               lib.mg_mesh_set_chunked_ell(mesh.handle, 64)):
+               lib.mg_mesh_set_chunked_ell(mesh.handle, 32)):
         assert rc == L.MG_ERR_ARG
     assert mesh.tuning() == before
     assert lib.mg_mesh_set_late_prefetch(mesh.handle, K["forward"], 3) == L.MG_OK
@@ -921,7 +921,7 @@ def test_wide_lanes_and_chunked_entries_give_identical_results(mg, S):
     ref = run()
     mesh.set_min_blocks(5)
     assert mesh.tuning()["forward"]["wide"] == 1
-    for chunk in (0, 2, 4, 8, 16, 32):
+    for chunk in (0, 2, 4, 8, 16):
         mesh.set_chunked_ell(chunk)
         for uniform, sweep, pf in ((False, 0, 0), (True, 3, 3), (False, 5, 3)):
             mesh.set_uniform_ell(uniform)
