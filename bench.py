@@ -218,21 +218,22 @@ TRAFFIC = {
     # steady-state launches) summarised in profiles/launch_list_asteroid_2d_bench.md
     # and profiles/forward_ellipsoid_3d_s64.md.
     # k_tangent_rows<16, 1, 5, 0>, fused forward + tangent writing the kept
-    # history, register cap, two shot groups of 64 columns: 10.5 MB read +
-    # 24.4 MB written per launch, two launches per step
-    ("asteroid_2d fused", (1, 0, 2, 5, 0, 0, 0, 0), True): (69.9e6, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
+    # history, register cap, chunk-major entries, two shot groups of 64
+    # columns: 14.9 MB read + 25.1 MB written per launch, two launches per step
+    ("asteroid_2d fused", (1, 0, 2, 5, 0, 0, 0, 0, "ellc", 16), True): (80.0e6, "5d5b071a75ce9ada4d8afad12424f573dd928a35"),
     # k_adjoint_rows<16, 2, 5, 0>, reverse step on the kept history, register
-    # cap, one launch of 128 columns: 36.8 MB read + 21.1 MB written
-    ("asteroid_2d reverse", (2, 0, 1, 5, 0, 0, 0, 0), True): (57.9e6, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
+    # cap, chunk-major entries, one launch of 128 columns: 42.3 MB read +
+    # 21.6 MB written
+    ("asteroid_2d reverse", (2, 0, 1, 5, 0, 0, 0, 0, "ellc", 16), True): (63.9e6, "5d5b071a75ce9ada4d8afad12424f573dd928a35"),
     # k_tangent_rows<16, 1, 5, 0>, lockstep forward + tangent (J v of the
-    # checkpointed step), register cap, two shot groups: 9.4 MB read +
-    # 15.1 MB written per launch
-    ("asteroid_2d tangent", (1, 0, 2, 5, 0, 0, 0, 0), True): (49.0e6, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
+    # checkpointed step), register cap, chunk-major entries, two shot groups:
+    # 14.5 MB read + 17.1 MB written per launch
+    ("asteroid_2d tangent", (1, 0, 2, 5, 0, 0, 0, 0, "ellc", 16), True): (63.2e6, "5d5b071a75ce9ada4d8afad12424f573dd928a35"),
     # k_step_rows_w<8, 5>, wide lanes, register cap, 4 row blocks per CTA,
-    # prefetch level 3, uniformly strided stiffness: 1244.8 MB read + 465.7 MB
-    # written per launch
-    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4, 0, "prefetch", 3, "wide"), True):
-        (1.7105e9, "be487e4f9a98948b6885e1742bc9abdcd27d85e5"),
+    # prefetch level 3, uniformly strided stiffness with the chunk-major copy
+    # for 8 lanes per row: 1249.1 MB read + 465.9 MB written per launch
+    ("ellipsoid_3d forward", (2, 0, 1, 5, 0, 0, 4, 0, "prefetch", 3, "wide", "ellc", 8), True):
+        (1.715e9, "5d5b071a75ce9ada4d8afad12424f573dd928a35"),
 }
 
 
