@@ -515,13 +515,16 @@ int mg_mesh_get_tuning(const mg_mesh* mesh, int32_t* out);
  * least `steps` samples), keeps the fastest per kind on the handle and
  * returns it in chosen[17] (may be NULL).  Candidates: row kernels with 1,
  * 2 or 4 float4 per lane; tiles of 64, 128 or 256 rows with 16 or 32 shots
- * per pass; for the forward also the 2- and 4-vector row kernels with the
- * register cap of mg_mesh_set_min_blocks; row kernels with 1, 2 or 4 float4
- * per lane and a gather ring of 4 or 8 slots (mg_mesh_set_gather_ring; the
- * chosen depths are read with mg_mesh_get_gather_ring); for the forward the
- * row kernels with 1 vector per lane, and with 2 and 4 under the register
- * cap, sweeping 4 row blocks per CTA (mg_mesh_get_row_sweep); then 2, 4 and 8 shot groups on
- * the two fastest of those.  Each
+ * per pass; row kernels under the register cap of 5 resident CTAs per SM
+ * (mg_mesh_set_kernel_min_blocks; 1, 2 and 4 vectors per lane) and of 6
+ * for the adjoint (1 and 2 vectors); row
+ * kernels with 1, 2 or 4 float4 per lane and a gather ring of 4 or 8 slots
+ * (mg_mesh_set_gather_ring; the chosen depths are read with
+ * mg_mesh_get_gather_ring); for the forward the row kernels with 1 vector
+ * per lane, and with 2 and 4 under the register cap, sweeping 4 row blocks
+ * per CTA (mg_mesh_get_row_sweep); then 2, 4 and 8 shot groups on the two
+ * fastest of those.  The handle's L1 streaming, prefetch, wide-lane and
+ * stiffness-layout switches stay as they are.  Each
  * candidate is timed as the best of three runs after the GPU has been
  * warmed up; shapes within 1% of the fastest count as equal (the earliest
  * listed wins) and shot groups must win by more than 1%.  The choice is cached on
