@@ -866,7 +866,14 @@ def main():
                                         for k in ("forward", "adjoint", "tangent"))
     elif (args.tile_rows == -1 and args.src_tile == -1 and args.lane_vec == -1
             and not args.no_autotune):
-        # launch shapes per kernel kind, timed on this problem (setup, untimed)
+        # launch shapes per kernel kind, timed on this problem (setup, untimed),
+        # with the chunk-major entries of the two-float4 row shape in place,
+        # so that the shapes that read them are timed as they will run
+        if args.chunked_ell != 0:
+            s_pad = max(4, 1 << (S - 1).bit_length()) if S <= 128 else (S + 127) // 128 * 128
+            c0 = args.chunked_ell if args.chunked_ell > 0 else lanes_per_row(s_pad, 2)
+            if 2 <= c0 <= 16 and c0 & (c0 - 1) == 0:
+                mesh.set_chunked_ell(c0)
         mesh.autotune(eps_d, w.shots, wav_d, dt, steps=128, level=LEVEL)
     tuning = mesh.tuning()
     stream = torch.cuda.current_stream(dev)
